@@ -1,0 +1,294 @@
+#!/usr/bin/env python3
+"""Benchmark: Newton steps/s of the Polya/SDP interior-point method on one GB300.
+
+Workload: the mid-size system n=20, l=4, d_p=2, d1=d2=3 (K=2100 dual
+variables, 56 + 84 blocks of 20 x 20), s=0.3, seed 0 of the synthetic
+generator.  One "step" is one full predictor-corrector Newton step (Schur
+assembly, dense Cholesky, both solves, directions, step length, update,
+scalars) from the cold start X = Z = I, y = 0, which is restored (untimed)
+before every timed step together with an L2 flush.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched under torchrun) every rank solves its own instance
+(seed = rank): replicas, weak scaling, no collective on the data path.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="mid", n=20, l=4, d_p=2, d1=3, s=0.3, seed=0)
+METRIC = "Newton steps/s (plain FP64 path; time-to-certificate in e2e)"
+UNIT = "steps/s"
+NOMINAL_BF16_TFLOPS = 2250.0
+NOMINAL_FP64_TFLOPS = 1.25
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-runs", type=int, default=2)
+    ap.add_argument("--cpu-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def oracle_steps(A, w, nsteps):
+    """Time nsteps oracle Newton steps from the cold start (test infrastructure)."""
+    from oracle import ipm, sdp
+    prob = sdp.Problem(A, w["d_p"], w["d1"])
+    times = []
+    for _ in range(nsteps):
+        st = ipm.start_point(prob)
+        t0 = time.perf_counter()
+        ipm.newton_step(prob, st, ipm.Options())
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1411_3769_gb300 import synth
+    w = WORKLOAD
+    A = synth.system(w["n"], w["l"], w["s"], w["seed"])
+    oracle_steps(A, w, max(0, args.warmup))
+    times = oracle_steps(A, w, args.steps)
+    tot = sum(times)
+    v = args.steps / tot
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "n=20 l=4 d_p=2 d1=d2=3 (K=2100, 140 blocks) s=0.3 seed=0",
+                       "l2": "oracle on host cores"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} oracle Newton steps from the cold start"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1411_3769_gb300 import build
+    build.build()
+    from paper_1411_3769_gb300 import binding as bd
+    from paper_1411_3769_gb300 import synth
+
+    w = WORKLOAD
+    A = synth.system(w["n"], w["l"], w["s"], w["seed"] + rank)
+    stream = torch.cuda.current_stream()
+    opts = bd.psdp_default_opts(stream=stream.cuda_stream, device=local)
+    h = bd.psdp_setup(w["n"], w["l"], w["d_p"], w["d1"], A, opts)
+    X0, Z0, y0 = bd.psdp_get_iterate(h)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def one_step(timed):
+        bd.psdp_load_iterate(h, X0, Z0, y0)
+        flush.zero_()
+        if timed:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        s, info = bd.psdp_step(h)
+        if s != 0:
+            raise RuntimeError(f"psdp_step failed: {bd.STATUS[s]}")
+        if timed:
+            e1.record(stream)
+            return e0, e1
+        return None
+
+    for _ in range(max(args.warmup, 3)):
+        one_step(False)
+    bd.psdp_profile_enable(h, True)
+    one_step(False)             # re-capture the graph with profiling events
+    bd.psdp_profile_reset(h)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        evs = [one_step(True) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    tot_ms = sum(ms)
+    prof = bd.psdp_profile_get(h)
+    work = bd.psdp_work(h)
+    sizes = bd.psdp_sizes(h)
+    bd.psdp_profile_enable(h, False)
+    if dist:
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+        dist.barrier()
+
+    # ---- end to end through the C ABI with host buffers: setup + solve + certify + P
+    e2e = []
+    for _ in range(args.e2e_runs):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with bd.Solver(A, w["d_p"], w["d1"], device=local) as s:
+            status, iters, info = s.solve()
+            verdict, _, _ = s.certify()
+            P = bd.psdp_get_P(s.h)
+        t1 = time.perf_counter()
+        e2e.append((t1 - t0, iters, status, verdict, P.nbytes))
+    best = min(e2e, key=lambda r: r[0])
+    bd.psdp_destroy(h)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (from the live CUDA events)
+    pk, pk_kind = peaks()
+    fp64_peak = pk["bf16_tflops"] * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
+    K, nb = sizes["K"], 64
+    syrk_flops = trsm_flops = 0.0
+    for j0 in range(0, K, nb):
+        wdt = min(nb, K - j0)
+        rest = K - j0 - wdt
+        if rest <= 0:
+            break
+        syrk_flops += rest * (rest + 1) * wdt
+        trsm_flops += 2.0 * rest * wdt * wdt
+    kern = {}
+    for name, flops_per_step in (("schur_gemm", work["schur_flops"]), ("chol_syrk_gemm", syrk_flops),
+                                 ("chol_trsm_gemm", trsm_flops)):
+        if name in prof and prof[name][0] > 0:
+            launches, tms = prof[name]
+            per_step_launches = launches / args.steps
+            avg_ms = tms / launches
+            kern[name] = {"launches_per_step": per_step_launches, "avg_ms": avg_ms,
+                          "tflops": flops_per_step / per_step_launches / (avg_ms * 1e-3) / 1e12,
+                          "share_of_step": tms / tot_ms}
+    for name in ("chol_potrf_diag", "dense_solve", "schur_operands", "schur_gather", "block_chol_inv",
+                 "block_maxstep"):
+        if name in prof and prof[name][0] > 0:
+            kern[name] = {"launches_per_step": prof[name][0] / args.steps, "avg_ms": prof[name][1] / prof[name][0],
+                          "share_of_step": prof[name][1] / tot_ms}
+    dom = max(("schur_gemm", "chol_syrk_gemm"), key=lambda k: kern.get(k, {}).get("share_of_step", 0))
+    roof = {"kernel": "k_gemm_tn (" + dom + ")", "bound": "fp64", "achieved": kern[dom]["tflops"],
+            "peak": fp64_peak, "unit": "TFLOP/s", "frac": kern[dom]["tflops"] / fp64_peak, "traffic": None,
+            "peak_source": f"{pk_kind} bf16 {pk['bf16_tflops']} TFLOP/s x nominal FP64/BF16 ratio 1.25/2250"}
+    try:
+        roof["fp64_probe_tflops"] = bd.psdp_fp64_peak(local)
+    except Exception:
+        pass
+
+    # ---- CPU oracle baseline on a bounded sample
+    ct = oracle_steps(A, w, args.cpu_steps)
+    cpu = {"value": len(ct) / sum(ct), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"{len(ct)} oracle Newton steps of this workload from the cold start (numpy FP64)"}
+
+    t_job, iters, status, verdict, pbytes = best
+    value = world * args.steps / (tot_ms * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "n=20 l=4 d_p=2 d1=d2=3 (K=2100, 140 blocks of 20x20) s=0.3 seed=0",
+                       "precision": "plain FP64", "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roof, "kernels": kern,
+            "cpu_baseline": cpu,
+            "e2e": {"value": iters / t_job, "unit": UNIT, "h2d_bytes_per_step": A.nbytes / max(iters, 1),
+                    "d2h_bytes_per_step": (pbytes + 16 * 8 * iters) / max(iters, 1),
+                    "time_to_certificate_s": t_job, "newton_steps": iters, "status": status, "verdict": verdict},
+            "gpu_launches": int(work["kernels_per_step"]) * args.steps,
+            "clocks": clk.summary(),
+            "work": {"schur_flops_per_step": work["schur_flops"], "chol_flops_per_step": work["chol_flops"],
+                     "schur_terms": work["schur_terms"], "schur_dense_flops": work["schur_dense_flops"]}}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * polya_sdp.h -- C ABI of the GB300 (sm_103a) Polya/SDP robust-stability library.
+ *
+ * The library certifies that x' = A(alpha) x is stable for every alpha on the
+ * unit simplex (Theorem 1 of Kamyar, Peet & Peet, "Solving Large-Scale Robust
+ * Stability Problems by Exploiting the Parallel Structure of Polya's
+ * Theorem", IEEE TAC 2013).  It builds the block-diagonal SDP that Polya's
+ * theorem (Theorem 2) gives for a homogeneous Lyapunov matrix
+ * P(alpha) = sum_h P_h alpha^h (Sec. III) and solves it with the primal-dual
+ * predictor-corrector interior-point method of Sec. IV-A / Algorithm 2.  Every
+ * numerical step runs in the library's own CUDA kernels on one GPU.
+ *
+ * Conventions (all entry points):
+ *  - Every pointer argument is a HOST pointer unless stated otherwise.  The
+ *    library copies inputs; the caller keeps ownership of its buffers.  All
+ *    device memory is owned by the context and freed by psdp_destroy.
+ *  - Matrices are row-major float64: M[i*n + j] = M_ij.
+ *  - Monomial sets W_d are in the paper's lexicographic order, (d,0,...,0)
+ *    first (Sec. I, text and worked examples).
+ *  - Symmetric-matrix variables use the basis E_k of S^n (Sec. I): the n
+ *    diagonal entries first, then the first superdiagonal (r, r+1), then the
+ *    second (r, r+2), and so on ("svec order"); each off-diagonal basis matrix
+ *    has unit entries, so y_{q + Ntil*h} is the (r,s) entry of P_h (Eq. V_h).
+ *  - Block-diagonal matrices X, Z (Eq. S) are stored as (L+M) consecutive
+ *    n x n blocks: the L P-side blocks gamma in W_{d_p+d1}, then the M
+ *    Lyapunov blocks gamma in W_{d_p+d_a+d2}.
+ *  - No exception crosses the ABI; every call returns a psdp_status.  A NULL
+ *    context or output pointer gives PSDP_EINVAL.  After PSDP_ECUDA the
+ *    context must only be destroyed.
+ */
+#ifndef POLYA_SDP_H
+#define POLYA_SDP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct psdp_ctx psdp_ctx;
+
+typedef enum {
+    PSDP_OK = 0,
+    PSDP_EINVAL = 1,        /* bad argument (size, NULL pointer, non-finite A, ...) */
+    PSDP_ENOMEM = 2,        /* device allocation failed */
+    PSDP_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    PSDP_ECHOL_BLOCK = 4,   /* a block Z_gamma or X_gamma lost positive definiteness */
+    PSDP_ECHOL_SCHUR = 5,   /* the Schur complement Omega was not positive definite */
+    PSDP_EMAXITER = 6,      /* psdp_solve hit max_iter; the iterate stays valid */
+    PSDP_ESTEP = 7,         /* step length collapsed to zero */
+    PSDP_EUNBOUNDED = 8,    /* primal ray: the LMIs are infeasible at these degrees */
+    PSDP_ENAN = 9,          /* a non-finite scalar appeared */
+    PSDP_ETIMEOUT = 10,     /* a bounded device wait gave up */
+    PSDP_ESTATE = 11        /* call not valid in the context's current state */
+} psdp_status;
+
+typedef enum { PSDP_FP64 = 0, PSDP_MIXED = 1 } psdp_precision;
+
+typedef struct {
+    double delta;       /* delta of Eq. (Cj): C_gamma = delta*multinomial(gamma)*I; default 1 */
+    double delta_L;     /* optional strict margin on the Lyapunov blocks (paper: 0); default 0 */
+    double eps;         /* stopping tolerance of the relative gap and residuals; default 1e-7 */
+    double sigma;       /* centring parameter of mu = sigma*tr(ZX)/n_X; default 1/3 */
+    double tau;         /* step = min(1, tau * max feasible step); default 0.95 */
+    int    max_iter;    /* iteration cap of psdp_solve; default 100 */
+    int    d2;          /* Polya exponent of the Lyapunov inequality; < 0 means d2 = d1 */
+    int    d_a;         /* degree of the homogeneous A(alpha); default 1 (affine) */
+    int    precision;   /* psdp_precision; default PSDP_FP64 */
+    int    use_graph;   /* capture one Newton step in a CUDA graph and replay it; default 1 */
+    void*  stream;      /* cudaStream_t to run on; NULL: the context creates its own */
+    int    device;      /* CUDA device ordinal; default 0 */
+} psdp_opts;
+
+/* Number of doubles psdp_step / psdp_solve write to their info array. */
+#define PSDP_INFO_LEN 16
+/* info layout: 0 phi=tr(CX), 1 psi=a^T y, 2 relative gap, 3 relative primal residual,
+ * 4 relative dual residual, 5 mu, 6 t_p, 7 t_d, 8 tr(ZX), 9 tr(X), 10 ||B(X)||,
+ * 11 iterations done so far, 12 mixed-precision refinement sweeps of the last step,
+ * 13 1 if the last step fell back from mixed to FP64, 14-15 reserved. */
+
+/* Fill *o with the defaults listed above. */
+void psdp_default_opts(psdp_opts* o);
+
+/* Build the SDP of Sec. III for dx/dt = A(alpha) x and allocate a solver context.
+ *  n   : states, 1 <= n <= 112
+ *  l   : uncertain parameters (simplex dimension), 1 <= l <= 16
+ *  d_p : degree of P(alpha), d_p >= 0;   d1 : Polya exponent of P (Eq. LMI_1), d1 >= 0
+ *  A   : host, N_a * n * n doubles, N_a = card W_{d_a} = C(l+d_a-1, l-1): the
+ *        coefficients A_lambda of the homogeneous A(alpha) (Eq. A_alpha), lambda in
+ *        W_{d_a} in lexicographic order; for the affine case d_a = 1 these are A_1..A_l.
+ *  o   : options (NULL = defaults);   out : receives the context.
+ * The Polya tables beta (Eqs. beta_init/beta) and H (Eqs. H_init/H) are computed on
+ * the device; the iterate is set to the cold start X = Z = I, y = 0 (Algorithm 2).
+ * Errors: EINVAL for sizes outside the ranges or non-finite A; ENOMEM; ECUDA. */
+psdp_status psdp_setup(int n, int l, int d_p, int d1, const double* A,
+                       const psdp_opts* o, psdp_ctx** out);
+
+/* Sizes of the SDP: out[0..8] = n, l, L0 = card W_{d_p}, L = card W_{d_p+d1},
+ * M = card W_{d_p+d_a+d2}, Ntil = n(n+1)/2, K = L0*Ntil (Eq. K), L+M, N_a. */
+psdp_status psdp_sizes(const psdp_ctx* c, int32_t* out9);
+
+/* One predictor-corrector Newton step (Sec. IV-A, Processors/Root steps 1-4 of
+ * Algorithm 2) entirely on the device; info (may be NULL) receives PSDP_INFO_LEN
+ * doubles describing the new iterate.  ECHOL_BLOCK / ECHOL_SCHUR / ENAN leave the
+ * iterate unchanged. */
+psdp_status psdp_step(psdp_ctx* c, double* info);
+
+/* Repeat psdp_step until the relative gap and both relative residuals are <= eps
+ * (the paper's gap rule plus feasibility), a failure, a primal ray (EUNBOUNDED)
+ * or max_iter (EMAXITER).  iters/info may be NULL. */
+psdp_status psdp_solve(psdp_ctx* c, int* iters, double* info);
+
+/* Certificate of Theorems 1-2 from the current y: P_h = smat(y_h) (Root step 4);
+ * every P-side coefficient sum_h beta_{h,gamma} P_h (Eq. LMI_3) and every negated
+ * Lyapunov coefficient -sum_h (H^T P_h + P_h H) (Eq. LMI_4) must have its smallest
+ * FP64 eigenvalue above 64*n*2^-53*||.||_F.  verdict = 1 certified, 0 not.
+ * minP_margin = smallest eigenvalue over the P-side coefficients; maxLyap_margin =
+ * largest eigenvalue over the Lyapunov coefficients sum_h(H^T P_h + P_h H)
+ * (negative when certified).  Any output pointer may be NULL. */
+psdp_status psdp_certify(psdp_ctx* c, int* verdict, double* minP_margin, double* maxLyap_margin);
+
+/* Theorem 1 on the simplex lattice {gamma/N : gamma in W_N}: minP = min over the
+ * lattice of lambda_min(P(alpha)), maxQ = max of lambda_max(A^T P + P A). N >= 1. */
+psdp_status psdp_grid_check(psdp_ctx* c, int N, double* minP, double* maxQ);
+
+/* Copy out P_h (L0 * n * n doubles, full symmetric) or y (K doubles). */
+psdp_status psdp_get_P(psdp_ctx* c, double* P);
+psdp_status psdp_get_y(psdp_ctx* c, double* y);
+
+/* The integer Polya tables: beta (L0 x L, row h) and c (L0 x M x N_a) with
+ * H_{h,gamma} = sum_lambda c[h][gamma][lambda] A_lambda. */
+psdp_status psdp_get_tables(psdp_ctx* c, int32_t* beta, int32_t* cH);
+
+/* Replace / read the iterate: X, Z as (L+M)*n*n doubles, y as K doubles.  X and Z
+ * must be symmetric positive definite block by block (checked on the next step). */
+psdp_status psdp_load_iterate(psdp_ctx* c, const double* X, const double* Z, const double* y);
+psdp_status psdp_get_iterate(psdp_ctx* c, double* X, double* Z, double* y);
+
+/* Schur complement Omega_ij = sum_k tr(B_i^k Z_k^{-1} B_j^k X_k) (Sec. IV-A,
+ * Processors step 1) at the current iterate, as a full K x K matrix (lower triangle
+ * authoritative; FP64 in both precision modes).  Test and inspection hook. */
+psdp_status psdp_get_schur(psdp_ctx* c, double* Omega);
+
+/* Operator hooks for parity tests: out_blocks = B^T(v) (Eq. AT) and
+ * out = B(W) = (tr(B_i W))_i for block-diagonal W ((L+M)*n*n doubles). */
+psdp_status psdp_apply_BT(psdp_ctx* c, const double* v, double* out_blocks);
+psdp_status psdp_apply_B(psdp_ctx* c, const double* W_blocks, double* out);
+
+/* Per-kernel timing with CUDA events recorded on the context's stream around
+ * each launch of the library's heavy kernels.  psdp_profile_get writes up to
+ * max_entries records of (name[32], launches, total_ms) into names/launches/ms and
+ * returns the count in *count. */
+psdp_status psdp_profile_enable(psdp_ctx* c, int on);
+psdp_status psdp_profile_reset(psdp_ctx* c);
+psdp_status psdp_profile_get(psdp_ctx* c, int max_entries, char* names, int64_t* launches,
+                             double* ms, int* count);
+
+/* Algorithmic floating-point work of one Newton step: out[0] = Schur assembly
+ * flops over the non-zero (pair, block) terms, out[1] = Cholesky flops K^3/3,
+ * out[2] = Schur terms in the contraction (sum over block pairs), out[3] = dense
+ * Schur flops (every block for every pair), out[4] = kernel launches in one
+ * captured Newton step (0 before the first graph-mode step). */
+psdp_status psdp_work(const psdp_ctx* c, double* out5);
+
+/* The CUDA stream the context runs on (cudaStream_t as void*). */
+void* psdp_stream(psdp_ctx* c);
+
+/* Measure this GPU's FP64 FMA throughput with a short dependent-chain kernel;
+ * *tflops receives FP64 TFLOP/s (2 flops per FMA). */
+psdp_status psdp_fp64_peak(int device, double* tflops);
+
+void psdp_destroy(psdp_ctx* c);
+const char* psdp_strerror(psdp_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POLYA_SDP_H */

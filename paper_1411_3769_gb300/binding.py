@@ -1,0 +1,310 @@
+"""Thin ctypes binding of ``include/polya_sdp.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it wraps and does
+nothing but convert numpy arrays to pointers and statuses to exceptions; all
+computation happens in ``lib/libpolya_sdp.so``.  Loading fails loudly when the
+library has not been built: there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libpolya_sdp.so")
+
+INFO_LEN = 16
+INFO_FIELDS = ("phi", "psi", "relgap", "pres", "dres", "mu", "tp", "td", "trZX", "trX", "BXnorm",
+               "iters", "refine_sweeps", "fallback", "r14", "r15")
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ECHOL_BLOCK", 5: "ECHOL_SCHUR", 6: "EMAXITER",
+          7: "ESTEP", 8: "EUNBOUNDED", 9: "ENAN", 10: "ETIMEOUT", 11: "ESTATE"}
+
+# every symbol the header declares
+EXPORTS = ("psdp_default_opts", "psdp_setup", "psdp_sizes", "psdp_step", "psdp_solve", "psdp_certify",
+           "psdp_grid_check", "psdp_get_P", "psdp_get_y", "psdp_get_tables", "psdp_load_iterate",
+           "psdp_get_iterate", "psdp_get_schur", "psdp_apply_BT", "psdp_apply_B", "psdp_profile_enable",
+           "psdp_profile_reset", "psdp_profile_get", "psdp_work", "psdp_stream", "psdp_fp64_peak",
+           "psdp_destroy", "psdp_strerror")
+
+
+class Opts(C.Structure):
+    _fields_ = [("delta", C.c_double), ("delta_L", C.c_double), ("eps", C.c_double), ("sigma", C.c_double),
+                ("tau", C.c_double), ("max_iter", C.c_int), ("d2", C.c_int), ("d_a", C.c_int),
+                ("precision", C.c_int), ("use_graph", C.c_int), ("stream", C.c_void_p), ("device", C.c_int)]
+
+
+class PsdpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        super().__init__(f"{where}: {self.name} ({_lib().psdp_strerror(status).decode()})")
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1411_3769_gb300.build.build()")
+        lib = C.CDLL(LIB_PATH)
+        dp = C.POINTER(C.c_double)
+        ip = C.POINTER(C.c_int32)
+        vp = C.c_void_p
+        sig = {
+            "psdp_default_opts": (None, [C.POINTER(Opts)]),
+            "psdp_setup": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, dp, C.POINTER(Opts), C.POINTER(vp)]),
+            "psdp_sizes": (C.c_int, [vp, ip]),
+            "psdp_step": (C.c_int, [vp, dp]),
+            "psdp_solve": (C.c_int, [vp, C.POINTER(C.c_int), dp]),
+            "psdp_certify": (C.c_int, [vp, C.POINTER(C.c_int), dp, dp]),
+            "psdp_grid_check": (C.c_int, [vp, C.c_int, dp, dp]),
+            "psdp_get_P": (C.c_int, [vp, dp]),
+            "psdp_get_y": (C.c_int, [vp, dp]),
+            "psdp_get_tables": (C.c_int, [vp, ip, ip]),
+            "psdp_load_iterate": (C.c_int, [vp, dp, dp, dp]),
+            "psdp_get_iterate": (C.c_int, [vp, dp, dp, dp]),
+            "psdp_get_schur": (C.c_int, [vp, dp]),
+            "psdp_apply_BT": (C.c_int, [vp, dp, dp]),
+            "psdp_apply_B": (C.c_int, [vp, dp, dp]),
+            "psdp_profile_enable": (C.c_int, [vp, C.c_int]),
+            "psdp_profile_reset": (C.c_int, [vp]),
+            "psdp_profile_get": (C.c_int, [vp, C.c_int, C.c_char_p, C.POINTER(C.c_int64), dp, C.POINTER(C.c_int)]),
+            "psdp_work": (C.c_int, [vp, dp]),
+            "psdp_stream": (vp, [vp]),
+            "psdp_fp64_peak": (C.c_int, [C.c_int, dp]),
+            "psdp_destroy": (None, [vp]),
+            "psdp_strerror": (C.c_char_p, [C.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise PsdpError(status, where)
+
+
+def psdp_default_opts(**kw) -> Opts:
+    o = Opts()
+    _lib().psdp_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def psdp_setup(n: int, l: int, d_p: int, d1: int, A: np.ndarray, opts: Opts | None = None):
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    h = C.c_void_p()
+    _check(_lib().psdp_setup(n, l, d_p, d1, _dp(A), C.byref(opts) if opts is not None else None, C.byref(h)),
+           "psdp_setup")
+    return h
+
+
+def psdp_sizes(h) -> dict:
+    out = np.zeros(9, dtype=np.int32)
+    _check(_lib().psdp_sizes(h, _ip(out)), "psdp_sizes")
+    return dict(zip(("n", "l", "L0", "L", "M", "Ntil", "K", "nblk", "Na"), (int(x) for x in out)))
+
+
+def psdp_step(h) -> tuple[int, np.ndarray]:
+    info = np.zeros(INFO_LEN)
+    return _lib().psdp_step(h, _dp(info)), info
+
+
+def psdp_solve(h) -> tuple[int, int, np.ndarray]:
+    info = np.zeros(INFO_LEN)
+    it = C.c_int(0)
+    s = _lib().psdp_solve(h, C.byref(it), _dp(info))
+    return s, it.value, info
+
+
+def psdp_certify(h) -> tuple[int, float, float]:
+    v = C.c_int(0)
+    mp = np.zeros(1)
+    ml = np.zeros(1)
+    _check(_lib().psdp_certify(h, C.byref(v), _dp(mp), _dp(ml)), "psdp_certify")
+    return v.value, float(mp[0]), float(ml[0])
+
+
+def psdp_grid_check(h, N: int) -> tuple[float, float]:
+    mp = np.zeros(1)
+    mq = np.zeros(1)
+    _check(_lib().psdp_grid_check(h, N, _dp(mp), _dp(mq)), "psdp_grid_check")
+    return float(mp[0]), float(mq[0])
+
+
+def psdp_get_P(h) -> np.ndarray:
+    sz = psdp_sizes(h)
+    P = np.zeros((sz["L0"], sz["n"], sz["n"]))
+    _check(_lib().psdp_get_P(h, _dp(P)), "psdp_get_P")
+    return P
+
+
+def psdp_get_y(h) -> np.ndarray:
+    y = np.zeros(psdp_sizes(h)["K"])
+    _check(_lib().psdp_get_y(h, _dp(y)), "psdp_get_y")
+    return y
+
+
+def psdp_get_tables(h) -> tuple[np.ndarray, np.ndarray]:
+    sz = psdp_sizes(h)
+    beta = np.zeros((sz["L0"], sz["L"]), dtype=np.int32)
+    c = np.zeros((sz["L0"], sz["M"], sz["Na"]), dtype=np.int32)
+    _check(_lib().psdp_get_tables(h, _ip(beta), _ip(c)), "psdp_get_tables")
+    return beta, c
+
+
+def psdp_load_iterate(h, X: np.ndarray, Z: np.ndarray, y: np.ndarray):
+    X, Z, y = (np.ascontiguousarray(a, dtype=np.float64) for a in (X, Z, y))
+    _check(_lib().psdp_load_iterate(h, _dp(X), _dp(Z), _dp(y)), "psdp_load_iterate")
+
+
+def psdp_get_iterate(h):
+    sz = psdp_sizes(h)
+    X = np.zeros((sz["nblk"], sz["n"], sz["n"]))
+    Z = np.zeros_like(X)
+    y = np.zeros(sz["K"])
+    _check(_lib().psdp_get_iterate(h, _dp(X), _dp(Z), _dp(y)), "psdp_get_iterate")
+    return X, Z, y
+
+
+def psdp_get_schur(h) -> np.ndarray:
+    K = psdp_sizes(h)["K"]
+    Om = np.zeros((K, K))
+    _check(_lib().psdp_get_schur(h, _dp(Om)), "psdp_get_schur")
+    return Om
+
+
+def psdp_apply_BT(h, v: np.ndarray) -> np.ndarray:
+    sz = psdp_sizes(h)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    out = np.zeros((sz["nblk"], sz["n"], sz["n"]))
+    _check(_lib().psdp_apply_BT(h, _dp(v), _dp(out)), "psdp_apply_BT")
+    return out
+
+
+def psdp_apply_B(h, W: np.ndarray) -> np.ndarray:
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    out = np.zeros(psdp_sizes(h)["K"])
+    _check(_lib().psdp_apply_B(h, _dp(W), _dp(out)), "psdp_apply_B")
+    return out
+
+
+def psdp_profile_enable(h, on: bool = True):
+    _check(_lib().psdp_profile_enable(h, int(on)), "psdp_profile_enable")
+
+
+def psdp_profile_reset(h):
+    _check(_lib().psdp_profile_reset(h), "psdp_profile_reset")
+
+
+def psdp_profile_get(h, max_entries: int = 64) -> dict:
+    names = C.create_string_buffer(32 * max_entries)
+    launches = np.zeros(max_entries, dtype=np.int64)
+    ms = np.zeros(max_entries)
+    cnt = C.c_int(0)
+    _check(_lib().psdp_profile_get(h, max_entries, names, launches.ctypes.data_as(C.POINTER(C.c_int64)), _dp(ms),
+                                   C.byref(cnt)), "psdp_profile_get")
+    out = {}
+    raw = names.raw
+    for i in range(cnt.value):
+        nm = raw[32 * i:32 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (int(launches[i]), float(ms[i]))
+    return out
+
+
+def psdp_work(h) -> dict:
+    out = np.zeros(5)
+    _check(_lib().psdp_work(h, _dp(out)), "psdp_work")
+    return dict(schur_flops=out[0], chol_flops=out[1], schur_terms=out[2], schur_dense_flops=out[3],
+                kernels_per_step=int(out[4]))
+
+
+def psdp_stream(h) -> int:
+    return _lib().psdp_stream(h) or 0
+
+
+def psdp_fp64_peak(device: int = 0) -> float:
+    v = np.zeros(1)
+    _check(_lib().psdp_fp64_peak(device, _dp(v)), "psdp_fp64_peak")
+    return float(v[0])
+
+
+def psdp_destroy(h):
+    if h:
+        _lib().psdp_destroy(h)
+
+
+def psdp_strerror(status: int) -> str:
+    return _lib().psdp_strerror(status).decode()
+
+
+class Solver:
+    """Owning handle: ``Solver(A, d_p, d1, **opts)`` then ``.solve()``, ``.certify()``."""
+
+    def __init__(self, A: np.ndarray, d_p: int, d1: int, **opts):
+        A = np.asarray(A, dtype=np.float64)
+        self.n = A.shape[-1]
+        d_a = opts.get("d_a", 1)
+        self.l = opts.pop("l", None) or _infer_l(A.shape[0], d_a)
+        self.h = psdp_setup(self.n, self.l, d_p, d1, A, psdp_default_opts(**opts))
+        self.sizes = psdp_sizes(self.h)
+
+    def step(self) -> dict:
+        s, info = psdp_step(self.h)
+        _check(s, "psdp_step")
+        return dict(zip(INFO_FIELDS, info))
+
+    def solve(self) -> tuple[str, int, dict]:
+        s, it, info = psdp_solve(self.h)
+        if s not in (0, 6, 8):
+            raise PsdpError(s, "psdp_solve")
+        return STATUS[s], it, dict(zip(INFO_FIELDS, info))
+
+    def certify(self):
+        return psdp_certify(self.h)
+
+    def close(self):
+        psdp_destroy(self.h)
+        self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                self.close()
+        except Exception:
+            pass
+
+
+def _infer_l(Na: int, d_a: int) -> int:
+    from math import comb
+    l = 1
+    while comb(l + d_a - 1, l - 1) < Na:
+        l += 1
+    return l

@@ -1,0 +1,783 @@
+// C ABI of the Polya/SDP library: context set-up, the Newton-step orchestration
+// (one CUDA graph per step), solve / certify and the inspection hooks.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "psdp_internal.h"
+
+void dense_cholesky(cudaStream_t st, double* A, int K, int nb, double* Linv, int* flag);
+void dense_solve(cudaStream_t st, const double* A, int K, int nb, const double* Linv, double* partial, double* x);
+void launch_vec_copy(cudaStream_t st, int K, const double* a, double* out);
+void launch_cdiag(cudaStream_t st, psdp_ctx* c);
+void init_attrs_linalg(int smem_max);
+void init_attrs_sdp(int smem_max);
+void init_attrs_dense(int smem_max);
+
+namespace {
+
+int64_t hbinom(int nn, int kk) {
+    if (kk < 0 || nn < 0 || kk > nn) return 0;
+    int64_t r = 1;
+    for (int i = 1; i <= kk; ++i) r = r * (nn - kk + i) / i;
+    return r;
+}
+int64_t hcard(int l, int d) { return (l <= 0 || d < 0) ? 0 : hbinom(l + d - 1, l - 1); }
+
+template <class T>
+psdp_status dalloc(T** p, size_t count) {
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc((void**)p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return PSDP_ENOMEM;
+    }
+    return PSDP_OK;
+}
+
+#define TRY(x) do { psdp_status s__ = (x); if (s__ != PSDP_OK) return s__; } while (0)
+
+// ------------------------------------------------------------------ profiling
+int prof_name_id(psdp_ctx* c, const char* name) {
+    for (size_t i = 0; i < c->prof_names.size(); ++i)
+        if (c->prof_names[i] == name) return (int)i;
+    c->prof_names.emplace_back(name);
+    c->prof_launches.push_back(0);
+    c->prof_ms.push_back(0.0);
+    return (int)c->prof_names.size() - 1;
+}
+
+int prof_begin(psdp_ctx* c, const char* name) {
+    if (!c->prof_on || c->prof_pool_used + 2 > c->prof_pool.size()) return -1;
+    ProfSite s;
+    s.name_id = prof_name_id(c, name);
+    s.a = c->prof_pool[c->prof_pool_used++];
+    s.b = c->prof_pool[c->prof_pool_used++];
+    cudaEventRecord(s.a, c->stream);
+    c->prof_sites.push_back(s);
+    return (int)c->prof_sites.size() - 1;
+}
+
+void prof_end(psdp_ctx* c, int site) {
+    if (site < 0) return;
+    cudaEventRecord(c->prof_sites[site].b, c->stream);
+}
+
+void prof_collect(psdp_ctx* c) {
+    if (!c->prof_on) return;
+    for (const ProfSite& s : c->prof_sites) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, s.a, s.b) == cudaSuccess) {
+            c->prof_ms[s.name_id] += ms;
+            c->prof_launches[s.name_id] += 1;
+        }
+    }
+    cudaGetLastError();
+}
+
+struct ProfScope {
+    psdp_ctx* c;
+    int site;
+    ProfScope(psdp_ctx* cc, const char* name) : c(cc), site(prof_begin(cc, name)) {}
+    ~ProfScope() { prof_end(c, site); }
+};
+
+// ---------------------------------------------------------------- step pieces
+void enqueue_schur(psdp_ctx* c) {
+    cudaStream_t st = c->stream;
+    {
+        ProfScope p(c, "schur_operands");
+        launch_schur_operands(st, c);
+    }
+    for (int p0 = 0; p0 < c->npairs; p0 += c->pairs_per_chunk) {
+        const int np = std::min(c->pairs_per_chunk, c->npairs - p0);
+        {
+            ProfScope p(c, "schur_gemm");
+            launch_gemm_tn(st, c->n2, c->n2, np, c->d_Aop, c->n2, c->d_term_off + p0, 0, c->d_Bop, c->n2,
+                           c->d_term_off + p0, 0, c->d_term_cnt + p0, 0, c->d_Tbuf, c->n2, (int64_t)c->n2 * c->n2,
+                           1.0, 0.0, 0);
+        }
+        {
+            ProfScope p(c, "schur_gather");
+            launch_schur_gather(st, c, p0, np);
+        }
+    }
+}
+
+// Omega = L L^T in place (column-major lower view of the row-major upper
+// triangle), right-looking with panels of nb_chol columns; the diagonal-block
+// inverses are kept for the triangular solves.
+void enqueue_cholesky(psdp_ctx* c) {
+    cudaStream_t st = c->stream;
+    const int K = c->K, nb = c->nb_chol;
+    double* A = c->d_Om;
+    for (int j0 = 0, p = 0; j0 < K; j0 += nb, ++p) {
+        const int w = std::min(nb, K - j0);
+        double* Lp = c->d_Linv + (size_t)p * nb * nb;
+        {
+            ProfScope q(c, "chol_potrf_diag");
+            launch_potrf_diag(st, A, K, j0, nb, Lp, c->d_flag);
+        }
+        const int rest = K - j0 - w;
+        if (rest <= 0) break;
+        double* panel = A + (int64_t)j0 * K + j0 + w;
+        {
+            // panel <- panel L_jj^{-T}:  C[k][i] = sum_m Linv(k,m) P(i,m)
+            ProfScope q(c, "chol_trsm_gemm");
+            launch_gemm_tn(st, w, rest, 1, Lp, nb, nullptr, 0, panel, K, nullptr, 0, nullptr, w, panel, K, 0, 1.0,
+                           0.0, 0);
+        }
+        {
+            // trailing lower triangle -= P P^T
+            ProfScope q(c, "chol_syrk_gemm");
+            launch_gemm_tn(st, rest, rest, 1, panel, K, nullptr, 0, panel, K, nullptr, 0, nullptr, w,
+                           A + (int64_t)(j0 + w) * K + j0 + w, K, 0, -1.0, 1.0, 1);
+        }
+    }
+}
+
+void enqueue_refresh(psdp_ctx* c) {
+    cudaStream_t st = c->stream;
+    launch_bt(st, c, c->d_y, c->d_T1);
+    launch_ew_G(st, c, c->d_T1, c->d_Z, c->d_G);
+    launch_b(st, c, c->d_X, c->d_BX, 0.0);
+    launch_partials(st, c);
+    launch_finalize(st, c, 0);
+}
+
+void enqueue_step(psdp_ctx* c) {
+    cudaStream_t st = c->stream;
+    const int n = c->n, nb = c->nblk;
+    c->prof_sites.clear();
+    c->prof_pool_used = 0;
+    {
+        ProfScope p(c, "block_chol_inv");
+        launch_block_chol_inv(st, nb, n, c->d_Z, c->d_Y, c->d_flag);
+    }
+    enqueue_schur(c);
+    // predictor right-hand side: B(Y G X) - a
+    launch_bgemm(st, n, nb, c->d_Y, nullptr, 1, 0, c->d_G, nullptr, 1, 0, c->d_T1, nullptr, 1, 0, 1.0, 0.0);
+    launch_bgemm(st, n, nb, c->d_T1, nullptr, 1, 0, c->d_X, nullptr, 1, 0, c->d_W, nullptr, 1, 0, 1.0, 0.0);
+    launch_b(st, c, c->d_W, c->d_dyh, 1.0);
+    enqueue_cholesky(c);
+    {
+        ProfScope p(c, "dense_solve");
+        dense_solve(st, c->d_Om, c->K, c->nb_chol, c->d_Linv, c->d_rhs, c->d_dyh);
+    }
+    // predictor directions
+    launch_bt(st, c, c->d_dyh, c->d_T2);
+    launch_ew_pred(st, c, c->d_G, c->d_T2, c->d_T1, c->d_dZh);
+    launch_bgemm(st, n, nb, c->d_Y, nullptr, 1, 0, c->d_T1, nullptr, 1, 0, c->d_W, nullptr, 1, 0, 1.0, 0.0);
+    launch_bgemm(st, n, nb, c->d_W, nullptr, 1, 0, c->d_X, nullptr, 1, 0, c->d_T2, nullptr, 1, 0, 1.0, 0.0);
+    launch_ew_symsub(st, c, c->d_T2, c->d_X, c->d_dXh);
+    // corrector right-hand side: B(mu Y - Y dZh dXh)
+    launch_bgemm(st, n, nb, c->d_Y, nullptr, 1, 0, c->d_dZh, nullptr, 1, 0, c->d_T1, nullptr, 1, 0, 1.0, 0.0);
+    launch_bgemm(st, n, nb, c->d_T1, nullptr, 1, 0, c->d_dXh, nullptr, 1, 0, c->d_W, nullptr, 1, 0, 1.0, 0.0);
+    launch_ew_muY(st, c, c->d_Y, c->d_W, c->d_scal + SC_MU, c->d_F);
+    launch_b(st, c, c->d_F, c->d_dyb, 0.0);
+    {
+        ProfScope p(c, "dense_solve");
+        dense_solve(st, c->d_Om, c->K, c->nb_chol, c->d_Linv, c->d_rhs, c->d_dyb);
+    }
+    // corrector directions and totals
+    launch_bt(st, c, c->d_dyb, c->d_T2);
+    launch_bgemm(st, n, nb, c->d_Y, nullptr, 1, 0, c->d_T2, nullptr, 1, 0, c->d_T1, nullptr, 1, 0, 1.0, 0.0);
+    launch_bgemm(st, n, nb, c->d_T1, nullptr, 1, 0, c->d_X, nullptr, 1, 0, c->d_W, nullptr, 1, 0, 1.0, 0.0);
+    launch_ew_corr(st, c, c->d_F, c->d_W, c->d_dXh, c->d_dZh, c->d_T2, c->d_dX, c->d_dZ);
+    {
+        ProfScope p(c, "block_maxstep");
+        launch_block_maxstep(st, nb, n, c->d_X, c->d_dX, c->d_Z, c->d_dZ, c->d_tstep, c->d_flag);
+    }
+    launch_steplen(st, c);
+    launch_update(st, c);
+    enqueue_refresh(c);
+    cudaMemcpyAsync(c->h_info, c->d_info, PSDP_INFO_LEN * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(c->h_flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+}
+
+psdp_status sync_check(psdp_ctx* c) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return PSDP_ECUDA;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return PSDP_ECUDA;
+    return PSDP_OK;
+}
+
+psdp_status refresh(psdp_ctx* c) {
+    enqueue_refresh(c);
+    cudaMemcpyAsync(c->h_info, c->d_info, PSDP_INFO_LEN * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    return sync_check(c);
+}
+
+void free_ctx(psdp_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    void* ptrs[] = {c->d_beta, c->d_cH, c->d_W0, c->d_Wa, c->d_A, c->d_H, c->d_cdiag, c->d_X, c->d_Z, c->d_G,
+                    c->d_Y, c->d_T1, c->d_T2, c->d_W, c->d_F, c->d_dXh, c->d_dZh, c->d_dX, c->d_dZ, c->d_S,
+                    c->d_adj, c->d_adj2, c->d_y, c->d_dyh, c->d_dyb, c->d_rhs, c->d_BX, c->d_part, c->d_tstep,
+                    c->d_scal, c->d_info, c->d_flag, c->d_pair_a, c->d_pair_b, c->d_term_off, c->d_term_cnt,
+                    c->d_term_desc, c->d_term_w, c->d_uv_idx, c->d_prod_idx, c->d_U, c->d_V, c->d_Aop, c->d_Bop,
+                    c->d_Tbuf, c->d_Om, c->d_Linv, c->d_grid, c->d_svec, c->d_cert};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->h_info) cudaFreeHost(c->h_info);
+    if (c->h_flag) cudaFreeHost(c->h_flag);
+    for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    cudaGetLastError();
+    delete c;
+}
+
+psdp_status build_schur_lists(psdp_ctx* c) {
+    const int L0 = c->L0, L = c->L, M = c->M, Na = c->Na;
+    std::vector<char> hz((size_t)L0 * M, 0);
+    for (int h = 0; h < L0; ++h)
+        for (int g = 0; g < M; ++g)
+            for (int li = 0; li < Na; ++li)
+                if (c->cH[((size_t)h * M + g) * Na + li]) hz[(size_t)h * M + g] = 1;
+    std::vector<int32_t> desc, prod_a2, prod_b2, prod_c2, prod_a3, prod_b3, prod_c3;
+    std::vector<double> w;
+    c->pair_a.clear();
+    c->pair_b.clear();
+    c->term_off.clear();
+    c->term_cnt.clear();
+    int t = 0;
+    double dense_terms = 0;
+    for (int a = 0; a < L0; ++a)
+        for (int b = a; b < L0; ++b) {
+            c->pair_a.push_back(a);
+            c->pair_b.push_back(b);
+            c->term_off.push_back(t);
+            const int t0 = t;
+            dense_terms += L + 4.0 * M;
+            for (int g = 0; g < L; ++g) {
+                const int wt = c->beta[(size_t)a * L + g] * c->beta[(size_t)b * L + g];
+                if (!wt) continue;
+                const int32_t d[8] = {1, g, 0, 2, g, 0, 0, 0};
+                desc.insert(desc.end(), d, d + 8);
+                w.push_back((double)wt);
+                ++t;
+            }
+            for (int g = 0; g < M; ++g) {
+                if (!hz[(size_t)a * M + g] || !hz[(size_t)b * M + g]) continue;
+                const int blk = L + g, ia = a * M + g, ib = b * M + g;
+                const int32_t d1[8] = {3, ib, 0, 4, ia, 1, 0, 0};   // (Y H_b^T, (X H_a^T)^T)
+                const int32_t d2[8] = {1, blk, 0, 0, 0, 0, 0, 0};   // (Y, H_a X H_b^T)
+                const int32_t d3[8] = {0, 0, 0, 2, blk, 0, 0, 0};   // (H_a Y H_b^T, X)
+                const int32_t d4[8] = {3, ia, 1, 4, ib, 0, 0, 0};   // ((Y H_a^T)^T, X H_b^T)
+                desc.insert(desc.end(), d1, d1 + 8);
+                desc.insert(desc.end(), d2, d2 + 8);
+                desc.insert(desc.end(), d3, d3 + 8);
+                desc.insert(desc.end(), d4, d4 + 8);
+                w.insert(w.end(), {1.0, 1.0, 1.0, 1.0});
+                prod_a2.push_back(ia); prod_b2.push_back(ib); prod_c2.push_back(t + 1);
+                prod_a3.push_back(ia); prod_b3.push_back(ib); prod_c3.push_back(t + 2);
+                t += 4;
+            }
+            c->term_cnt.push_back(t - t0);
+        }
+    c->npairs = (int)c->pair_a.size();
+    c->nterms = t;
+    c->nlyap_prod = (int)prod_a2.size();
+    if ((int64_t)c->nterms * c->n2 >= ((int64_t)1 << 31)) return PSDP_EINVAL;
+    c->flops_schur_dense = 2.0 * c->n2 * (double)c->n2 * dense_terms;
+    c->flops_schur = 2.0 * c->n2 * (double)c->n2 * (double)c->nterms;
+    std::vector<int32_t> offs(c->npairs);
+    for (int p = 0; p < c->npairs; ++p) offs[p] = c->term_off[p] * c->n2;
+    TRY(dalloc(&c->d_pair_a, c->npairs));
+    TRY(dalloc(&c->d_pair_b, c->npairs));
+    TRY(dalloc(&c->d_term_off, c->npairs));
+    TRY(dalloc(&c->d_term_cnt, c->npairs));
+    TRY(dalloc(&c->d_term_desc, (size_t)8 * std::max(1, t)));
+    TRY(dalloc(&c->d_term_w, std::max(1, t)));
+    const int np = c->nlyap_prod;
+    TRY(dalloc(&c->d_prod_idx, (size_t)6 * std::max(1, np)));
+    cudaMemcpy(c->d_pair_a, c->pair_a.data(), c->npairs * sizeof(int32_t), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->d_pair_b, c->pair_b.data(), c->npairs * sizeof(int32_t), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->d_term_off, offs.data(), c->npairs * sizeof(int32_t), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->d_term_cnt, c->term_cnt.data(), c->npairs * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (t) {
+        cudaMemcpy(c->d_term_desc, desc.data(), desc.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->d_term_w, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice);
+    }
+    if (np) {
+        std::vector<int32_t> all;
+        for (auto* v : {&prod_a2, &prod_b2, &prod_c2, &prod_a3, &prod_b3, &prod_c3}) all.insert(all.end(), v->begin(), v->end());
+        cudaMemcpy(c->d_prod_idx, all.data(), all.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    }
+    std::vector<int32_t> uv((size_t)L0 * M);
+    for (int e = 0; e < L0 * M; ++e) uv[e] = e % M;
+    TRY(dalloc(&c->d_uv_idx, uv.size()));
+    cudaMemcpy(c->d_uv_idx, uv.data(), uv.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    TRY(dalloc(&c->d_U, (size_t)L0 * M * c->n2));
+    TRY(dalloc(&c->d_V, (size_t)L0 * M * c->n2));
+    TRY(dalloc(&c->d_Aop, (size_t)std::max(1, t) * c->n2));
+    TRY(dalloc(&c->d_Bop, (size_t)std::max(1, t) * c->n2));
+    // contraction output: as many pairs per launch as fit in ~2 GiB
+    const size_t per_pair = (size_t)c->n2 * c->n2 * sizeof(double);
+    c->pairs_per_chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)c->npairs, ((size_t)2 << 30) / per_pair));
+    TRY(dalloc(&c->d_Tbuf, (size_t)c->pairs_per_chunk * c->n2 * c->n2));
+    return PSDP_OK;
+}
+
+psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psdp_opts* o, psdp_ctx** out) {
+    psdp_opts opt;
+    psdp_default_opts(&opt);
+    if (o) opt = *o;
+    const int d2 = opt.d2 < 0 ? d1 : opt.d2;
+    const int d_a = opt.d_a;
+    if (n < 1 || n > PSDP_MAX_N || l < 1 || l > PSDP_MAX_L || d_p < 0 || d1 < 0 || d2 < 0 || d_a < 1 ||
+        d_p > 12 || d1 > 12 || d2 > 12 || d_a > 12 || !A)
+        return PSDP_EINVAL;
+    if (!(opt.tau > 0 && opt.tau < 1) || !(opt.sigma >= 0 && opt.sigma < 1) || !(opt.eps > 0) || opt.max_iter < 1 ||
+        !std::isfinite(opt.delta) || !std::isfinite(opt.delta_L))
+        return PSDP_EINVAL;
+    const int64_t Na = hcard(l, d_a), L0 = hcard(l, d_p), L = hcard(l, d_p + d1), M = hcard(l, d_p + d_a + d2);
+    const int64_t Nt = (int64_t)n * (n + 1) / 2, K = L0 * Nt;
+    if (K > 65536 || L + M > 100000 || L0 * M * Na > (1 << 26)) return PSDP_EINVAL;
+    for (int64_t i = 0; i < Na * n * n; ++i)
+        if (!std::isfinite(A[i])) return PSDP_EINVAL;
+    if (cudaSetDevice(opt.device) != cudaSuccess) { cudaGetLastError(); return PSDP_ECUDA; }
+    int smem_max = 0;
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, opt.device);
+    if ((size_t)2 * n * (n + 1) * sizeof(double) + 4 * n * sizeof(double) > (size_t)smem_max) return PSDP_EINVAL;
+    init_attrs_linalg(smem_max);
+    init_attrs_sdp(smem_max);
+    init_attrs_dense(smem_max);
+
+    psdp_ctx* c = new (std::nothrow) psdp_ctx();
+    if (!c) return PSDP_ENOMEM;
+    c->n = n; c->l = l; c->d_p = d_p; c->d1 = d1; c->d2 = d2; c->d_a = d_a;
+    c->L0 = (int)L0; c->L = (int)L; c->M = (int)M; c->Na = (int)Na; c->Nt = (int)Nt; c->K = (int)K;
+    c->nblk = (int)(L + M); c->n2 = n * n;
+    c->opt = opt;
+    c->device = opt.device;
+    c->flops_chol = (double)K * K * K / 3.0;
+    if (opt.stream) {
+        c->stream = (cudaStream_t)opt.stream;
+        c->own_stream = false;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { free_ctx(c); return PSDP_ECUDA; }
+        c->own_stream = true;
+    }
+    psdp_status s = PSDP_OK;
+    auto fail = [&](psdp_status e) { free_ctx(c); return e; };
+    const size_t nbn2 = (size_t)c->nblk * c->n2;
+    if ((s = dalloc(&c->d_beta, (size_t)L0 * L)) || (s = dalloc(&c->d_cH, (size_t)L0 * M * Na)) ||
+        (s = dalloc(&c->d_W0, (size_t)L0 * l)) || (s = dalloc(&c->d_Wa, (size_t)Na * l)) ||
+        (s = dalloc(&c->d_A, (size_t)Na * c->n2)) || (s = dalloc(&c->d_H, (size_t)L0 * M * c->n2)) ||
+        (s = dalloc(&c->d_cdiag, c->nblk)))
+        return fail(s);
+    double** blocks[] = {&c->d_X, &c->d_Z, &c->d_G, &c->d_Y, &c->d_T1, &c->d_T2, &c->d_W, &c->d_F,
+                         &c->d_dXh, &c->d_dZh, &c->d_dX, &c->d_dZ};
+    for (double** p : blocks)
+        if ((s = dalloc(p, nbn2))) return fail(s);
+    if ((s = dalloc(&c->d_S, (size_t)M * Na * c->n2)) || (s = dalloc(&c->d_adj, (size_t)L0 * (Na + 1) * c->n2)) ||
+        (s = dalloc(&c->d_adj2, (size_t)L0 * Na * c->n2)))
+        return fail(s);
+    const int nbc = c->nb_chol;
+    const int npanel = (int)((K + nbc - 1) / nbc);
+    const size_t rhs_len = std::max<size_t>(K, (size_t)nbc * (K / 2048 + 2));
+    double** vecs[] = {&c->d_y, &c->d_dyh, &c->d_dyb, &c->d_BX};
+    for (double** p : vecs)
+        if ((s = dalloc(p, (size_t)K))) return fail(s);
+    if ((s = dalloc(&c->d_rhs, rhs_len)) || (s = dalloc(&c->d_part, (size_t)4 * (c->nblk + 1))) ||
+        (s = dalloc(&c->d_tstep, (size_t)2 * c->nblk)) || (s = dalloc(&c->d_scal, SC_COUNT)) ||
+        (s = dalloc(&c->d_info, PSDP_INFO_LEN)) || (s = dalloc(&c->d_flag, 1)) || (s = dalloc(&c->d_cert, 4)) ||
+        (s = dalloc(&c->d_Om, (size_t)K * K)) || (s = dalloc(&c->d_Linv, (size_t)npanel * nbc * nbc)) ||
+        (s = dalloc(&c->d_svec, (size_t)2 * Nt)))
+        return fail(s);
+    if (cudaMallocHost((void**)&c->h_info, PSDP_INFO_LEN * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void**)&c->h_flag, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PSDP_ENOMEM);
+    }
+    cudaStream_t st = c->stream;
+    cudaMemsetAsync(c->d_flag, 0, sizeof(int), st);
+    cudaMemsetAsync(c->d_scal, 0, SC_COUNT * sizeof(double), st);
+    cudaMemsetAsync(c->d_info, 0, PSDP_INFO_LEN * sizeof(double), st);
+    cudaMemcpyAsync(c->d_A, A, (size_t)Na * c->n2 * sizeof(double), cudaMemcpyHostToDevice, st);
+    launch_tables(st, l, d_p, d1, d2, d_a, c->L0, c->L, c->M, c->Na, c->d_beta, c->d_cH, c->d_W0, c->d_Wa);
+    launch_cdiag(st, c);
+    launch_hmat(st, c->L0, c->M, c->Na, n, c->d_cH, c->d_A, c->d_H);
+    c->beta.resize((size_t)L0 * L);
+    c->cH.resize((size_t)L0 * M * Na);
+    c->cdiag.resize(c->nblk);
+    cudaMemcpyAsync(c->beta.data(), c->d_beta, c->beta.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(c->cH.data(), c->d_cH, c->cH.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(c->cdiag.data(), c->d_cdiag, c->nblk * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if ((s = sync_check(c))) return fail(s);
+    std::vector<int32_t> sv;
+    for (int off = 0; off < n; ++off)
+        for (int r = 0; r + off < n; ++r) { sv.push_back(r); sv.push_back(r + off); }
+    cudaMemcpy(c->d_svec, sv.data(), sv.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if ((s = build_schur_lists(c))) return fail(s);
+    launch_identity(st, c->nblk, n, c->d_X);
+    launch_identity(st, c->nblk, n, c->d_Z);
+    cudaMemsetAsync(c->d_y, 0, (size_t)K * sizeof(double), st);
+    if ((s = refresh(c))) return fail(s);
+    *out = c;
+    return PSDP_OK;
+}
+
+psdp_status step_impl(psdp_ctx* c, double* info) {
+    cudaSetDevice(c->device);
+    if (c->opt.use_graph) {
+        if (!c->have_graph) {
+            if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PSDP_ECUDA;
+            enqueue_step(c);
+            if (cudaStreamEndCapture(c->stream, &c->graph) != cudaSuccess) { cudaGetLastError(); return PSDP_ECUDA; }
+            if (cudaGraphInstantiate(&c->graph_exec, c->graph, 0) != cudaSuccess) { cudaGetLastError(); return PSDP_ECUDA; }
+            c->have_graph = true;
+            size_t nn = 0;
+            cudaGraphGetNodes(c->graph, nullptr, &nn);
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (nn) cudaGraphGetNodes(c->graph, nodes.data(), &nn);
+            int nk = 0;
+            for (size_t i = 0; i < nn; ++i) {
+                cudaGraphNodeType ty;
+                if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++nk;
+            }
+            c->kernels_per_step = nk;
+        }
+        if (cudaGraphLaunch(c->graph_exec, c->stream) != cudaSuccess) return PSDP_ECUDA;
+    } else {
+        enqueue_step(c);
+    }
+    TRY(sync_check(c));
+    prof_collect(c);
+    c->h_info[11] = (double)(c->iters + 1);
+    const int flag = *c->h_flag;
+    if (flag) {
+        cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream);
+        TRY(sync_check(c));
+        if (info) memcpy(info, c->h_info, PSDP_INFO_LEN * sizeof(double));
+        if (flag & FL_CHOL_BLOCK) return PSDP_ECHOL_BLOCK;
+        if (flag & FL_CHOL_SCHUR) return PSDP_ECHOL_SCHUR;
+        if (flag & FL_TIMEOUT) return PSDP_ETIMEOUT;
+        return PSDP_ENAN;
+    }
+    c->iters += 1;
+    if (info) memcpy(info, c->h_info, PSDP_INFO_LEN * sizeof(double));
+    return PSDP_OK;
+}
+
+void invalidate_graph(psdp_ctx* c) {
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+    c->have_graph = false;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+extern "C" {
+
+void psdp_default_opts(psdp_opts* o) {
+    if (!o) return;
+    o->delta = 1.0;
+    o->delta_L = 0.0;
+    o->eps = 1e-7;
+    o->sigma = 1.0 / 3.0;
+    o->tau = 0.95;
+    o->max_iter = 100;
+    o->d2 = -1;
+    o->d_a = 1;
+    o->precision = PSDP_FP64;
+    o->use_graph = 1;
+    o->stream = nullptr;
+    o->device = 0;
+}
+
+psdp_status psdp_setup(int n, int l, int d_p, int d1, const double* A, const psdp_opts* o, psdp_ctx** out) {
+    if (!out) return PSDP_EINVAL;
+    *out = nullptr;
+    try {
+        return setup_impl(n, l, d_p, d1, A, o, out);
+    } catch (...) {
+        return PSDP_ENOMEM;
+    }
+}
+
+psdp_status psdp_sizes(const psdp_ctx* c, int32_t* o) {
+    if (!c || !o) return PSDP_EINVAL;
+    const int32_t v[9] = {c->n, c->l, c->L0, c->L, c->M, c->Nt, c->K, c->nblk, c->Na};
+    memcpy(o, v, sizeof(v));
+    return PSDP_OK;
+}
+
+psdp_status psdp_step(psdp_ctx* c, double* info) {
+    if (!c) return PSDP_EINVAL;
+    try {
+        return step_impl(c, info);
+    } catch (...) {
+        return PSDP_ENOMEM;
+    }
+}
+
+psdp_status psdp_solve(psdp_ctx* c, int* iters, double* info) {
+    if (!c) return PSDP_EINVAL;
+    double inf[PSDP_INFO_LEN];
+    psdp_status s = PSDP_EMAXITER;
+    int it = 0;
+    for (; it < c->opt.max_iter; ++it) {
+        psdp_status r = psdp_step(c, inf);
+        if (r != PSDP_OK) {
+            s = r;
+            ++it;
+            break;
+        }
+        const double eps = c->opt.eps;
+        if (inf[2] <= eps && inf[3] <= eps && inf[4] <= eps) {
+            s = PSDP_OK;
+            ++it;
+            break;
+        }
+        // primal ray: X grows without bound along B(X) ~ 0 with tr(CX) > 0
+        const double trX = inf[9];
+        if (trX > 1e8 && inf[10] / trX < 1e-6 && inf[0] / trX > 1e-8) {
+            s = PSDP_EUNBOUNDED;
+            ++it;
+            break;
+        }
+    }
+    if (iters) *iters = it;
+    if (info) memcpy(info, c->h_info, PSDP_INFO_LEN * sizeof(double));
+    return s;
+}
+
+psdp_status psdp_certify(psdp_ctx* c, int* verdict, double* minP, double* maxL) {
+    if (!c) return PSDP_EINVAL;
+    cudaSetDevice(c->device);
+    cudaStream_t st = c->stream;
+    launch_bt(st, c, c->d_y, c->d_T1);
+    launch_block_mineig(st, c->nblk, c->n, c->d_T1, 1.0, c->d_tstep);
+    launch_certify_finalize(st, c->nblk, c->n, c->d_tstep, c->L, c->d_cert);
+    double h[3];
+    cudaMemcpyAsync(h, c->d_cert, 3 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    TRY(sync_check(c));
+    if (verdict) *verdict = (int)h[0];
+    if (minP) *minP = h[1];
+    if (maxL) *maxL = h[2];
+    return PSDP_OK;
+}
+
+psdp_status psdp_grid_check(psdp_ctx* c, int N, double* minP, double* maxQ) {
+    if (!c || N < 1 || N > 4096) return PSDP_EINVAL;
+    cudaSetDevice(c->device);
+    const int64_t total = hcard(c->l, N);
+    const int chunk = (int)std::min<int64_t>(total, 2048);
+    const size_t need = (size_t)3 * chunk * c->n2 + (size_t)4 * chunk;
+    if (c->grid_cap < need) {
+        if (c->d_grid) cudaFree(c->d_grid);
+        c->d_grid = nullptr;
+        c->grid_cap = 0;
+        TRY(dalloc(&c->d_grid, need));
+        c->grid_cap = need;
+    }
+    double* P = c->d_grid;
+    double* Aal = P + (size_t)chunk * c->n2;
+    double* Q = Aal + (size_t)chunk * c->n2;
+    double* eig = Q + (size_t)chunk * c->n2;
+    std::vector<double> h((size_t)4 * chunk);
+    double mp = 1e300, mq = -1e300;
+    cudaStream_t st = c->stream;
+    for (int64_t first = 0; first < total; first += chunk) {
+        const int cnt = (int)std::min<int64_t>(chunk, total - first);
+        launch_grid_build(st, c, N, first, cnt, P, Aal);
+        launch_bgemm(st, c->n, cnt, Aal, nullptr, 1, 1, P, nullptr, 1, 0, Q, nullptr, 1, 0, 1.0, 0.0);
+        launch_bgemm(st, c->n, cnt, P, nullptr, 1, 0, Aal, nullptr, 1, 0, Q, nullptr, 1, 0, 1.0, 1.0);
+        launch_block_mineig(st, cnt, c->n, P, 1.0, eig);
+        launch_block_mineig(st, cnt, c->n, Q, -1.0, eig + 2 * chunk);
+        cudaMemcpyAsync(h.data(), eig, (size_t)4 * chunk * sizeof(double), cudaMemcpyDeviceToHost, st);
+        TRY(sync_check(c));
+        for (int i = 0; i < cnt; ++i) {
+            mp = std::min(mp, h[2 * i]);
+            mq = std::max(mq, -h[2 * chunk + 2 * i]);
+        }
+    }
+    if (minP) *minP = mp;
+    if (maxQ) *maxQ = mq;
+    return PSDP_OK;
+}
+
+psdp_status psdp_get_P(psdp_ctx* c, double* P) {
+    if (!c || !P) return PSDP_EINVAL;
+    std::vector<double> y(c->K);
+    TRY(psdp_get_y(c, y.data()));
+    const int n = c->n;
+    for (int h = 0; h < c->L0; ++h) {
+        int q = 0;
+        for (int off = 0; off < n; ++off)
+            for (int r = 0; r + off < n; ++r, ++q) {
+                const double v = y[(size_t)h * c->Nt + q];
+                P[((size_t)h * n + r) * n + r + off] = v;
+                P[((size_t)h * n + r + off) * n + r] = v;
+            }
+    }
+    return PSDP_OK;
+}
+
+psdp_status psdp_get_y(psdp_ctx* c, double* y) {
+    if (!c || !y) return PSDP_EINVAL;
+    cudaSetDevice(c->device);
+    cudaMemcpyAsync(y, c->d_y, (size_t)c->K * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    return sync_check(c);
+}
+
+psdp_status psdp_get_tables(psdp_ctx* c, int32_t* beta, int32_t* cH) {
+    if (!c) return PSDP_EINVAL;
+    if (beta) memcpy(beta, c->beta.data(), c->beta.size() * sizeof(int32_t));
+    if (cH) memcpy(cH, c->cH.data(), c->cH.size() * sizeof(int32_t));
+    return PSDP_OK;
+}
+
+psdp_status psdp_load_iterate(psdp_ctx* c, const double* X, const double* Z, const double* y) {
+    if (!c || !X || !Z || !y) return PSDP_EINVAL;
+    cudaSetDevice(c->device);
+    const size_t nb = (size_t)c->nblk * c->n2 * sizeof(double);
+    cudaMemcpyAsync(c->d_X, X, nb, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->d_Z, Z, nb, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->d_y, y, (size_t)c->K * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    return refresh(c);
+}
+
+psdp_status psdp_get_iterate(psdp_ctx* c, double* X, double* Z, double* y) {
+    if (!c) return PSDP_EINVAL;
+    cudaSetDevice(c->device);
+    const size_t nb = (size_t)c->nblk * c->n2 * sizeof(double);
+    if (X) cudaMemcpyAsync(X, c->d_X, nb, cudaMemcpyDeviceToHost, c->stream);
+    if (Z) cudaMemcpyAsync(Z, c->d_Z, nb, cudaMemcpyDeviceToHost, c->stream);
+    if (y) cudaMemcpyAsync(y, c->d_y, (size_t)c->K * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    return sync_check(c);
+}
+
+psdp_status psdp_get_schur(psdp_ctx* c, double* Om) {
+    if (!c || !Om) return PSDP_EINVAL;
+    cudaSetDevice(c->device);
+    cudaStream_t st = c->stream;
+    cudaMemsetAsync(c->d_flag, 0, sizeof(int), st);
+    launch_block_chol_inv(st, c->nblk, c->n, c->d_Z, c->d_Y, c->d_flag);
+    const bool on = c->prof_on;
+    c->prof_on = false;
+    enqueue_schur(c);
+    c->prof_on = on;
+    int flag = 0;
+    cudaMemcpyAsync(Om, c->d_Om, (size_t)c->K * c->K * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    TRY(sync_check(c));
+    if (flag) {
+        cudaMemsetAsync(c->d_flag, 0, sizeof(int), st);
+        sync_check(c);
+        return PSDP_ECHOL_BLOCK;
+    }
+    const size_t K = c->K;
+    for (size_t i = 0; i < K; ++i)
+        for (size_t j = 0; j < i; ++j) Om[i * K + j] = Om[j * K + i];
+    return PSDP_OK;
+}
+
+psdp_status psdp_apply_BT(psdp_ctx* c, const double* v, double* out) {
+    if (!c || !v || !out) return PSDP_EINVAL;
+    cudaSetDevice(c->device);
+    cudaStream_t st = c->stream;
+    cudaMemcpyAsync(c->d_dyb, v, (size_t)c->K * sizeof(double), cudaMemcpyHostToDevice, st);
+    launch_bt(st, c, c->d_dyb, c->d_T1);
+    cudaMemcpyAsync(out, c->d_T1, (size_t)c->nblk * c->n2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    return sync_check(c);
+}
+
+psdp_status psdp_apply_B(psdp_ctx* c, const double* W, double* out) {
+    if (!c || !W || !out) return PSDP_EINVAL;
+    cudaSetDevice(c->device);
+    cudaStream_t st = c->stream;
+    cudaMemcpyAsync(c->d_T1, W, (size_t)c->nblk * c->n2 * sizeof(double), cudaMemcpyHostToDevice, st);
+    launch_b(st, c, c->d_T1, c->d_dyb, 0.0);
+    cudaMemcpyAsync(out, c->d_dyb, (size_t)c->K * sizeof(double), cudaMemcpyDeviceToHost, st);
+    return sync_check(c);
+}
+
+psdp_status psdp_profile_enable(psdp_ctx* c, int on) {
+    if (!c) return PSDP_EINVAL;
+    cudaSetDevice(c->device);
+    if (on && c->prof_pool.empty()) {
+        c->prof_pool.resize(8192);
+        for (auto& e : c->prof_pool)
+            if (cudaEventCreate(&e) != cudaSuccess) return PSDP_ECUDA;
+    }
+    if ((bool)on != c->prof_on) invalidate_graph(c);
+    c->prof_on = on != 0;
+    return PSDP_OK;
+}
+
+psdp_status psdp_profile_reset(psdp_ctx* c) {
+    if (!c) return PSDP_EINVAL;
+    std::fill(c->prof_launches.begin(), c->prof_launches.end(), 0);
+    std::fill(c->prof_ms.begin(), c->prof_ms.end(), 0.0);
+    return PSDP_OK;
+}
+
+psdp_status psdp_profile_get(psdp_ctx* c, int max_entries, char* names, int64_t* launches, double* ms, int* count) {
+    if (!c || !count) return PSDP_EINVAL;
+    const int nn = std::min<int>(max_entries, (int)c->prof_names.size());
+    for (int i = 0; i < nn; ++i) {
+        if (names) {
+            memset(names + 32 * i, 0, 32);
+            strncpy(names + 32 * i, c->prof_names[i].c_str(), 31);
+        }
+        if (launches) launches[i] = c->prof_launches[i];
+        if (ms) ms[i] = c->prof_ms[i];
+    }
+    *count = nn;
+    return PSDP_OK;
+}
+
+psdp_status psdp_work(const psdp_ctx* c, double* out) {
+    if (!c || !out) return PSDP_EINVAL;
+    out[0] = c->flops_schur;
+    out[1] = c->flops_chol;
+    out[2] = (double)c->nterms;
+    out[3] = c->flops_schur_dense;
+    out[4] = (double)c->kernels_per_step;
+    return PSDP_OK;
+}
+
+void* psdp_stream(psdp_ctx* c) { return c ? (void*)c->stream : nullptr; }
+
+psdp_status psdp_fp64_peak(int device, double* tflops) {
+    if (!tflops) return PSDP_EINVAL;
+    const double v = fp64_peak_probe(device);
+    if (v <= 0) return PSDP_ECUDA;
+    *tflops = v;
+    return PSDP_OK;
+}
+
+void psdp_destroy(psdp_ctx* c) { free_ctx(c); }
+
+const char* psdp_strerror(psdp_status s) {
+    switch (s) {
+        case PSDP_OK: return "ok";
+        case PSDP_EINVAL: return "invalid argument";
+        case PSDP_ENOMEM: return "device allocation failed";
+        case PSDP_ECUDA: return "CUDA error";
+        case PSDP_ECHOL_BLOCK: return "a block of X or Z is not positive definite";
+        case PSDP_ECHOL_SCHUR: return "Schur complement is not positive definite";
+        case PSDP_EMAXITER: return "iteration limit reached";
+        case PSDP_ESTEP: return "step length collapsed";
+        case PSDP_EUNBOUNDED: return "primal ray found: LMIs infeasible at these degrees";
+        case PSDP_ENAN: return "non-finite value";
+        case PSDP_ETIMEOUT: return "bounded device wait gave up";
+        case PSDP_ESTATE: return "call not valid in the current state";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

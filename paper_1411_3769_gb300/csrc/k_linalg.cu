@@ -1,0 +1,525 @@
+// Dense FP64 building blocks: batched n x n GEMM, the tiled TN GEMM used by the
+// Schur-complement contraction and the Cholesky trailing update, per-block
+// Cholesky / inverse, per-block smallest eigenvalue (Householder
+// tridiagonalisation + Sturm-count multisection) and the per-block maximum step.
+#include <cfloat>
+#include <cmath>
+
+#include "psdp_internal.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Sum over the CTA in a fixed order; every thread gets the same value.
+__device__ double block_sum(double v, double* red) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    const int nw = blockDim.x >> 5;
+    for (int i = 0; i < nw; ++i) s += red[i];
+    return s;
+}
+
+// ---------------------------------------------------------------- batched GEMM
+constexpr int BG = 32;
+
+__global__ void __launch_bounds__(kThreads)
+k_bgemm(int n, int count, const double* __restrict__ A, const int32_t* __restrict__ ia, int sa, int ta,
+        const double* __restrict__ B, const int32_t* __restrict__ ib, int sb, int tb,
+        double* C, const int32_t* __restrict__ ic, int sc, int tc, double alpha, double beta) {
+    __shared__ double As[BG][BG + 1];
+    __shared__ double Bs[BG][BG + 1];
+    const int tiles = (n + BG - 1) / BG;
+    const int i0 = (blockIdx.x / tiles) * BG, j0 = (blockIdx.x % tiles) * BG;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const size_t n2 = (size_t)n * n;
+    for (int e = blockIdx.y; e < count; e += gridDim.y) {
+        const double* Ae = A + (size_t)(ia ? ia[e] : e * sa) * n2;
+        const double* Be = B + (size_t)(ib ? ib[e] : e * sb) * n2;
+        double* Ce = C + (size_t)(ic ? ic[e] : e * sc) * n2;
+        double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+        for (int k0 = 0; k0 < n; k0 += BG) {
+            for (int idx = threadIdx.x; idx < BG * BG; idx += kThreads) {
+                const int a = idx / BG, b = idx % BG;
+                int i, k;
+                if (!ta) { i = i0 + a; k = k0 + b; } else { k = k0 + a; i = i0 + b; }
+                double v = 0.0;
+                if (i < n && k < n) v = ta ? Ae[(size_t)k * n + i] : Ae[(size_t)i * n + k];
+                As[k - k0][i - i0] = v;
+                int j;
+                if (!tb) { k = k0 + a; j = j0 + b; } else { j = j0 + a; k = k0 + b; }
+                double w = 0.0;
+                if (j < n && k < n) w = tb ? Be[(size_t)j * n + k] : Be[(size_t)k * n + j];
+                Bs[k - k0][j - j0] = w;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int kk = 0; kk < BG; ++kk) {
+                const double a0 = As[kk][ty], a1 = As[kk][ty + 16];
+                const double b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+                acc[0][0] = fma(a0, b0, acc[0][0]);
+                acc[0][1] = fma(a0, b1, acc[0][1]);
+                acc[1][0] = fma(a1, b0, acc[1][0]);
+                acc[1][1] = fma(a1, b1, acc[1][1]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const int i = i0 + ty + 16 * r, j = j0 + tx + 16 * s;
+                if (i < n && j < n) {
+                    const size_t o = tc ? (size_t)j * n + i : (size_t)i * n + j;
+                    double val = alpha * acc[r][s];
+                    if (beta != 0.0) val += beta * Ce[o];
+                    Ce[o] = val;
+                }
+            }
+    }
+}
+
+// ------------------------------------------------------------------ TN GEMM
+// C[r][c] = alpha * sum_k A[k*lda + r] * B[k*ldb + c] + beta * C[r*ldc + c]
+constexpr int TM = 64, TK = 16;
+
+__global__ void __launch_bounds__(kThreads)
+k_gemm_tn(int m, int ncol, const double* __restrict__ A, int lda, const int32_t* __restrict__ a_off, int64_t a_stride,
+          const double* __restrict__ B, int ldb, const int32_t* __restrict__ b_off, int64_t b_stride,
+          const int32_t* __restrict__ kd, int kd_uniform, double* C, int ldc, int64_t c_stride,
+          double alpha, double beta, int tri) {
+    const int tr = blockIdx.y, tcn = blockIdx.x;
+    if (tri && tcn < tr) return;
+    const int bz = blockIdx.z;
+    const double* Ab = A + (a_off ? (int64_t)a_off[bz] : bz * a_stride);
+    const double* Bb = B + (b_off ? (int64_t)b_off[bz] : bz * b_stride);
+    double* Cb = C + bz * c_stride;
+    const int K = kd ? kd[bz] : kd_uniform;
+    const int r0 = tr * TM, c0 = tcn * TM;
+    __shared__ double As[2][TK][TM];
+    __shared__ double Bs[2][TK][TM];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    // each thread stages 4 elements of A and 4 of B per k-slab
+    double ra[4], rb[4];
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int idx = threadIdx.x + q * kThreads;
+            const int kk = idx / TM, rr = idx % TM;
+            const int k = k0 + kk;
+            ra[q] = (k < K && r0 + rr < m) ? Ab[(int64_t)k * lda + r0 + rr] : 0.0;
+            rb[q] = (k < K && c0 + rr < ncol) ? Bb[(int64_t)k * ldb + c0 + rr] : 0.0;
+        }
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int idx = threadIdx.x + q * kThreads;
+            As[buf][idx / TM][idx % TM] = ra[q];
+            Bs[buf][idx / TM][idx % TM] = rb[q];
+        }
+    };
+    int buf = 0;
+    if (K > 0) {
+        fetch(0);
+        stash(0);
+    }
+    __syncthreads();
+    for (int k0 = 0; k0 < K; k0 += TK) {
+        const bool more = k0 + TK < K;
+        if (more) fetch(k0 + TK);
+#pragma unroll
+        for (int kk = 0; kk < TK; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[buf][kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        if (more) stash(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = r0 + ty + 16 * i, cc = c0 + tx + 16 * j;
+            if (r < m && cc < ncol) {
+                double* p = Cb + (int64_t)r * ldc + cc;
+                double v = alpha * acc[i][j];
+                if (beta != 0.0) v += beta * (*p);
+                *p = v;
+            }
+        }
+}
+
+// ------------------------------------------------- shared-memory factorisations
+// In-place Cholesky of the symmetric n x n matrix held column-major in L
+// (L[j*ld + i] = A_ij); on exit the lower triangle holds the factor.  A pivot
+// that is not positive and finite sets *bad and is replaced by 1 so the sweep
+// still terminates deterministically.
+__device__ void chol_smem(double* L, int ld, int n, int* bad) {
+    for (int j = 0; j < n; ++j) {
+        if (threadIdx.x == 0) {
+            double d = L[j * ld + j];
+            if (!(d > 0.0) || !isfinite(d)) {
+                *bad = 1;
+                d = 1.0;
+            }
+            L[j * ld + j] = sqrt(d);
+        }
+        __syncthreads();
+        const double piv = L[j * ld + j];
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) L[j * ld + i] /= piv;
+        __syncthreads();
+        const int m = n - j - 1;
+        for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+            const int c = j + 1 + idx / m, r = j + 1 + idx % m;
+            if (r >= c) L[c * ld + r] -= L[j * ld + r] * L[j * ld + c];
+        }
+        __syncthreads();
+    }
+}
+
+// I = L^{-1} (both column-major, lower); one thread per column.
+__device__ void trinv_smem(const double* L, double* I, int ld, int n) {
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        for (int r = 0; r < c; ++r) I[c * ld + r] = 0.0;
+        for (int r = c; r < n; ++r) {
+            double s = (r == c) ? 1.0 : 0.0;
+            for (int k = c; k < r; ++k) s -= L[k * ld + r] * I[c * ld + k];
+            I[c * ld + r] = s / L[r * ld + r];
+        }
+    }
+    __syncthreads();
+}
+
+// Householder reduction of the symmetric n x n matrix S (row-major, full storage,
+// destroyed) to tridiagonal form: diagonal dv[0..n-1], off-diagonal ev[0..n-2].
+__device__ void tridiag_smem(double* S, int ld, int n, double* dv, double* ev, double* v, double* p, double* red) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int k = 0; k + 2 < n; ++k) {
+        double part = 0.0;
+        for (int i = k + 1 + tid; i < n; i += nt) {
+            const double x = S[i * ld + k];
+            part += x * x;
+        }
+        const double sigma = block_sum(part, red);
+        const double x0 = S[(k + 1) * ld + k];
+        if (sigma == 0.0) {
+            if (tid == 0) ev[k] = 0.0;
+            __syncthreads();
+            continue;
+        }
+        const double alpha = -copysign(sqrt(sigma), x0);
+        const double inv = 1.0 / sqrt(2.0 * (sigma - alpha * x0));
+        for (int i = k + 1 + tid; i < n; i += nt) v[i] = (i == k + 1 ? x0 - alpha : S[i * ld + k]) * inv;
+        __syncthreads();
+        for (int i = k + 1 + tid; i < n; i += nt) {
+            double s = 0.0;
+            for (int j = k + 1; j < n; ++j) s = fma(S[i * ld + j], v[j], s);
+            p[i] = s;
+        }
+        __syncthreads();
+        part = 0.0;
+        for (int i = k + 1 + tid; i < n; i += nt) part += v[i] * p[i];
+        const double kc = block_sum(part, red);
+        for (int i = k + 1 + tid; i < n; i += nt) p[i] = 2.0 * (p[i] - kc * v[i]);
+        __syncthreads();
+        const int m = n - k - 1;
+        for (int idx = tid; idx < m * m; idx += nt) {
+            const int i = k + 1 + idx / m, j = k + 1 + idx % m;
+            S[i * ld + j] -= v[i] * p[j] + p[i] * v[j];
+        }
+        if (tid == 0) ev[k] = alpha;
+        __syncthreads();
+    }
+    for (int i = tid; i < n; i += nt) dv[i] = S[i * ld + i];
+    if (tid == 0 && n >= 2) ev[n - 2] = S[(n - 1) * ld + (n - 2)];
+    __syncthreads();
+}
+
+// Smallest eigenvalue of the symmetric tridiagonal (dv, ev) by Sturm counts:
+// 32 lanes of one warp evaluate 32 interior points per round (multisection).
+// Bounded: at most 80 rounds.  Must be called by a whole warp.
+__device__ double sturm_min(const double* dv, const double* ev, int n) {
+    const int lane = threadIdx.x & 31;
+    if (n == 1) return dv[0];
+    double lo = INFINITY, hi = -INFINITY, e2max = 0.0;
+    for (int i = lane; i < n; i += 32) {
+        const double r = (i > 0 ? fabs(ev[i - 1]) : 0.0) + (i < n - 1 ? fabs(ev[i]) : 0.0);
+        lo = fmin(lo, dv[i] - r);
+        hi = fmax(hi, dv[i] + r);
+        if (i < n - 1) e2max = fmax(e2max, ev[i] * ev[i]);
+    }
+    lo = warp_min(lo);
+    hi = warp_max(hi);
+    e2max = warp_max(e2max);
+    const double pivmin = DBL_MIN * fmax(1.0, e2max);
+    const double sc = fmax(fabs(lo), fabs(hi));
+    lo -= 4.0 * DBL_EPSILON * sc + pivmin;
+    hi += 4.0 * DBL_EPSILON * sc + pivmin;
+    for (int it = 0; it < 80; ++it) {
+        if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 2.0 * pivmin) break;
+        const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+        int cnt = 0;
+        double q = dv[0] - x;
+        if (fabs(q) < pivmin) q = -pivmin;
+        cnt += q < 0.0;
+        for (int i = 1; i < n; ++i) {
+            q = dv[i] - x - ev[i - 1] * ev[i - 1] / q;
+            if (fabs(q) < pivmin) q = -pivmin;
+            cnt += q < 0.0;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, cnt >= 1);
+        const int j = bal ? __ffs(bal) - 1 : 31;
+        const double xj = __shfl_sync(0xffffffffu, x, j);
+        const double xjm = __shfl_sync(0xffffffffu, x, j > 0 ? j - 1 : 0);
+        if (bal == 0) {
+            lo = xj;
+        } else {
+            hi = xj;
+            if (j > 0) lo = xjm;
+        }
+    }
+    return 0.5 * (lo + hi);
+}
+
+// ------------------------------------------------------------ per-block kernels
+__global__ void __launch_bounds__(kThreads)
+k_block_chol_inv(int n, const double* __restrict__ Z, double* __restrict__ Y, int* flag) {
+    extern __shared__ double sm[];
+    const int ld = n + 1;
+    double* L = sm;
+    double* I = sm + (size_t)n * ld;
+    __shared__ int bad;
+    const int g = blockIdx.x;
+    const double* Zg = Z + (size_t)g * n * n;
+    if (threadIdx.x == 0) bad = 0;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int i = idx / n, j = idx % n;
+        L[j * ld + i] = Zg[idx];   // symmetric: column-major copy equals row-major copy
+    }
+    __syncthreads();
+    chol_smem(L, ld, n, &bad);
+    trinv_smem(L, I, ld, n);
+    double* Yg = Y + (size_t)g * n * n;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int i = idx / n, j = idx % n;
+        double s = 0.0;
+        for (int k = max(i, j); k < n; ++k) s = fma(I[i * ld + k], I[j * ld + k], s);
+        Yg[idx] = s;
+    }
+    if (threadIdx.x == 0 && bad) atomicOr(flag, (int)FL_CHOL_BLOCK);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_block_maxstep(int nb, int n, const double* __restrict__ X, const double* __restrict__ dX,
+                const double* __restrict__ Z, const double* __restrict__ dZ, double* tstep, int* flag) {
+    extern __shared__ double sm[];
+    const int ld = n + 1;
+    double* L = sm;
+    double* S = sm + (size_t)n * ld;
+    double* dv = S + (size_t)n * ld;
+    double* ev = dv + n;
+    double* v = ev + n;
+    double* p = v + n;
+    __shared__ double red[32];
+    __shared__ int bad;
+    const int g = blockIdx.x;
+    const size_t off = (size_t)(g % nb) * n * n;
+    const double* Mg = (g < nb ? X : Z) + off;
+    const double* Dg = (g < nb ? dX : dZ) + off;
+    if (threadIdx.x == 0) bad = 0;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int i = idx / n, j = idx % n;
+        L[j * ld + i] = Mg[idx];
+        S[i * ld + j] = Dg[idx];
+    }
+    __syncthreads();
+    chol_smem(L, ld, n, &bad);
+    // S <- L^{-1} S (forward substitution, one thread per column)
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        for (int i = 0; i < n; ++i) {
+            double s = S[i * ld + j];
+            for (int k = 0; k < i; ++k) s -= L[k * ld + i] * S[k * ld + j];
+            S[i * ld + j] = s / L[i * ld + i];
+        }
+    }
+    __syncthreads();
+    // S <- S L^{-T} (forward substitution along each row)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        for (int j = 0; j < n; ++j) {
+            double s = S[i * ld + j];
+            for (int k = 0; k < j; ++k) s -= L[k * ld + j] * S[i * ld + k];
+            S[i * ld + j] = s / L[j * ld + j];
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int i = idx / n, j = idx % n;
+        if (i < j) {
+            const double a = 0.5 * (S[i * ld + j] + S[j * ld + i]);
+            S[i * ld + j] = a;
+            S[j * ld + i] = a;
+        }
+    }
+    __syncthreads();
+    tridiag_smem(S, ld, n, dv, ev, v, p, red);
+    if (threadIdx.x < 32) {
+        const double lam = sturm_min(dv, ev, n);
+        if (threadIdx.x == 0) {
+            tstep[g] = (lam < 0.0) ? -1.0 / lam : 1e300;
+            if (bad) {
+                tstep[g] = 0.0;
+                atomicOr(flag, (int)FL_CHOL_BLOCK);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_block_mineig(int n, const double* __restrict__ M, double sign, double* out) {
+    extern __shared__ double sm[];
+    const int ld = n + 1;
+    double* S = sm;
+    double* dv = S + (size_t)n * ld;
+    double* ev = dv + n;
+    double* v = ev + n;
+    double* p = v + n;
+    __shared__ double red[32];
+    const int g = blockIdx.x;
+    const double* Mg = M + (size_t)g * n * n;
+    double part = 0.0;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int i = idx / n, j = idx % n;
+        const double a = sign * 0.5 * (Mg[idx] + Mg[(size_t)j * n + i]);
+        S[i * ld + j] = a;
+        part += a * a;
+    }
+    const double fro = sqrt(block_sum(part, red));
+    __syncthreads();
+    tridiag_smem(S, ld, n, dv, ev, v, p, red);
+    if (threadIdx.x < 32) {
+        const double lam = sturm_min(dv, ev, n);
+        if (threadIdx.x == 0) {
+            out[2 * g] = lam;
+            out[2 * g + 1] = fro;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- FP64 probe
+__global__ void k_fp64_probe(double* out, int iters, double seed) {
+    double a0 = seed + threadIdx.x, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3;
+    double a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6, a7 = a0 + 7;
+    const double b = 0.999999, c = 1e-7;
+    for (int i = 0; i < iters; ++i) {
+        a0 = fma(a0, b, c); a1 = fma(a1, b, c); a2 = fma(a2, b, c); a3 = fma(a3, b, c);
+        a4 = fma(a4, b, c); a5 = fma(a5, b, c); a6 = fma(a6, b, c); a7 = fma(a7, b, c);
+    }
+    const double s = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+    if (s == 123.456) out[0] = s;   // keeps the chain live
+}
+
+size_t smem_two_mats(int n) { return (size_t)2 * n * (n + 1) * sizeof(double); }
+
+}  // namespace
+
+// ===================================================================== launchers
+void launch_bgemm(cudaStream_t st, int n, int count, const double* A, const int32_t* ia, int sa, int ta,
+                  const double* B, const int32_t* ib, int sb, int tb, double* C, const int32_t* ic, int sc,
+                  int tc, double alpha, double beta) {
+    if (count <= 0) return;
+    const int tiles = (n + BG - 1) / BG;
+    dim3 grid(tiles * tiles, count < 65535 ? count : 65535);
+    k_bgemm<<<grid, kThreads, 0, st>>>(n, count, A, ia, sa, ta, B, ib, sb, tb, C, ic, sc, tc, alpha, beta);
+}
+
+void launch_gemm_tn(cudaStream_t st, int m, int ncol, int batch, const double* A, int lda, const int32_t* a_off,
+                    int64_t a_stride, const double* B, int ldb, const int32_t* b_off, int64_t b_stride,
+                    const int32_t* kd, int kd_uniform, double* C, int ldc, int64_t c_stride, double alpha,
+                    double beta, int tri) {
+    if (m <= 0 || ncol <= 0 || batch <= 0) return;
+    dim3 grid((ncol + TM - 1) / TM, (m + TM - 1) / TM, batch);
+    k_gemm_tn<<<grid, kThreads, 0, st>>>(m, ncol, A, lda, a_off, a_stride, B, ldb, b_off, b_stride, kd, kd_uniform,
+                                         C, ldc, c_stride, alpha, beta, tri);
+}
+
+void launch_block_chol_inv(cudaStream_t st, int nb, int n, const double* Z, double* Y, int* flag) {
+    const size_t sm = smem_two_mats(n);
+    k_block_chol_inv<<<nb, kThreads, sm, st>>>(n, Z, Y, flag);
+}
+
+void launch_block_maxstep(cudaStream_t st, int nb, int n, const double* X, const double* dX, const double* Z,
+                          const double* dZ, double* tstep, int* flag) {
+    const size_t sm = smem_two_mats(n) + (size_t)4 * n * sizeof(double);
+    k_block_maxstep<<<2 * nb, kThreads, sm, st>>>(nb, n, X, dX, Z, dZ, tstep, flag);
+}
+
+void launch_block_mineig(cudaStream_t st, int count, int n, const double* M, double sign, double* out) {
+    if (count <= 0) return;
+    const size_t sm = (size_t)n * (n + 1) * sizeof(double) + (size_t)4 * n * sizeof(double);
+    k_block_mineig<<<count, kThreads, sm, st>>>(n, M, sign, out);
+}
+
+double fp64_peak_probe(int device) {
+    cudaSetDevice(device);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    double* out = nullptr;
+    if (cudaMalloc(&out, sizeof(double)) != cudaSuccess) return -1.0;
+    const int iters = 4096, threads = 256, blocks = sms * 8;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    k_fp64_probe<<<blocks, threads>>>(out, 64, 1.0);   // warm-up
+    cudaEventRecord(a);
+    k_fp64_probe<<<blocks, threads>>>(out, iters, 1.0);
+    cudaEventRecord(b);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(out);
+    if (cudaGetLastError() != cudaSuccess || ms <= 0.f) return -1.0;
+    const double flops = 2.0 * 8.0 * (double)iters * threads * (double)blocks;
+    return flops / (ms * 1e-3) / 1e12;
+}
+
+void init_attrs_linalg(int smem_max) {
+    cudaFuncSetAttribute(k_block_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    cudaFuncSetAttribute(k_block_maxstep, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    cudaFuncSetAttribute(k_block_mineig, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+}

@@ -1,0 +1,195 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/polya_sdp.h"
+
+#define PSDP_MAX_N 112
+#define PSDP_MAX_L 16
+
+// Slots of the device scalar array ctx->d_scal.
+enum ScalarSlot {
+    SC_TRZX = 0,   // tr(ZX) at the current iterate
+    SC_MU = 1,     // sigma * tr(ZX) / n_X for the next corrector
+    SC_TP = 2,     // primal step of the last update
+    SC_TD = 3,     // dual step of the last update
+    SC_PHI = 4,    // tr(CX)
+    SC_PSI = 5,    // a^T y
+    SC_RELGAP = 6,
+    SC_PRES = 7,
+    SC_DRES = 8,
+    SC_TRX = 9,
+    SC_BXN = 10,   // ||B(X)||
+    SC_TPMAX = 11, // raw max steps before tau
+    SC_TDMAX = 12,
+    SC_COUNT = 16
+};
+
+// Bits of the device failure flag ctx->d_flag.
+enum FlagBits {
+    FL_CHOL_BLOCK = 1,
+    FL_CHOL_SCHUR = 2,
+    FL_NAN = 4,
+    FL_TIMEOUT = 8,
+};
+
+struct ProfSite {
+    int name_id;
+    cudaEvent_t a, b;
+};
+
+struct psdp_ctx {
+    // ----- sizes
+    int n, l, d_p, d1, d2, d_a;
+    int L0, L, M, Na, Nt, K, nblk, n2;
+    psdp_opts opt;
+    int device;
+    cudaStream_t stream;
+    bool own_stream;
+
+    // ----- host copies of the tables
+    std::vector<int32_t> beta;   // [L0][L]
+    std::vector<int32_t> cH;     // [L0][M][Na]
+    std::vector<double> cdiag;   // C_gamma = cdiag[gamma] * I  (all nblk blocks)
+
+    // ----- device tables and data
+    int32_t *d_beta = nullptr, *d_cH = nullptr;
+    int32_t *d_W0 = nullptr, *d_Wa = nullptr;   // monomial exponents [L0][l], [Na][l]
+    double *d_A = nullptr;                      // [Na][n][n]
+    double *d_H = nullptr;                      // [L0][M][n][n]
+    double *d_cdiag = nullptr;                  // [nblk]
+
+    // ----- iterate and per-block work arrays, each [nblk][n][n]
+    double *d_X = nullptr, *d_Z = nullptr, *d_G = nullptr, *d_Y = nullptr;
+    double *d_T1 = nullptr, *d_T2 = nullptr, *d_W = nullptr, *d_F = nullptr;
+    double *d_dXh = nullptr, *d_dZh = nullptr, *d_dX = nullptr, *d_dZ = nullptr;
+    double *d_S = nullptr;      // [M][Na][n][n]   B^T scratch
+    double *d_adj = nullptr;    // [L0][Na+1][n][n] adjoint scratch
+    double *d_adj2 = nullptr;   // [L0][Na][n][n]
+    double *d_y = nullptr, *d_dyh = nullptr, *d_dyb = nullptr, *d_rhs = nullptr, *d_BX = nullptr;
+    double *d_part = nullptr;   // per-block partial sums [2*nblk][4]
+    double *d_tstep = nullptr;  // per-block max steps [2*nblk]
+    double *d_scal = nullptr;   // [SC_COUNT]
+    double *d_info = nullptr;   // [PSDP_INFO_LEN]
+    int *d_flag = nullptr;
+    double *h_info = nullptr;   // pinned host mirror of d_info
+    int *h_flag = nullptr;
+
+    // ----- Schur complement
+    int npairs = 0, nterms = 0, nlyap_prod = 0;
+    std::vector<int> pair_a, pair_b, term_off, term_cnt;
+    int32_t *d_pair_a = nullptr, *d_pair_b = nullptr, *d_term_off = nullptr, *d_term_cnt = nullptr;
+    int32_t *d_term_desc = nullptr;   // [nterms][8] operand sources
+    double *d_term_w = nullptr;       // [nterms]
+    int32_t *d_uv_idx = nullptr;      // index arrays for U/V GEMMs [3][L0*M]
+    int32_t *d_prod_idx = nullptr;    // index arrays for pair products [3][nlyap_prod*2]
+    double *d_U = nullptr, *d_V = nullptr;   // [L0][M][n][n]
+    double *d_Aop = nullptr, *d_Bop = nullptr;  // [nterms][n][n]
+    double *d_Tbuf = nullptr;         // [pairs_per_chunk][n2][n2]
+    int pairs_per_chunk = 1;
+    double *d_Om = nullptr;           // [K][K] row-major, upper triangle authoritative
+    double *d_Linv = nullptr;         // diagonal-block inverses of the dense factor [npanel][nb][nb]
+    int nb_chol = 64;
+    double flops_schur = 0, flops_chol = 0, flops_schur_dense = 0;
+
+    // ----- misc
+    double *d_grid = nullptr; size_t grid_cap = 0;   // grid-check scratch
+    int32_t *d_svec = nullptr;        // (r, s) of each svec index [Nt][2]
+    double *d_cert = nullptr;         // certificate outputs [4]
+    int iters = 0;
+    int kernels_per_step = 0;   // kernel nodes in the captured Newton-step graph
+    bool have_graph = false;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaGraph_t graph = nullptr;
+
+    // ----- profiling
+    bool prof_on = false;
+    std::vector<std::string> prof_names;
+    std::vector<int64_t> prof_launches;
+    std::vector<double> prof_ms;
+    std::vector<ProfSite> prof_sites;     // sites recorded in the current step
+    std::vector<cudaEvent_t> prof_pool;   // reusable events
+    size_t prof_pool_used = 0;
+};
+
+// ------------------------------------------------------------- launchers
+// All launchers enqueue on `st` and never synchronise.
+
+// tables: beta [L0][L], cH [L0][M][Na], monomial lists; closed-form multinomials
+void launch_tables(cudaStream_t st, int l, int d_p, int d1, int d2, int d_a, int L0, int L, int M, int Na,
+                   int32_t* beta, int32_t* cH, int32_t* W0, int32_t* Wa);
+// H[h][g] = sum_lambda cH[h][g][lambda] A[lambda]
+void launch_hmat(cudaStream_t st, int L0, int M, int Na, int n, const int32_t* cH, const double* A, double* H);
+
+// batched n x n GEMM: C_e = alpha op(A_e) op(B_e) + beta C_e (or its transpose if tc);
+// matrix index of operand X for element e is (ix ? ix[e] : e * sx).
+void launch_bgemm(cudaStream_t st, int n, int count,
+                  const double* A, const int32_t* ia, int sa, int ta,
+                  const double* B, const int32_t* ib, int sb, int tb,
+                  double* C, const int32_t* ic, int sc, int tc, double alpha, double beta);
+
+// batched TN GEMM: C_b[r][c] = alpha * sum_{k<kd_b} A_b[k*lda + r] * B_b[k*ldb + c] + beta * C_b[r*ldc + c]
+// for r < m, c < ncol; per-batch offsets (elements) and contraction lengths from device arrays
+// (or uniform when the arrays are null).  tri: only tiles with tile_c >= tile_r.
+void launch_gemm_tn(cudaStream_t st, int m, int ncol, int batch,
+                    const double* A, int lda, const int32_t* a_off, int64_t a_stride,
+                    const double* B, int ldb, const int32_t* b_off, int64_t b_stride,
+                    const int32_t* kd, int kd_uniform,
+                    double* C, int ldc, int64_t c_stride, double alpha, double beta, int tri);
+
+// per-block Cholesky of Z and inverse Y = Z^{-1}; flag |= FL_CHOL_BLOCK on failure
+void launch_block_chol_inv(cudaStream_t st, int nb, int n, const double* Z, double* Y, int* flag);
+// per-block max step sup{t: M + t D >= 0} for (X,dX) blocks [0,nb) and (Z,dZ) blocks [nb,2nb)
+void launch_block_maxstep(cudaStream_t st, int nb, int n, const double* X, const double* dX,
+                          const double* Z, const double* dZ, double* tstep, int* flag);
+// per-matrix smallest eigenvalue of sign*M and Frobenius norm; out[2*i] = lambda_min, out[2*i+1] = ||M||
+void launch_block_mineig(cudaStream_t st, int count, int n, const double* M, double sign, double* out);
+
+// SDP operators
+void launch_bt(cudaStream_t st, psdp_ctx* c, const double* v, double* out_blocks);       // out = B^T(v)
+void launch_b(cudaStream_t st, psdp_ctx* c, const double* W, double* out, double acoef);  // out = B(W) - acoef*1
+
+// elementwise
+void launch_ew_G(cudaStream_t st, psdp_ctx* c, const double* BTy, const double* Z, double* G);
+void launch_ew_pred(cudaStream_t st, psdp_ctx* c, const double* G, const double* D, double* E, double* dZh);
+void launch_ew_symsub(cudaStream_t st, psdp_ctx* c, const double* T, const double* X, double* out);
+void launch_ew_muY(cudaStream_t st, psdp_ctx* c, const double* Y, const double* W2, const double* mu, double* F);
+void launch_ew_corr(cudaStream_t st, psdp_ctx* c, const double* F, const double* T, const double* dXh,
+                    const double* dZh, const double* dZb, double* dX, double* dZ);
+void launch_update(cudaStream_t st, psdp_ctx* c);
+void launch_identity(cudaStream_t st, int nb, int n, double* X);
+void launch_partials(cudaStream_t st, psdp_ctx* c);
+void launch_finalize(cudaStream_t st, psdp_ctx* c, int iter);  // iter unused on device
+void launch_steplen(cudaStream_t st, psdp_ctx* c);
+
+// Schur complement
+void launch_schur_operands(cudaStream_t st, psdp_ctx* c);
+void launch_schur_gather(cudaStream_t st, psdp_ctx* c, int p0, int np);
+
+// dense Cholesky (Omega stored row-major with the upper triangle, i.e. column-major lower)
+void launch_potrf_diag(cudaStream_t st, double* A, int K, int j0, int nb, double* Linv, int* flag);
+void dense_cholesky(cudaStream_t st, double* A, int K, int nb, double* Linv, int* flag);
+void dense_solve(cudaStream_t st, const double* A, int K, int nb, const double* Linv, double* partial, double* x);
+void launch_vec_copy(cudaStream_t st, int K, const double* a, double* out);
+void launch_cdiag(cudaStream_t st, psdp_ctx* c);
+
+// raise the dynamic shared-memory limit of the shared-memory-heavy kernels once,
+// outside any stream capture
+void init_attrs_linalg(int smem_max);
+void init_attrs_sdp(int smem_max);
+void init_attrs_dense(int smem_max);
+
+// certificate / grid
+void launch_certify_finalize(cudaStream_t st, int count, int n, const double* eig, int L, double* out);
+void launch_grid_build(cudaStream_t st, psdp_ctx* c, int N, int64_t first, int cnt, double* P, double* Aal);
+
+// FP64 throughput probe
+double fp64_peak_probe(int device);
+
+// errors
+#define CK(x) do { cudaError_t e__ = (x); if (e__ != cudaSuccess) return PSDP_ECUDA; } while (0)
