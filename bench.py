@@ -212,7 +212,7 @@ def run_ours(args):
             P = bd.psdp_get_P(s.h)
         t1 = time.perf_counter()
         e2e.append((t1 - t0, iters, status, verdict, P.nbytes))
-    best = min(e2e, key=lambda r: r[0])
+    best = min(e2e, key=lambda r: r[0]) if e2e else (float("nan"), 0, "skipped", -1, 0)
     bd.psdp_destroy(h)
     if rank != 0:
         if dist:
@@ -247,8 +247,9 @@ def run_ours(args):
             kern[name] = {"launches_per_step": prof[name][0] / args.steps, "avg_ms": prof[name][1] / prof[name][0],
                           "share_of_step": prof[name][1] / tot_ms}
     dom = max(("schur_gemm", "chol_syrk_gemm"), key=lambda k: kern.get(k, {}).get("share_of_step", 0))
-    roof = {"kernel": "k_gemm_tn (" + dom + ")", "bound": "fp64", "achieved": kern[dom]["tflops"],
-            "peak": fp64_peak, "unit": "TFLOP/s", "frac": kern[dom]["tflops"] / fp64_peak, "traffic": None,
+    ach = kern.get(dom, {}).get("tflops")
+    roof = {"kernel": "k_gemm_tn (" + dom + ")", "bound": "fp64", "achieved": ach,
+            "peak": fp64_peak, "unit": "TFLOP/s", "frac": (ach / fp64_peak) if ach else None, "traffic": None,
             "peak_source": f"{pk_kind} bf16 {pk['bf16_tflops']} TFLOP/s x nominal FP64/BF16 ratio 1.25/2250"}
     try:
         roof["fp64_probe_tflops"] = bd.psdp_fp64_peak(local)
@@ -257,7 +258,7 @@ def run_ours(args):
 
     # ---- CPU oracle baseline on a bounded sample
     ct = oracle_steps(A, w, args.cpu_steps)
-    cpu = {"value": len(ct) / sum(ct), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+    cpu = {"value": (len(ct) / sum(ct)) if ct else None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
            "sample": f"{len(ct)} oracle Newton steps of this workload from the cold start (numpy FP64)"}
 
     t_job, iters, status, verdict, pbytes = best
@@ -270,7 +271,7 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roof, "kernels": kern,
             "cpu_baseline": cpu,
-            "e2e": {"value": iters / t_job, "unit": UNIT, "h2d_bytes_per_step": A.nbytes / max(iters, 1),
+            "e2e": {"value": (iters / t_job) if iters else None, "unit": UNIT, "h2d_bytes_per_step": A.nbytes / max(iters, 1),
                     "d2h_bytes_per_step": (pbytes + 16 * 8 * iters) / max(iters, 1),
                     "time_to_certificate_s": t_job, "newton_steps": iters, "status": status, "verdict": verdict},
             "gpu_launches": int(work["kernels_per_step"]) * args.steps,

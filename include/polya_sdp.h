@@ -165,6 +165,16 @@ psdp_status psdp_work(const psdp_ctx* c, double* out5);
 /* The CUDA stream the context runs on (cudaStream_t as void*). */
 void* psdp_stream(psdp_ctx* c);
 
+/* Self-test of the library's tcgen05 tensor-core GEMM (no counterpart in the
+ * paper; it is the contraction engine of the mixed-precision path and the MLP).
+ * A: M x K, B: N x K, both row-major host arrays; C receives D = A B^T stored
+ * column-major (C[n*M + m] = D[m][n]), float32, M*N values.
+ * dtype 0: A, B float32, multiplied as TF32 (split 1) or as the 3xTF32 split
+ * hi*hi + hi*lo + lo*hi (split 3); dtype 1: A, B bfloat16 bit patterns (uint16),
+ * split must be 1.  Runs on the current device; allocates its own scratch.
+ * Errors: EINVAL on bad sizes/flags, ETIMEOUT if a bounded device wait expired. */
+psdp_status psdp_tc_gemm_check(int M, int N, int K, int dtype, int split, const void* A, const void* B, float* C);
+
 /* Measure this GPU's FP64 FMA throughput with a short dependent-chain kernel;
  * *tflops receives FP64 TFLOP/s (2 flops per FMA). */
 psdp_status psdp_fp64_peak(int device, double* tflops);

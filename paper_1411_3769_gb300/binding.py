@@ -28,7 +28,7 @@ EXPORTS = ("psdp_default_opts", "psdp_setup", "psdp_sizes", "psdp_step", "psdp_s
            "psdp_grid_check", "psdp_get_P", "psdp_get_y", "psdp_get_tables", "psdp_load_iterate",
            "psdp_get_iterate", "psdp_get_schur", "psdp_apply_BT", "psdp_apply_B", "psdp_profile_enable",
            "psdp_profile_reset", "psdp_profile_get", "psdp_work", "psdp_stream", "psdp_fp64_peak",
-           "psdp_destroy", "psdp_strerror")
+           "psdp_destroy", "psdp_strerror", "psdp_tc_gemm_check")
 
 
 class Opts(C.Structure):
@@ -80,6 +80,7 @@ def _lib():
             "psdp_fp64_peak": (C.c_int, [C.c_int, dp]),
             "psdp_destroy": (None, [vp]),
             "psdp_strerror": (C.c_char_p, [C.c_int]),
+            "psdp_tc_gemm_check": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -248,6 +249,19 @@ def psdp_fp64_peak(device: int = 0) -> float:
     v = np.zeros(1)
     _check(_lib().psdp_fp64_peak(device, _dp(v)), "psdp_fp64_peak")
     return float(v[0])
+
+
+def psdp_tc_gemm_check(A: np.ndarray, B: np.ndarray, split: int = 1) -> np.ndarray:
+    """D = A B^T on the tensor cores; A, B float32 (TF32 / 3xTF32) or uint16 BF16 bit patterns."""
+    dtype = 1 if A.dtype == np.uint16 else 0
+    A = np.ascontiguousarray(A)
+    B = np.ascontiguousarray(B)
+    M, K = A.shape
+    N = B.shape[0]
+    C_ = np.zeros((N, M), dtype=np.float32)
+    _check(_lib().psdp_tc_gemm_check(M, N, K, dtype, split, A.ctypes.data, B.ctypes.data, C_.ctypes.data),
+           "psdp_tc_gemm_check")
+    return C_.T
 
 
 def psdp_destroy(h):

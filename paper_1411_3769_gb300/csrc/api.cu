@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -50,20 +51,31 @@ int prof_name_id(psdp_ctx* c, const char* name) {
     return (int)c->prof_names.size() - 1;
 }
 
+// Inside a stream capture an event record must be an external node to be
+// timeable after each replay of the graph.
+void record_event(psdp_ctx* c, cudaEvent_t e) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(c->stream, &cs);
+    if (cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, c->stream);
+}
+
 int prof_begin(psdp_ctx* c, const char* name) {
     if (!c->prof_on || c->prof_pool_used + 2 > c->prof_pool.size()) return -1;
     ProfSite s;
     s.name_id = prof_name_id(c, name);
     s.a = c->prof_pool[c->prof_pool_used++];
     s.b = c->prof_pool[c->prof_pool_used++];
-    cudaEventRecord(s.a, c->stream);
+    record_event(c, s.a);
     c->prof_sites.push_back(s);
     return (int)c->prof_sites.size() - 1;
 }
 
 void prof_end(psdp_ctx* c, int site) {
     if (site < 0) return;
-    cudaEventRecord(c->prof_sites[site].b, c->stream);
+    record_event(c, c->prof_sites[site].b);
 }
 
 void prof_collect(psdp_ctx* c) {
@@ -198,11 +210,17 @@ void enqueue_step(psdp_ctx* c) {
     cudaMemcpyAsync(c->h_flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
 }
 
+psdp_status cuda_fail(cudaError_t e, const char* where) {
+    static const bool dbg = getenv("PSDP_DEBUG") != nullptr;
+    if (dbg) fprintf(stderr, "[psdp] %s: %s (%s)\n", where, cudaGetErrorName(e), cudaGetErrorString(e));
+    return PSDP_ECUDA;
+}
+
 psdp_status sync_check(psdp_ctx* c) {
     cudaError_t e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return PSDP_ECUDA;
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
     e = cudaGetLastError();
-    if (e != cudaSuccess) return PSDP_ECUDA;
+    if (e != cudaSuccess) return cuda_fail(e, "launch");
     return PSDP_OK;
 }
 
@@ -350,6 +368,7 @@ psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psd
     init_attrs_linalg(smem_max);
     init_attrs_sdp(smem_max);
     init_attrs_dense(smem_max);
+    cudaGetLastError();
 
     psdp_ctx* c = new (std::nothrow) psdp_ctx();
     if (!c) return PSDP_ENOMEM;

@@ -193,5 +193,5 @@ void launch_vec_copy(cudaStream_t st, int K, const double* a, double* out) {
 }
 
 void init_attrs_dense(int smem_max) {
-    cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    set_max_dynamic_smem((const void*)k_potrf_diag, smem_max);
 }

@@ -519,7 +519,7 @@ double fp64_peak_probe(int device) {
 }
 
 void init_attrs_linalg(int smem_max) {
-    cudaFuncSetAttribute(k_block_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
-    cudaFuncSetAttribute(k_block_maxstep, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
-    cudaFuncSetAttribute(k_block_mineig, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    set_max_dynamic_smem((const void*)k_block_chol_inv, smem_max);
+    set_max_dynamic_smem((const void*)k_block_maxstep, smem_max);
+    set_max_dynamic_smem((const void*)k_block_mineig, smem_max);
 }

@@ -655,5 +655,5 @@ void launch_grid_build(cudaStream_t st, psdp_ctx* c, int N, int64_t first, int c
 }
 
 void init_attrs_sdp(int smem_max) {
-    cudaFuncSetAttribute(k_schur_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    set_max_dynamic_smem((const void*)k_schur_gather, smem_max);
 }

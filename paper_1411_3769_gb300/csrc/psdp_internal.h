@@ -193,3 +193,12 @@ double fp64_peak_probe(int device);
 
 // errors
 #define CK(x) do { cudaError_t e__ = (x); if (e__ != cudaSuccess) return PSDP_ECUDA; } while (0)
+
+// Allow `f` the largest dynamic shared memory the device permits next to its
+// static shared memory; clears the error state either way.
+inline void set_max_dynamic_smem(const void* f, int smem_optin) {
+    cudaFuncAttributes a;
+    if (cudaFuncGetAttributes(&a, f) == cudaSuccess)
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin - (int)a.sharedSizeBytes);
+    cudaGetLastError();
+}

@@ -157,7 +157,7 @@ def test_tiny_solve_verdicts(bd, name, seed):
         assert abs(minP - cert_y["minP_margin"]) <= 1e-9 * (1 + abs(cert_y["minP_margin"]))
         assert abs(maxL - cert_y["maxLyap_margin"]) <= 1e-9 * (1 + abs(cert_y["maxLyap_margin"]))
     assert verdict == cert_o["verdict"]
-    assert status == st_o
+    assert status.removeprefix("E") == st_o
     if status == "OK":
         assert info["relgap"] <= 1e-7 and abs(iters - state.it) <= 2
 
