@@ -141,6 +141,13 @@ psdp_status psdp_get_iterate(psdp_ctx* c, double* X, double* Z, double* y);
  * authoritative; FP64 in both precision modes).  Test and inspection hook. */
 psdp_status psdp_get_schur(psdp_ctx* c, double* Omega);
 
+/* The same Omega as computed by the mixed-precision path (PSDP_MIXED contexts only,
+ * else ESTATE): operands rounded to FP32 and contracted on the tensor cores in
+ * 3xTF32 with FP32 accumulation; K x K float32, full (upper triangle computed,
+ * lower mirrored on the host).  Its error against psdp_get_schur is the stated
+ * error of the mixed path's Schur complement. */
+psdp_status psdp_get_schur_mixed(psdp_ctx* c, float* Omega);
+
 /* Operator hooks for parity tests: out_blocks = B^T(v) (Eq. AT) and
  * out = B(W) = (tr(B_i W))_i for block-diagonal W ((L+M)*n*n doubles). */
 psdp_status psdp_apply_BT(psdp_ctx* c, const double* v, double* out_blocks);

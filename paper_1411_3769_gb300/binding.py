@@ -28,7 +28,7 @@ EXPORTS = ("psdp_default_opts", "psdp_setup", "psdp_sizes", "psdp_step", "psdp_s
            "psdp_grid_check", "psdp_get_P", "psdp_get_y", "psdp_get_tables", "psdp_load_iterate",
            "psdp_get_iterate", "psdp_get_schur", "psdp_apply_BT", "psdp_apply_B", "psdp_profile_enable",
            "psdp_profile_reset", "psdp_profile_get", "psdp_work", "psdp_stream", "psdp_fp64_peak",
-           "psdp_destroy", "psdp_strerror", "psdp_tc_gemm_check")
+           "psdp_destroy", "psdp_strerror", "psdp_tc_gemm_check", "psdp_get_schur_mixed")
 
 
 class Opts(C.Structure):
@@ -81,6 +81,7 @@ def _lib():
             "psdp_destroy": (None, [vp]),
             "psdp_strerror": (C.c_char_p, [C.c_int]),
             "psdp_tc_gemm_check": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp]),
+            "psdp_get_schur_mixed": (C.c_int, [vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -193,6 +194,13 @@ def psdp_get_schur(h) -> np.ndarray:
     K = psdp_sizes(h)["K"]
     Om = np.zeros((K, K))
     _check(_lib().psdp_get_schur(h, _dp(Om)), "psdp_get_schur")
+    return Om
+
+
+def psdp_get_schur_mixed(h) -> np.ndarray:
+    K = psdp_sizes(h)["K"]
+    Om = np.zeros((K, K), dtype=np.float32)
+    _check(_lib().psdp_get_schur_mixed(h, Om.ctypes.data), "psdp_get_schur_mixed")
     return Om
 
 

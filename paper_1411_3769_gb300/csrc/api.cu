@@ -63,24 +63,24 @@ void record_event(psdp_ctx* c, cudaEvent_t e) {
 }
 
 int prof_begin(psdp_ctx* c, const char* name) {
-    if (!c->prof_on || c->prof_pool_used + 2 > c->prof_pool.size()) return -1;
+    if (!c->prof_on || !c->prof_cur || c->prof_pool_used + 2 > c->prof_pool_limit) return -1;
     ProfSite s;
     s.name_id = prof_name_id(c, name);
     s.a = c->prof_pool[c->prof_pool_used++];
     s.b = c->prof_pool[c->prof_pool_used++];
     record_event(c, s.a);
-    c->prof_sites.push_back(s);
-    return (int)c->prof_sites.size() - 1;
+    c->prof_cur->push_back(s);
+    return (int)c->prof_cur->size() - 1;
 }
 
 void prof_end(psdp_ctx* c, int site) {
     if (site < 0) return;
-    record_event(c, c->prof_sites[site].b);
+    record_event(c, (*c->prof_cur)[site].b);
 }
 
-void prof_collect(psdp_ctx* c) {
+void prof_collect(psdp_ctx* c, bool mixed) {
     if (!c->prof_on) return;
-    for (const ProfSite& s : c->prof_sites) {
+    for (const ProfSite& s : (mixed ? c->prof_sites32 : c->prof_sites)) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, s.a, s.b) == cudaSuccess) {
             c->prof_ms[s.name_id] += ms;
@@ -151,6 +151,96 @@ void enqueue_cholesky(psdp_ctx* c) {
     }
 }
 
+// ----------------------------------------------------------- mixed precision
+// Omega in FP32 from the 3xTF32 tensor-core contraction: operands packed K-major
+// (Phi^T as the M side, Psi as the N side), T' = sum_t Psi_t (x) Phi_t^T per pair
+// in FP32, then the same sub-block gather as the FP64 path.
+void enqueue_schur_mixed(psdp_ctx* c) {
+    cudaStream_t st = c->stream;
+    const int n = c->n, n2 = c->n2, LM = c->L0 * c->M;
+    const int64_t Loff = (int64_t)c->L * n2;
+    {
+        ProfScope p(c, "schur_operands");
+        launch_bgemm(st, n, LM, c->d_Y + Loff, c->d_uv_idx, 0, 0, c->d_H, nullptr, 1, 1, c->d_U, nullptr, 1, 0, 1.0, 0.0);
+        launch_bgemm(st, n, LM, c->d_X + Loff, c->d_uv_idx, 0, 0, c->d_H, nullptr, 1, 1, c->d_V, nullptr, 1, 0, 1.0, 0.0);
+        const int np = c->nlyap_prod;
+        if (np > 0) {
+            const int32_t* ix = c->d_prod_idx;
+            launch_bgemm(st, n, np, c->d_H, ix, 0, 0, c->d_V, ix + np, 0, 0, c->d_prodB, nullptr, 1, 0, 1.0, 0.0);
+            launch_bgemm(st, n, np, c->d_H, ix + 3 * np, 0, 0, c->d_U, ix + 4 * np, 0, 0, c->d_prodA, nullptr, 1, 0,
+                         1.0, 0.0);
+        }
+        launch_schur_pack32(st, c);
+    }
+    for (int p0 = 0; p0 < c->npairs; p0 += c->pairs_per_chunk32) {
+        const int np = std::min(c->pairs_per_chunk32, c->npairs - p0);
+        {
+            ProfScope p(c, "schur_tc_gemm");
+            launch_tc_gemm(st, false, 3, c->map_opB_hi, c->map_opA_hi, &c->map_opB_lo, &c->map_opA_lo, n2, n2, np, p0,
+                           c->d_term_cnt + p0, 0, c->d_T32, n2, (int64_t)n2 * n2, 1.f, 0.f, 0, c->d_flag);
+        }
+        {
+            ProfScope p(c, "schur_gather");
+            launch_schur_gather32(st, c, p0, np, c->d_T32, c->d_Om32);
+        }
+    }
+}
+
+// FP32 Cholesky of Omega32: diagonal blocks in FP64 arithmetic, panel TRSM on
+// CUDA cores, trailing update as a 3xTF32 tensor-core SYRK.
+void enqueue_cholesky_mixed(psdp_ctx* c) {
+    cudaStream_t st = c->stream;
+    const int K = c->K, nb = c->nb32;
+    float* A = c->d_Om32;
+    for (int j0 = 0, p = 0; j0 < K; j0 += nb, ++p) {
+        const int w = std::min(nb, K - j0);
+        float* Lp = c->d_Linv32 + (size_t)p * nb * nb;
+        {
+            ProfScope q(c, "chol32_potrf_diag");
+            launch_potrf_diag32(st, A, K, j0, nb, Lp, c->d_flag);
+        }
+        const int rest = K - j0 - w;
+        if (rest <= 0) break;
+        {
+            ProfScope q(c, "chol32_trsm");
+            launch_trsm32_pack(st, A, K, j0, nb, Lp, c->d_Pt_hi, c->d_Pt_lo);
+        }
+        CUtensorMap hi, lo;
+        if (!tc_make_map(&hi, c->d_Pt_hi, false, w, rest, 1, nb, 0, 128) ||
+            !tc_make_map(&lo, c->d_Pt_lo, false, w, rest, 1, nb, 0, 128))
+            continue;
+        {
+            ProfScope q(c, "chol32_syrk_tc");
+            launch_tc_gemm(st, false, 3, hi, hi, &lo, &lo, rest, rest, 1, 0, nullptr, w,
+                           A + (int64_t)(j0 + w) * K + j0 + w, K, 0, -1.f, 1.f, 1, c->d_flag);
+        }
+    }
+}
+
+// x <- Omega^{-1} b by conjugate gradients in FP64 with the matrix-free product
+// Omega v = B(Z^{-1} B^T(v) X) and the FP32 factor as preconditioner; the
+// iterations after convergence are skipped on the device.
+void enqueue_pcg(psdp_ctx* c, double* b) {
+    cudaStream_t st = c->stream;
+    const int K = c->K, n = c->n, nb = c->nblk;
+    const int* done = c->d_pcg_done;
+    ProfScope p(c, "pcg_solve");
+    launch_pcg_init(st, K, b, c->d_pcg_x, c->d_pcg_r, c->d_pcg_state, c->d_pcg_done);
+    launch_precond32(st, c->d_Om32, K, c->nb32, c->d_Linv32, c->d_z32, c->d_part32, c->d_pcg_r, c->d_pcg_z, done);
+    launch_pcg_start(st, K, c->d_pcg_r, c->d_pcg_z, c->d_pcg_p, c->d_pcg_state, done);
+    for (int it = 0; it < c->pcg_max; ++it) {
+        launch_bt(st, c, c->d_pcg_p, c->d_M1, done);
+        launch_bgemm(st, n, nb, c->d_Y, nullptr, 1, 0, c->d_M1, nullptr, 1, 0, c->d_M2, nullptr, 1, 0, 1.0, 0.0, done);
+        launch_bgemm(st, n, nb, c->d_M2, nullptr, 1, 0, c->d_X, nullptr, 1, 0, c->d_M1, nullptr, 1, 0, 1.0, 0.0, done);
+        launch_b(st, c, c->d_M1, c->d_pcg_q, 0.0, done);
+        launch_pcg_alpha(st, K, c->d_pcg_p, c->d_pcg_q, c->d_pcg_x, c->d_pcg_r, c->d_pcg_state, c->d_pcg_done,
+                         c->pcg_tol);
+        launch_precond32(st, c->d_Om32, K, c->nb32, c->d_Linv32, c->d_z32, c->d_part32, c->d_pcg_r, c->d_pcg_z, done);
+        launch_pcg_beta(st, K, c->d_pcg_r, c->d_pcg_z, c->d_pcg_p, c->d_pcg_state, done);
+    }
+    launch_pcg_finish(st, K, c->d_pcg_x, b, c->d_pcg_state, done, c->d_flag, c->pcg_fail, c->d_info + 12);
+}
+
 void enqueue_refresh(psdp_ctx* c) {
     cudaStream_t st = c->stream;
     launch_bt(st, c, c->d_y, c->d_T1);
@@ -160,22 +250,35 @@ void enqueue_refresh(psdp_ctx* c) {
     launch_finalize(st, c, 0);
 }
 
-void enqueue_step(psdp_ctx* c) {
+// One predictor-corrector step.  mixed: Schur complement and its Cholesky in
+// 3xTF32/FP32 on the tensor cores, both Newton systems solved by FP64 PCG;
+// otherwise everything in FP64 with direct solves.
+void enqueue_step(psdp_ctx* c, bool mixed) {
     cudaStream_t st = c->stream;
     const int n = c->n, nb = c->nblk;
-    c->prof_sites.clear();
-    c->prof_pool_used = 0;
+    // each step graph owns half of the profiling event pool and its own site list
+    c->prof_cur = mixed ? &c->prof_sites32 : &c->prof_sites;
+    c->prof_cur->clear();
+    c->prof_pool_used = mixed ? c->prof_pool.size() / 2 : 0;
+    c->prof_pool_limit = mixed ? c->prof_pool.size() : c->prof_pool.size() / 2;
+    cudaMemsetAsync(c->d_info + 12, 0, 2 * sizeof(double), st);
     {
         ProfScope p(c, "block_chol_inv");
         launch_block_chol_inv(st, nb, n, c->d_Z, c->d_Y, c->d_flag);
     }
-    enqueue_schur(c);
+    if (mixed)
+        enqueue_schur_mixed(c);
+    else
+        enqueue_schur(c);
     // predictor right-hand side: B(Y G X) - a
     launch_bgemm(st, n, nb, c->d_Y, nullptr, 1, 0, c->d_G, nullptr, 1, 0, c->d_T1, nullptr, 1, 0, 1.0, 0.0);
     launch_bgemm(st, n, nb, c->d_T1, nullptr, 1, 0, c->d_X, nullptr, 1, 0, c->d_W, nullptr, 1, 0, 1.0, 0.0);
     launch_b(st, c, c->d_W, c->d_dyh, 1.0);
-    enqueue_cholesky(c);
-    {
+    if (mixed) {
+        enqueue_cholesky_mixed(c);
+        enqueue_pcg(c, c->d_dyh);
+    } else {
+        enqueue_cholesky(c);
         ProfScope p(c, "dense_solve");
         dense_solve(st, c->d_Om, c->K, c->nb_chol, c->d_Linv, c->d_rhs, c->d_dyh);
     }
@@ -190,7 +293,9 @@ void enqueue_step(psdp_ctx* c) {
     launch_bgemm(st, n, nb, c->d_T1, nullptr, 1, 0, c->d_dXh, nullptr, 1, 0, c->d_W, nullptr, 1, 0, 1.0, 0.0);
     launch_ew_muY(st, c, c->d_Y, c->d_W, c->d_scal + SC_MU, c->d_F);
     launch_b(st, c, c->d_F, c->d_dyb, 0.0);
-    {
+    if (mixed) {
+        enqueue_pcg(c, c->d_dyb);
+    } else {
         ProfScope p(c, "dense_solve");
         dense_solve(st, c->d_Om, c->K, c->nb_chol, c->d_Linv, c->d_rhs, c->d_dyb);
     }
@@ -236,12 +341,17 @@ void free_ctx(psdp_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->graph) cudaGraphDestroy(c->graph);
+    if (c->graph_exec32) cudaGraphExecDestroy(c->graph_exec32);
+    if (c->graph32) cudaGraphDestroy(c->graph32);
     void* ptrs[] = {c->d_beta, c->d_cH, c->d_W0, c->d_Wa, c->d_A, c->d_H, c->d_cdiag, c->d_X, c->d_Z, c->d_G,
                     c->d_Y, c->d_T1, c->d_T2, c->d_W, c->d_F, c->d_dXh, c->d_dZh, c->d_dX, c->d_dZ, c->d_S,
                     c->d_adj, c->d_adj2, c->d_y, c->d_dyh, c->d_dyb, c->d_rhs, c->d_BX, c->d_part, c->d_tstep,
                     c->d_scal, c->d_info, c->d_flag, c->d_pair_a, c->d_pair_b, c->d_term_off, c->d_term_cnt,
                     c->d_term_desc, c->d_term_w, c->d_uv_idx, c->d_prod_idx, c->d_U, c->d_V, c->d_Aop, c->d_Bop,
-                    c->d_Tbuf, c->d_Om, c->d_Linv, c->d_grid, c->d_svec, c->d_cert};
+                    c->d_Tbuf, c->d_Om, c->d_Linv, c->d_grid, c->d_svec, c->d_cert, c->d_term_off_t,
+                    c->d_opA_hi, c->d_opA_lo, c->d_opB_hi, c->d_opB_lo, c->d_prodA, c->d_prodB, c->d_T32,
+                    c->d_Om32, c->d_Linv32, c->d_Pt_hi, c->d_Pt_lo, c->d_z32, c->d_part32, c->d_pcg_x, c->d_pcg_r,
+                    c->d_pcg_z, c->d_pcg_p, c->d_pcg_q, c->d_pcg_state, c->d_pcg_done, c->d_M1, c->d_M2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_info) cudaFreeHost(c->h_info);
@@ -285,9 +395,10 @@ psdp_status build_schur_lists(psdp_ctx* c) {
             for (int g = 0; g < M; ++g) {
                 if (!hz[(size_t)a * M + g] || !hz[(size_t)b * M + g]) continue;
                 const int blk = L + g, ia = a * M + g, ib = b * M + g;
+                const int j = (int)prod_a2.size();                  // index of this (pair, block) product
                 const int32_t d1[8] = {3, ib, 0, 4, ia, 1, 0, 0};   // (Y H_b^T, (X H_a^T)^T)
-                const int32_t d2[8] = {1, blk, 0, 0, 0, 0, 0, 0};   // (Y, H_a X H_b^T)
-                const int32_t d3[8] = {0, 0, 0, 2, blk, 0, 0, 0};   // (H_a Y H_b^T, X)
+                const int32_t d2[8] = {1, blk, 0, 0, 0, 0, 0, j};   // (Y, H_a X H_b^T)
+                const int32_t d3[8] = {0, 0, 0, 2, blk, 0, j, 0};   // (H_a Y H_b^T, X)
                 const int32_t d4[8] = {3, ia, 1, 4, ib, 0, 0, 0};   // ((Y H_a^T)^T, X H_b^T)
                 desc.insert(desc.end(), d1, d1 + 8);
                 desc.insert(desc.end(), d2, d2 + 8);
@@ -335,13 +446,67 @@ psdp_status build_schur_lists(psdp_ctx* c) {
     cudaMemcpy(c->d_uv_idx, uv.data(), uv.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     TRY(dalloc(&c->d_U, (size_t)L0 * M * c->n2));
     TRY(dalloc(&c->d_V, (size_t)L0 * M * c->n2));
-    TRY(dalloc(&c->d_Aop, (size_t)std::max(1, t) * c->n2));
-    TRY(dalloc(&c->d_Bop, (size_t)std::max(1, t) * c->n2));
+    std::vector<int32_t> toff_t(c->term_off.begin(), c->term_off.end());
+    TRY(dalloc(&c->d_term_off_t, c->npairs));
+    cudaMemcpy(c->d_term_off_t, toff_t.data(), c->npairs * sizeof(int32_t), cudaMemcpyHostToDevice);
+    int tmax = 1;
+    for (int p = 0; p < c->npairs; ++p) tmax = std::max(tmax, c->term_cnt[p]);
+    c->tpad = (tmax + 31) / 32 * 32;
+    return PSDP_OK;
+}
+
+// Buffers of the FP64 Schur contraction and Cholesky (allocated at set-up in
+// FP64 mode, on first need in mixed mode).
+psdp_status alloc_fp64(psdp_ctx* c) {
+    if (c->have_fp64) return PSDP_OK;
+    const int t = std::max(1, c->nterms);
+    TRY(dalloc(&c->d_Aop, (size_t)t * c->n2));
+    TRY(dalloc(&c->d_Bop, (size_t)t * c->n2));
     // contraction output: as many pairs per launch as fit in ~2 GiB
     const size_t per_pair = (size_t)c->n2 * c->n2 * sizeof(double);
     c->pairs_per_chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)c->npairs, ((size_t)2 << 30) / per_pair));
     TRY(dalloc(&c->d_Tbuf, (size_t)c->pairs_per_chunk * c->n2 * c->n2));
+    const int nbc = c->nb_chol;
+    const int npanel = (c->K + nbc - 1) / nbc;
+    TRY(dalloc(&c->d_Om, (size_t)c->K * c->K));
+    TRY(dalloc(&c->d_Linv, (size_t)npanel * nbc * nbc));
+    c->have_fp64 = true;
     return PSDP_OK;
+}
+
+// Buffers of the mixed-precision step and the Schur operand tensor maps.
+psdp_status alloc_mixed(psdp_ctx* c) {
+    const size_t K = c->K, n2 = c->n2, np = std::max(1, c->nlyap_prod);
+    const size_t opsz = (size_t)c->npairs * n2 * c->tpad;
+    float** ops[] = {&c->d_opA_hi, &c->d_opA_lo, &c->d_opB_hi, &c->d_opB_lo};
+    for (float** p : ops) {
+        TRY(dalloc(p, opsz));
+        cudaMemset(*p, 0, opsz * sizeof(float));   // padding terms stay zero
+    }
+    TRY(dalloc(&c->d_prodA, np * n2));
+    TRY(dalloc(&c->d_prodB, np * n2));
+    const size_t per_pair = n2 * n2 * sizeof(float);
+    c->pairs_per_chunk32 = (int)std::max<size_t>(1, std::min<size_t>((size_t)c->npairs, ((size_t)2 << 30) / per_pair));
+    TRY(dalloc(&c->d_T32, (size_t)c->pairs_per_chunk32 * n2 * n2));
+    const int nb = c->nb32, npanel = (c->K + nb - 1) / nb;
+    TRY(dalloc(&c->d_Om32, K * K));
+    TRY(dalloc(&c->d_Linv32, (size_t)npanel * nb * nb));
+    TRY(dalloc(&c->d_Pt_hi, K * nb));
+    TRY(dalloc(&c->d_Pt_lo, K * nb));
+    TRY(dalloc(&c->d_z32, K));
+    TRY(dalloc(&c->d_part32, (size_t)nb * (K / 2048 + 2)));
+    double** vecs[] = {&c->d_pcg_x, &c->d_pcg_r, &c->d_pcg_z, &c->d_pcg_p, &c->d_pcg_q};
+    for (double** p : vecs) TRY(dalloc(p, K));
+    TRY(dalloc(&c->d_pcg_state, 8));
+    TRY(dalloc(&c->d_pcg_done, 1));
+    TRY(dalloc(&c->d_M1, (size_t)c->nblk * n2));
+    TRY(dalloc(&c->d_M2, (size_t)c->nblk * n2));
+    // operands: element (t, e, pair) at pair*n2*tpad + e*tpad + t
+    const bool ok = tc_make_map(&c->map_opA_hi, c->d_opA_hi, false, c->tpad, n2, c->npairs, c->tpad, n2 * c->tpad, 128) &&
+                    tc_make_map(&c->map_opA_lo, c->d_opA_lo, false, c->tpad, n2, c->npairs, c->tpad, n2 * c->tpad, 128) &&
+                    tc_make_map(&c->map_opB_hi, c->d_opB_hi, false, c->tpad, n2, c->npairs, c->tpad, n2 * c->tpad, 128) &&
+                    tc_make_map(&c->map_opB_lo, c->d_opB_lo, false, c->tpad, n2, c->npairs, c->tpad, n2 * c->tpad, 128);
+    return ok ? PSDP_OK : PSDP_ECUDA;
 }
 
 psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psdp_opts* o, psdp_ctx** out) {
@@ -354,7 +519,8 @@ psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psd
         d_p > 12 || d1 > 12 || d2 > 12 || d_a > 12 || !A)
         return PSDP_EINVAL;
     if (!(opt.tau > 0 && opt.tau < 1) || !(opt.sigma >= 0 && opt.sigma < 1) || !(opt.eps > 0) || opt.max_iter < 1 ||
-        !std::isfinite(opt.delta) || !std::isfinite(opt.delta_L))
+        !std::isfinite(opt.delta) || !std::isfinite(opt.delta_L) ||
+        (opt.precision != PSDP_FP64 && opt.precision != PSDP_MIXED))
         return PSDP_EINVAL;
     const int64_t Na = hcard(l, d_a), L0 = hcard(l, d_p), L = hcard(l, d_p + d1), M = hcard(l, d_p + d_a + d2);
     const int64_t Nt = (int64_t)n * (n + 1) / 2, K = L0 * Nt;
@@ -368,6 +534,8 @@ psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psd
     init_attrs_linalg(smem_max);
     init_attrs_sdp(smem_max);
     init_attrs_dense(smem_max);
+    init_attrs_tc(smem_max);
+    init_attrs_mixed(smem_max);
     cudaGetLastError();
 
     psdp_ctx* c = new (std::nothrow) psdp_ctx();
@@ -377,6 +545,7 @@ psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psd
     c->nblk = (int)(L + M); c->n2 = n * n;
     c->opt = opt;
     c->device = opt.device;
+    c->mixed = opt.precision == PSDP_MIXED;
     c->flops_chol = (double)K * K * K / 3.0;
     if (opt.stream) {
         c->stream = (cudaStream_t)opt.stream;
@@ -401,7 +570,6 @@ psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psd
         (s = dalloc(&c->d_adj2, (size_t)L0 * Na * c->n2)))
         return fail(s);
     const int nbc = c->nb_chol;
-    const int npanel = (int)((K + nbc - 1) / nbc);
     const size_t rhs_len = std::max<size_t>(K, (size_t)nbc * (K / 2048 + 2));
     double** vecs[] = {&c->d_y, &c->d_dyh, &c->d_dyb, &c->d_BX};
     for (double** p : vecs)
@@ -409,7 +577,6 @@ psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psd
     if ((s = dalloc(&c->d_rhs, rhs_len)) || (s = dalloc(&c->d_part, (size_t)4 * (c->nblk + 1))) ||
         (s = dalloc(&c->d_tstep, (size_t)2 * c->nblk)) || (s = dalloc(&c->d_scal, SC_COUNT)) ||
         (s = dalloc(&c->d_info, PSDP_INFO_LEN)) || (s = dalloc(&c->d_flag, 1)) || (s = dalloc(&c->d_cert, 4)) ||
-        (s = dalloc(&c->d_Om, (size_t)K * K)) || (s = dalloc(&c->d_Linv, (size_t)npanel * nbc * nbc)) ||
         (s = dalloc(&c->d_svec, (size_t)2 * Nt)))
         return fail(s);
     if (cudaMallocHost((void**)&c->h_info, PSDP_INFO_LEN * sizeof(double)) != cudaSuccess ||
@@ -437,6 +604,7 @@ psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psd
         for (int r = 0; r + off < n; ++r) { sv.push_back(r); sv.push_back(r + off); }
     cudaMemcpy(c->d_svec, sv.data(), sv.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     if ((s = build_schur_lists(c))) return fail(s);
+    if ((s = c->mixed ? alloc_mixed(c) : alloc_fp64(c))) return fail(s);
     launch_identity(st, c->nblk, n, c->d_X);
     launch_identity(st, c->nblk, n, c->d_Z);
     cudaMemsetAsync(c->d_y, 0, (size_t)K * sizeof(double), st);
@@ -445,34 +613,56 @@ psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psd
     return PSDP_OK;
 }
 
+// Capture (once) and launch the Newton-step graph of the given precision.
+psdp_status launch_step(psdp_ctx* c, bool mixed) {
+    if (!mixed) TRY(alloc_fp64(c));
+    if (!c->opt.use_graph) {
+        enqueue_step(c, mixed);
+        return PSDP_OK;
+    }
+    cudaGraph_t& g = mixed ? c->graph32 : c->graph;
+    cudaGraphExec_t& ge = mixed ? c->graph_exec32 : c->graph_exec;
+    bool& have = mixed ? c->have_graph32 : c->have_graph;
+    if (!have) {
+        if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PSDP_ECUDA;
+        enqueue_step(c, mixed);
+        if (cudaStreamEndCapture(c->stream, &g) != cudaSuccess) { cudaGetLastError(); return PSDP_ECUDA; }
+        if (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) { cudaGetLastError(); return PSDP_ECUDA; }
+        have = true;
+        size_t nn = 0;
+        cudaGraphGetNodes(g, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+        int nk = 0;
+        for (size_t i = 0; i < nn; ++i) {
+            cudaGraphNodeType ty;
+            if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++nk;
+        }
+        c->kernels_per_step = nk;
+    }
+    if (cudaGraphLaunch(ge, c->stream) != cudaSuccess) return PSDP_ECUDA;
+    return PSDP_OK;
+}
+
 psdp_status step_impl(psdp_ctx* c, double* info) {
     cudaSetDevice(c->device);
-    if (c->opt.use_graph) {
-        if (!c->have_graph) {
-            if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PSDP_ECUDA;
-            enqueue_step(c);
-            if (cudaStreamEndCapture(c->stream, &c->graph) != cudaSuccess) { cudaGetLastError(); return PSDP_ECUDA; }
-            if (cudaGraphInstantiate(&c->graph_exec, c->graph, 0) != cudaSuccess) { cudaGetLastError(); return PSDP_ECUDA; }
-            c->have_graph = true;
-            size_t nn = 0;
-            cudaGraphGetNodes(c->graph, nullptr, &nn);
-            std::vector<cudaGraphNode_t> nodes(nn);
-            if (nn) cudaGraphGetNodes(c->graph, nodes.data(), &nn);
-            int nk = 0;
-            for (size_t i = 0; i < nn; ++i) {
-                cudaGraphNodeType ty;
-                if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++nk;
-            }
-            c->kernels_per_step = nk;
-        }
-        if (cudaGraphLaunch(c->graph_exec, c->stream) != cudaSuccess) return PSDP_ECUDA;
-    } else {
-        enqueue_step(c);
-    }
+    const bool mixed = c->mixed && !c->mixed_failed;
+    TRY(launch_step(c, mixed));
     TRY(sync_check(c));
-    prof_collect(c);
+    prof_collect(c, mixed);
+    int flag = *c->h_flag;
+    if (mixed && (flag & (FL_MIXED | FL_CHOL_SCHUR)) && !(flag & (FL_CHOL_BLOCK | FL_TIMEOUT))) {
+        // The mixed-precision direction missed its residual target (the iterate
+        // was left untouched): take this and all later steps in FP64.
+        c->mixed_failed = true;
+        cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream);
+        TRY(launch_step(c, false));
+        TRY(sync_check(c));
+        prof_collect(c, false);
+        flag = *c->h_flag;
+    }
     c->h_info[11] = (double)(c->iters + 1);
-    const int flag = *c->h_flag;
+    c->h_info[13] = (c->mixed && c->mixed_failed) ? 1.0 : 0.0;
     if (flag) {
         cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream);
         TRY(sync_check(c));
@@ -490,9 +680,14 @@ psdp_status step_impl(psdp_ctx* c, double* info) {
 void invalidate_graph(psdp_ctx* c) {
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->graph) cudaGraphDestroy(c->graph);
+    if (c->graph_exec32) cudaGraphExecDestroy(c->graph_exec32);
+    if (c->graph32) cudaGraphDestroy(c->graph32);
     c->graph_exec = nullptr;
     c->graph = nullptr;
+    c->graph_exec32 = nullptr;
+    c->graph32 = nullptr;
     c->have_graph = false;
+    c->have_graph32 = false;
 }
 
 }  // namespace
@@ -679,9 +874,36 @@ psdp_status psdp_get_iterate(psdp_ctx* c, double* X, double* Z, double* y) {
     return sync_check(c);
 }
 
+psdp_status psdp_get_schur_mixed(psdp_ctx* c, float* Om) {
+    if (!c || !Om) return PSDP_EINVAL;
+    if (!c->mixed) return PSDP_ESTATE;
+    cudaSetDevice(c->device);
+    cudaStream_t st = c->stream;
+    cudaMemsetAsync(c->d_flag, 0, sizeof(int), st);
+    launch_block_chol_inv(st, c->nblk, c->n, c->d_Z, c->d_Y, c->d_flag);
+    const bool on = c->prof_on;
+    c->prof_on = false;
+    enqueue_schur_mixed(c);
+    c->prof_on = on;
+    int flag = 0;
+    cudaMemcpyAsync(Om, c->d_Om32, (size_t)c->K * c->K * sizeof(float), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    TRY(sync_check(c));
+    if (flag) {
+        cudaMemsetAsync(c->d_flag, 0, sizeof(int), st);
+        sync_check(c);
+        return (flag & FL_TIMEOUT) ? PSDP_ETIMEOUT : PSDP_ECHOL_BLOCK;
+    }
+    const size_t K = c->K;
+    for (size_t i = 0; i < K; ++i)
+        for (size_t j = 0; j < i; ++j) Om[i * K + j] = Om[j * K + i];
+    return PSDP_OK;
+}
+
 psdp_status psdp_get_schur(psdp_ctx* c, double* Om) {
     if (!c || !Om) return PSDP_EINVAL;
     cudaSetDevice(c->device);
+    TRY(alloc_fp64(c));
     cudaStream_t st = c->stream;
     cudaMemsetAsync(c->d_flag, 0, sizeof(int), st);
     launch_block_chol_inv(st, c->nblk, c->n, c->d_Z, c->d_Y, c->d_flag);

@@ -69,6 +69,58 @@ k_potrf_diag(double* A, int K, int j0, int w, int nb, double* Linv, int* flag) {
     if (threadIdx.x == 0 && bad) atomicOr(flag, (int)FL_CHOL_SCHUR);
 }
 
+// Diagonal block of at most 32 columns factored by one warp with no barriers:
+// lane i keeps row i of the block in registers; column j's pivot and
+// multipliers travel by shuffles.  Rows past w are padded with the identity.
+// The inverse is then solved column-parallel (lane c owns column c of L^{-1}).
+__global__ void __launch_bounds__(32)
+k_potrf_diag_warp(double* A, int K, int j0, int w, int nb, double* Linv, int* flag) {
+    const int lane = threadIdx.x;
+    double a[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        double v = (lane == k) ? 1.0 : 0.0;
+        if (lane < w && k < w && k <= lane) v = A[(int64_t)(j0 + k) * K + j0 + lane];
+        a[k] = v;
+    }
+    int bad = 0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        double piv = __shfl_sync(0xffffffffu, a[j], j);
+        if (!(piv > 0.0) || !isfinite(piv)) {
+            bad = 1;
+            piv = 1.0;
+        }
+        const double ljj = sqrt(piv);
+        const double lij = (lane > j) ? a[j] / ljj : (lane == j ? ljj : 0.0);
+        a[j] = lij;
+#pragma unroll
+        for (int k = j + 1; k < 32; ++k) {
+            const double lkj = __shfl_sync(0xffffffffu, lij, k);
+            if (lane >= k) a[k] = fma(-lij, lkj, a[k]);
+        }
+    }
+    // x = column `lane` of L^{-1}: solve L x = e_lane by forward substitution
+    double x[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+        double s = (r == lane) ? 1.0 : 0.0;
+#pragma unroll
+        for (int k = 0; k < r; ++k) s = fma(-__shfl_sync(0xffffffffu, a[k], r), x[k], s);
+        x[r] = s / __shfl_sync(0xffffffffu, a[r], r);
+    }
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+        if (lane < w && k < w && k <= lane) A[(int64_t)(j0 + k) * K + j0 + lane] = a[k];
+#pragma unroll
+    for (int r = 0; r < 32; ++r)
+        if (r < nb) Linv[(size_t)lane * nb + r] = (lane < w && r < w) ? x[r] : 0.0;
+    for (int r = 32; r < nb; ++r) Linv[(size_t)lane * nb + r] = 0.0;
+    for (int c = 32 + lane; c < nb; c += 32)
+        for (int r = 0; r < nb; ++r) Linv[(size_t)c * nb + r] = 0.0;
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, (int)FL_CHOL_SCHUR);
+}
+
 // b[j0 .. j0+w) <- L_jj^{-1} b[j0 .. j0+w)   (Linv column-major, leading dim nb)
 __global__ void k_trsv_fwd_diag(const double* __restrict__ Linv, int nb, int w, int j0, double* b) {
     __shared__ double z[128];
@@ -139,6 +191,10 @@ __global__ void k_vec_copy(int K, const double* __restrict__ a, double* out) {
 
 void launch_potrf_diag(cudaStream_t st, double* A, int K, int j0, int nb, double* Linv, int* flag) {
     const int w = (K - j0 < nb) ? K - j0 : nb;
+    if (w <= 32) {
+        k_potrf_diag_warp<<<1, 32, 0, st>>>(A, K, j0, w, nb, Linv, flag);
+        return;
+    }
     const size_t sm = (size_t)2 * w * (w + 1) * sizeof(double);
     k_potrf_diag<<<1, kThreads, sm, st>>>(A, K, j0, w, nb, Linv, flag);
 }

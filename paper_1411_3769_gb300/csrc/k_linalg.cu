@@ -46,7 +46,8 @@ constexpr int BG = 32;
 __global__ void __launch_bounds__(kThreads)
 k_bgemm(int n, int count, const double* __restrict__ A, const int32_t* __restrict__ ia, int sa, int ta,
         const double* __restrict__ B, const int32_t* __restrict__ ib, int sb, int tb,
-        double* C, const int32_t* __restrict__ ic, int sc, int tc, double alpha, double beta) {
+        double* C, const int32_t* __restrict__ ic, int sc, int tc, double alpha, double beta, const int* skip) {
+    if (skip && *skip) return;
     __shared__ double As[BG][BG + 1];
     __shared__ double Bs[BG][BG + 1];
     const int tiles = (n + BG - 1) / BG;
@@ -459,11 +460,11 @@ size_t smem_two_mats(int n) { return (size_t)2 * n * (n + 1) * sizeof(double); }
 // ===================================================================== launchers
 void launch_bgemm(cudaStream_t st, int n, int count, const double* A, const int32_t* ia, int sa, int ta,
                   const double* B, const int32_t* ib, int sb, int tb, double* C, const int32_t* ic, int sc,
-                  int tc, double alpha, double beta) {
+                  int tc, double alpha, double beta, const int* skip) {
     if (count <= 0) return;
     const int tiles = (n + BG - 1) / BG;
     dim3 grid(tiles * tiles, count < 65535 ? count : 65535);
-    k_bgemm<<<grid, kThreads, 0, st>>>(n, count, A, ia, sa, ta, B, ib, sb, tb, C, ic, sc, tc, alpha, beta);
+    k_bgemm<<<grid, kThreads, 0, st>>>(n, count, A, ia, sa, ta, B, ib, sb, tb, C, ic, sc, tc, alpha, beta, skip);
 }
 
 void launch_gemm_tn(cudaStream_t st, int m, int ncol, int batch, const double* A, int lda, const int32_t* a_off,

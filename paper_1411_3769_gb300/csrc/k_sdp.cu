@@ -129,7 +129,9 @@ __device__ __forceinline__ int svec_index(int i, int j, int n) {
 // targets t < L: out[t] = sum_h beta[h][t] smat(v_h)  (P-side blocks)
 // targets t >= L: S[(t-L)] = sum_h c[h][gamma][lambda] smat(v_h), (gamma,lambda) = divmod(t-L, Na)
 __global__ void k_bt_combine(int n, int Nt, int L0, int L, int M, int Na, const int32_t* __restrict__ beta,
-                             const int32_t* __restrict__ cH, const double* __restrict__ v, double* out, double* S) {
+                             const int32_t* __restrict__ cH, const double* __restrict__ v, double* out, double* S,
+                             const int* skip) {
+    if (skip && *skip) return;
     const int n2 = n * n;
     const int t = blockIdx.y;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n2; e += gridDim.x * blockDim.x) {
@@ -154,7 +156,8 @@ __global__ void k_bt_combine(int n, int Nt, int L0, int L, int M, int Na, const 
 }
 
 // in place: out = -(N + N^T) on the Lyapunov blocks
-__global__ void k_symneg(int nb, int n, double* N) {
+__global__ void k_symneg(int nb, int n, double* N, const int* skip) {
+    if (skip && *skip) return;
     const int g = blockIdx.y;
     double* Ng = N + (int64_t)g * n * n;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
@@ -171,7 +174,9 @@ __global__ void k_symneg(int nb, int n, double* N) {
 // targets t = h*(Na+1) + lp: lp == Na -> Q_h = sum_{gamma in P} beta sym(W_gamma);
 // else R_{h,lp} = sum_{gamma in Lyap} c[h][gamma][lp] sym(W_{L+gamma}).
 __global__ void k_adj_combine(int n, int L0, int L, int M, int Na, const int32_t* __restrict__ beta,
-                              const int32_t* __restrict__ cH, const double* __restrict__ W, double* out) {
+                              const int32_t* __restrict__ cH, const double* __restrict__ W, double* out,
+                              const int* skip) {
+    if (skip && *skip) return;
     const int n2 = n * n;
     const int t = blockIdx.y;
     const int h = t / (Na + 1), lp = t % (Na + 1);
@@ -200,7 +205,8 @@ __global__ void k_adj_combine(int n, int L0, int L, int M, int Na, const int32_t
 // out[h*Nt + q] = svec_adj(Q_h)_q - 2 sum_lambda svec_adj(A_lambda R_{h,lambda})_q - acoef
 __global__ void k_adj_finish(int n, int Nt, int L0, int Na, const double* __restrict__ adj,
                              const double* __restrict__ adj2, const int32_t* __restrict__ svec, double acoef,
-                             double* out) {
+                             double* out, const int* skip) {
+    if (skip && *skip) return;
     const int n2 = n * n;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < L0 * Nt; t += gridDim.x * blockDim.x) {
         const int h = t / Nt, q = t % Nt;
@@ -449,27 +455,29 @@ __global__ void k_schur_copy(int n, int nterms, const int32_t* __restrict__ desc
 
 // One CTA per (pair, p): Omega[(a,p),(b,q)] for all q from the sub-blocks
 // F_{iv}[j][u] = T'[(i n + j) n^2 + v n + u] of the pair's contraction T'.
+template <class F>
 __global__ void __launch_bounds__(kThreads)
 k_schur_gather(int n, int Nt, int K, int p0, const int32_t* __restrict__ pa, const int32_t* __restrict__ pb,
-               const int32_t* __restrict__ svec, const double* __restrict__ T, double* Om) {
-    extern __shared__ double sm[];
+               const int32_t* __restrict__ svec, const F* __restrict__ T, F* Om) {
+    extern __shared__ double smd[];
+    F* sm = reinterpret_cast<F*>(smd);
     const int n2 = n * n;
     const int p = blockIdx.x, pl = blockIdx.y, pair = p0 + pl;
     const int a = pa[pair], b = pb[pair];
     const int r = svec[2 * p], s = svec[2 * p + 1];
-    const double* Tp = T + (int64_t)pl * n2 * n2;
-    double* F1 = sm;              // F_rs
-    double* F2 = sm + n2;         // F_sr (only if r != s)
+    const F* Tp = T + (int64_t)pl * n2 * n2;
+    F* F1 = sm;                   // F_rs
+    F* F2 = sm + n2;              // F_sr (only if r != s)
     for (int e = threadIdx.x; e < n2; e += blockDim.x) {
         const int j = e / n, u = e % n;
         F1[e] = Tp[((int64_t)r * n + j) * n2 + s * n + u];
         if (r != s) F2[e] = Tp[((int64_t)s * n + j) * n2 + r * n + u];
     }
     __syncthreads();
-    double* row = Om + (int64_t)(a * Nt + p) * K + (int64_t)b * Nt;
+    F* row = Om + (int64_t)(a * Nt + p) * K + (int64_t)b * Nt;
     for (int q = threadIdx.x; q < Nt; q += blockDim.x) {
         const int k = svec[2 * q], m = svec[2 * q + 1];
-        double v = F1[k * n + m];
+        F v = F1[k * n + m];
         if (k != m) v += F1[m * n + k];
         if (r != s) {
             v += F2[k * n + m];
@@ -554,28 +562,29 @@ void launch_cdiag(cudaStream_t st, psdp_ctx* c) {
                                                     c->opt.delta, c->opt.delta_L, c->d_cdiag);
 }
 
-void launch_bt(cudaStream_t st, psdp_ctx* c, const double* v, double* out) {
+void launch_bt(cudaStream_t st, psdp_ctx* c, const double* v, double* out, const int* skip) {
     const int n = c->n, n2 = c->n2;
     dim3 g1((n2 + kThreads - 1) / kThreads, c->L + c->M * c->Na);
-    k_bt_combine<<<g1, kThreads, 0, st>>>(n, c->Nt, c->L0, c->L, c->M, c->Na, c->d_beta, c->d_cH, v, out, c->d_S);
+    k_bt_combine<<<g1, kThreads, 0, st>>>(n, c->Nt, c->L0, c->L, c->M, c->Na, c->d_beta, c->d_cH, v, out, c->d_S,
+                                          skip);
     // N_gamma = sum_lambda S_{gamma,lambda} A_lambda  (written into the Lyapunov output blocks)
     double* outL = out + (int64_t)c->L * n2;
     for (int li = 0; li < c->Na; ++li)
         launch_bgemm(st, n, c->M, c->d_S + (int64_t)li * n2, nullptr, c->Na, 0, c->d_A + (int64_t)li * n2, nullptr, 0,
-                     0, outL, nullptr, 1, 0, 1.0, li ? 1.0 : 0.0);
+                     0, outL, nullptr, 1, 0, 1.0, li ? 1.0 : 0.0, skip);
     dim3 g2((n2 + kThreads - 1) / kThreads, c->M);
-    k_symneg<<<g2, kThreads, 0, st>>>(c->M, n, outL);
+    k_symneg<<<g2, kThreads, 0, st>>>(c->M, n, outL, skip);
 }
 
-void launch_b(cudaStream_t st, psdp_ctx* c, const double* W, double* out, double acoef) {
+void launch_b(cudaStream_t st, psdp_ctx* c, const double* W, double* out, double acoef, const int* skip) {
     const int n = c->n, n2 = c->n2;
     dim3 g1((n2 + kThreads - 1) / kThreads, c->L0 * (c->Na + 1));
-    k_adj_combine<<<g1, kThreads, 0, st>>>(n, c->L0, c->L, c->M, c->Na, c->d_beta, c->d_cH, W, c->d_adj);
+    k_adj_combine<<<g1, kThreads, 0, st>>>(n, c->L0, c->L, c->M, c->Na, c->d_beta, c->d_cH, W, c->d_adj, skip);
     for (int li = 0; li < c->Na; ++li)
         launch_bgemm(st, n, c->L0, c->d_A + (int64_t)li * n2, nullptr, 0, 0, c->d_adj + (int64_t)li * n2, nullptr,
-                     c->Na + 1, 0, c->d_adj2 + (int64_t)li * n2, nullptr, c->Na, 0, 1.0, 0.0);
+                     c->Na + 1, 0, c->d_adj2 + (int64_t)li * n2, nullptr, c->Na, 0, 1.0, 0.0, skip);
     k_adj_finish<<<grid_for((int64_t)c->L0 * c->Nt), kThreads, 0, st>>>(n, c->Nt, c->L0, c->Na, c->d_adj, c->d_adj2,
-                                                                        c->d_svec, acoef, out);
+                                                                        c->d_svec, acoef, out, skip);
 }
 
 void launch_ew_G(cudaStream_t st, psdp_ctx* c, const double* BTy, const double* Z, double* G) {
@@ -640,8 +649,15 @@ void launch_schur_operands(cudaStream_t st, psdp_ctx* c) {
 void launch_schur_gather(cudaStream_t st, psdp_ctx* c, int p0, int np) {
     const size_t sm = (size_t)2 * c->n2 * sizeof(double);
     dim3 g(c->Nt, np);
-    k_schur_gather<<<g, kThreads, sm, st>>>(c->n, c->Nt, c->K, p0, c->d_pair_a, c->d_pair_b, c->d_svec,
-                                            c->d_Tbuf, c->d_Om);
+    k_schur_gather<double><<<g, kThreads, sm, st>>>(c->n, c->Nt, c->K, p0, c->d_pair_a, c->d_pair_b, c->d_svec,
+                                                    c->d_Tbuf, c->d_Om);
+}
+
+void launch_schur_gather32(cudaStream_t st, psdp_ctx* c, int p0, int np, const float* T, float* Om) {
+    const size_t sm = (size_t)2 * c->n2 * sizeof(float);
+    dim3 g(c->Nt, np);
+    k_schur_gather<float><<<g, kThreads, sm, st>>>(c->n, c->Nt, c->K, p0, c->d_pair_a, c->d_pair_b, c->d_svec, T,
+                                                   Om);
 }
 
 void launch_certify_finalize(cudaStream_t st, int count, int n, const double* eig, int L, double* out) {
@@ -655,5 +671,6 @@ void launch_grid_build(cudaStream_t st, psdp_ctx* c, int N, int64_t first, int c
 }
 
 void init_attrs_sdp(int smem_max) {
-    set_max_dynamic_smem((const void*)k_schur_gather, smem_max);
+    set_max_dynamic_smem((const void*)k_schur_gather<double>, smem_max);
+    set_max_dynamic_smem((const void*)k_schur_gather<float>, smem_max);
 }

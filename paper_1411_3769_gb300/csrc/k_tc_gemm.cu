@@ -119,7 +119,7 @@ __host__ __device__ constexpr uint32_t make_idesc() {
 template <bool BF16, int SPLIT, int STAGES>
 __global__ void __launch_bounds__(128, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
-          const __grid_constant__ CUtensorMap mAlo, const __grid_constant__ CUtensorMap mBlo, int M, int N,
+          const __grid_constant__ CUtensorMap mAlo, const __grid_constant__ CUtensorMap mBlo, int M, int N, int b0,
           const int32_t* __restrict__ kd, int kd_uniform, float* C, int64_t ldc, int64_t c_batch, float alpha,
           float beta, int tri, int* flag) {
     constexpr int STAGE_BYTES = (SPLIT == 3) ? 2 * (TILE_A + TILE_B) : (TILE_A + TILE_B);
@@ -172,11 +172,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtens
                 const uint32_t st = base + s * STAGE_BYTES;
                 const uint32_t fb = full0 + 8 * s;
                 mbar_expect_tx(fb, STAGE_BYTES);
-                tma_load_3d(st, &mA, fb, kt * BK, m0, b);
-                tma_load_3d(st + TILE_A, &mB, fb, kt * BK, n0, b);
+                tma_load_3d(st, &mA, fb, kt * BK, m0, b0 + b);
+                tma_load_3d(st + TILE_A, &mB, fb, kt * BK, n0, b0 + b);
                 if constexpr (SPLIT == 3) {
-                    tma_load_3d(st + TILE_A + TILE_B, &mAlo, fb, kt * BK, m0, b);
-                    tma_load_3d(st + 2 * TILE_A + TILE_B, &mBlo, fb, kt * BK, n0, b);
+                    tma_load_3d(st + TILE_A + TILE_B, &mAlo, fb, kt * BK, m0, b0 + b);
+                    tma_load_3d(st + 2 * TILE_A + TILE_B, &mBlo, fb, kt * BK, n0, b0 + b);
                 }
             }
         } else if (warp == 1 && lane == 0) {
@@ -286,20 +286,21 @@ bool tc_make_map(CUtensorMap* map, const void* base, bool bf16, int64_t kdim, in
 // D = A B^T over a batch; see the file header.  Returns false if a tensor map
 // could not be encoded (nothing is launched then).
 bool launch_tc_gemm(cudaStream_t st, bool bf16, int split, const CUtensorMap& A, const CUtensorMap& B,
-                    const CUtensorMap* Alo, const CUtensorMap* Blo, int M, int N, int batch, const int32_t* kd,
-                    int kd_uniform, float* C, int64_t ldc, int64_t c_batch, float alpha, float beta, int tri,
-                    int* flag) {
+                    const CUtensorMap* Alo, const CUtensorMap* Blo, int M, int N, int batch, int b0,
+                    const int32_t* kd, int kd_uniform, float* C, int64_t ldc, int64_t c_batch, float alpha,
+                    float beta, int tri, int* flag) {
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
     if (grid.x == 0 || grid.y == 0 || batch <= 0) return true;
     if (bf16) {
-        k_tc_gemm<true, 1, 4><<<grid, 128, smem_bytes<true, 1, 4>(), st>>>(A, B, A, B, M, N, kd, kd_uniform, C, ldc,
-                                                                         c_batch, alpha, beta, tri, flag);
+        k_tc_gemm<true, 1, 4><<<grid, 128, smem_bytes<true, 1, 4>(), st>>>(A, B, A, B, M, N, b0, kd, kd_uniform, C,
+                                                                         ldc, c_batch, alpha, beta, tri, flag);
     } else if (split == 3) {
-        k_tc_gemm<false, 3, 3><<<grid, 128, smem_bytes<false, 3, 3>(), st>>>(A, B, *Alo, *Blo, M, N, kd, kd_uniform, C,
-                                                                           ldc, c_batch, alpha, beta, tri, flag);
+        k_tc_gemm<false, 3, 3><<<grid, 128, smem_bytes<false, 3, 3>(), st>>>(A, B, *Alo, *Blo, M, N, b0, kd,
+                                                                           kd_uniform, C, ldc, c_batch, alpha, beta,
+                                                                           tri, flag);
     } else {
-        k_tc_gemm<false, 1, 4><<<grid, 128, smem_bytes<false, 1, 4>(), st>>>(A, B, A, B, M, N, kd, kd_uniform, C, ldc,
-                                                                           c_batch, alpha, beta, tri, flag);
+        k_tc_gemm<false, 1, 4><<<grid, 128, smem_bytes<false, 1, 4>(), st>>>(A, B, A, B, M, N, b0, kd, kd_uniform, C,
+                                                                           ldc, c_batch, alpha, beta, tri, flag);
     }
     return true;
 }
@@ -373,11 +374,11 @@ extern "C" psdp_status psdp_tc_gemm_check(int M, int N, int K, int dtype, int sp
             launch_split_tf32(st, (int64_t)N * kpad, (const float*)dB, (float*)dBh, (float*)dBl);
             ok = tc_make_map(&mA, dAh, false, K, M, 1, kpad, 0, 128) && tc_make_map(&mB, dBh, false, K, N, 1, kpad, 0, 128) &&
                  tc_make_map(&mAl, dAl, false, K, M, 1, kpad, 0, 128) && tc_make_map(&mBl, dBl, false, K, N, 1, kpad, 0, 128);
-            if (ok) launch_tc_gemm(st, false, 3, mA, mB, &mAl, &mBl, M, N, 1, nullptr, K, dC, M, 0, 1.f, 0.f, 0, dflag);
+            if (ok) launch_tc_gemm(st, false, 3, mA, mB, &mAl, &mBl, M, N, 1, 0, nullptr, K, dC, M, 0, 1.f, 0.f, 0, dflag);
         } else {
             ok = tc_make_map(&mA, dA, dtype == 1, K, M, 1, kpad, 0, 128) &&
                  tc_make_map(&mB, dB, dtype == 1, K, N, 1, kpad, 0, 128);
-            if (ok) launch_tc_gemm(st, dtype == 1, 1, mA, mB, nullptr, nullptr, M, N, 1, nullptr, K, dC, M, 0, 1.f, 0.f, 0, dflag);
+            if (ok) launch_tc_gemm(st, dtype == 1, 1, mA, mB, nullptr, nullptr, M, N, 1, 0, nullptr, K, dC, M, 0, 1.f, 0.f, 0, dflag);
         }
         if (!ok) s = PSDP_ECUDA;
         int flag = 0;

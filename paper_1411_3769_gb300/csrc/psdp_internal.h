@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -36,6 +37,7 @@ enum FlagBits {
     FL_CHOL_SCHUR = 2,
     FL_NAN = 4,
     FL_TIMEOUT = 8,
+    FL_MIXED = 16,     // mixed-precision solve did not reach its residual target
 };
 
 struct ProfSite {
@@ -94,12 +96,33 @@ struct psdp_ctx {
     int pairs_per_chunk = 1;
     double *d_Om = nullptr;           // [K][K] row-major, upper triangle authoritative
     double *d_Linv = nullptr;         // diagonal-block inverses of the dense factor [npanel][nb][nb]
-    int nb_chol = 64;
+    int nb_chol = 32;
     double flops_schur = 0, flops_chol = 0, flops_schur_dense = 0;
 
     // ----- misc
     double *d_grid = nullptr; size_t grid_cap = 0;   // grid-check scratch
     int32_t *d_svec = nullptr;        // (r, s) of each svec index [Nt][2]
+
+    // ----- mixed precision (3xTF32 Schur and Cholesky, FP64 PCG)
+    bool mixed = false;               // precision == PSDP_MIXED
+    bool mixed_failed = false;        // sticky: fell back to the FP64 step
+    bool have_fp64 = false;           // FP64 Schur / Cholesky buffers allocated
+    int tpad = 0, nb32 = 128, pairs_per_chunk32 = 1;
+    int pcg_max = 8;
+    double pcg_tol = 1e-12, pcg_fail = 1e-9;
+    int32_t *d_term_off_t = nullptr;  // first term of each pair [npairs]
+    float *d_opA_hi = nullptr, *d_opA_lo = nullptr, *d_opB_hi = nullptr, *d_opB_lo = nullptr;
+    double *d_prodA = nullptr, *d_prodB = nullptr;     // GEMM-built operand products [nlyap_prod][n][n]
+    float *d_T32 = nullptr, *d_Om32 = nullptr, *d_Linv32 = nullptr, *d_Pt_hi = nullptr, *d_Pt_lo = nullptr;
+    float *d_z32 = nullptr, *d_part32 = nullptr;
+    double *d_pcg_x = nullptr, *d_pcg_r = nullptr, *d_pcg_z = nullptr, *d_pcg_p = nullptr, *d_pcg_q = nullptr;
+    double *d_pcg_state = nullptr;
+    int *d_pcg_done = nullptr;
+    double *d_M1 = nullptr, *d_M2 = nullptr;          // matrix-free Omega*v scratch blocks
+    CUtensorMap map_opA_hi, map_opA_lo, map_opB_hi, map_opB_lo;
+    bool have_graph32 = false;
+    cudaGraphExec_t graph_exec32 = nullptr;
+    cudaGraph_t graph32 = nullptr;
     double *d_cert = nullptr;         // certificate outputs [4]
     int iters = 0;
     int kernels_per_step = 0;   // kernel nodes in the captured Newton-step graph
@@ -112,9 +135,11 @@ struct psdp_ctx {
     std::vector<std::string> prof_names;
     std::vector<int64_t> prof_launches;
     std::vector<double> prof_ms;
-    std::vector<ProfSite> prof_sites;     // sites recorded in the current step
+    std::vector<ProfSite> prof_sites;     // sites of the FP64 step
+    std::vector<ProfSite> prof_sites32;   // sites of the mixed-precision step
+    std::vector<ProfSite>* prof_cur = nullptr;
     std::vector<cudaEvent_t> prof_pool;   // reusable events
-    size_t prof_pool_used = 0;
+    size_t prof_pool_used = 0, prof_pool_limit = 0;
 };
 
 // ------------------------------------------------------------- launchers
@@ -131,7 +156,8 @@ void launch_hmat(cudaStream_t st, int L0, int M, int Na, int n, const int32_t* c
 void launch_bgemm(cudaStream_t st, int n, int count,
                   const double* A, const int32_t* ia, int sa, int ta,
                   const double* B, const int32_t* ib, int sb, int tb,
-                  double* C, const int32_t* ic, int sc, int tc, double alpha, double beta);
+                  double* C, const int32_t* ic, int sc, int tc, double alpha, double beta,
+                  const int* skip = nullptr);
 
 // batched TN GEMM: C_b[r][c] = alpha * sum_{k<kd_b} A_b[k*lda + r] * B_b[k*ldb + c] + beta * C_b[r*ldc + c]
 // for r < m, c < ncol; per-batch offsets (elements) and contraction lengths from device arrays
@@ -151,8 +177,9 @@ void launch_block_maxstep(cudaStream_t st, int nb, int n, const double* X, const
 void launch_block_mineig(cudaStream_t st, int count, int n, const double* M, double sign, double* out);
 
 // SDP operators
-void launch_bt(cudaStream_t st, psdp_ctx* c, const double* v, double* out_blocks);       // out = B^T(v)
-void launch_b(cudaStream_t st, psdp_ctx* c, const double* W, double* out, double acoef);  // out = B(W) - acoef*1
+// out = B^T(v);  out = B(W) - acoef*1.  With skip non-null the kernels do nothing while *skip != 0.
+void launch_bt(cudaStream_t st, psdp_ctx* c, const double* v, double* out_blocks, const int* skip = nullptr);
+void launch_b(cudaStream_t st, psdp_ctx* c, const double* W, double* out, double acoef, const int* skip = nullptr);
 
 // elementwise
 void launch_ew_G(cudaStream_t st, psdp_ctx* c, const double* BTy, const double* Z, double* G);
@@ -190,6 +217,33 @@ void launch_grid_build(cudaStream_t st, psdp_ctx* c, int N, int64_t first, int c
 
 // FP64 throughput probe
 double fp64_peak_probe(int device);
+
+// tensor-core GEMM (k_tc_gemm.cu)
+bool tc_make_map(CUtensorMap* map, const void* base, bool bf16, int64_t kdim, int64_t rows, int64_t batch,
+                 int64_t row_stride, int64_t batch_stride, int box_rows);
+bool launch_tc_gemm(cudaStream_t st, bool bf16, int split, const CUtensorMap& A, const CUtensorMap& B,
+                    const CUtensorMap* Alo, const CUtensorMap* Blo, int M, int N, int batch, int b0,
+                    const int32_t* kd, int kd_uniform, float* C, int64_t ldc, int64_t c_batch, float alpha,
+                    float beta, int tri, int* flag);
+void launch_split_tf32(cudaStream_t st, int64_t n, const float* x, float* hi, float* lo);
+void init_attrs_tc(int smem_optin);
+
+// mixed precision (k_mixed.cu)
+void launch_schur_pack32(cudaStream_t st, psdp_ctx* c);
+void launch_schur_gather32(cudaStream_t st, psdp_ctx* c, int p0, int np, const float* T, float* Om);
+void launch_potrf_diag32(cudaStream_t st, float* A, int K, int j0, int nb, float* Linv, int* flag);
+void launch_trsm32_pack(cudaStream_t st, float* A, int K, int j0, int nb, const float* Linv, float* PtHi,
+                        float* PtLo);
+void launch_precond32(cudaStream_t st, const float* A, int K, int nb, const float* Linv, float* z32, float* partial,
+                      const double* r, double* z, const int* skip);
+void launch_pcg_init(cudaStream_t st, int K, const double* b, double* x, double* r, double* s, int* done);
+void launch_pcg_start(cudaStream_t st, int K, const double* r, const double* z, double* p, double* s, const int* done);
+void launch_pcg_alpha(cudaStream_t st, int K, const double* p, const double* q, double* x, double* r, double* s,
+                      int* done, double tol);
+void launch_pcg_beta(cudaStream_t st, int K, const double* r, const double* z, double* p, double* s, const int* done);
+void launch_pcg_finish(cudaStream_t st, int K, const double* x, double* out, double* s, const int* done, int* flag,
+                       double tol_fail, double* info_slot);
+void init_attrs_mixed(int smem_optin);
 
 // errors
 #define CK(x) do { cudaError_t e__ = (x); if (e__ != cudaSuccess) return PSDP_ECUDA; } while (0)
