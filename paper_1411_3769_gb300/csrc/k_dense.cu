@@ -69,56 +69,85 @@ k_potrf_diag(double* A, int K, int j0, int w, int nb, double* Linv, int* flag) {
     if (threadIdx.x == 0 && bad) atomicOr(flag, (int)FL_CHOL_SCHUR);
 }
 
-// Diagonal block of at most 32 columns factored by one warp with no barriers:
-// lane i keeps row i of the block in registers; column j's pivot and
-// multipliers travel by shuffles.  Rows past w are padded with the identity.
-// The inverse is then solved column-parallel (lane c owns column c of L^{-1}).
-__global__ void __launch_bounds__(32)
-k_potrf_diag_warp(double* A, int K, int j0, int w, int nb, double* Linv, int* flag) {
-    const int lane = threadIdx.x;
-    double a[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        double v = (lane == k) ? 1.0 : 0.0;
-        if (lane < w && k < w && k <= lane) v = A[(int64_t)(j0 + k) * K + j0 + lane];
-        a[k] = v;
+// Diagonal block of at most 32 columns, four warps.  GB300's FP64 pipe is
+// narrow, so the critical path is counted in dependent FP64 operations:
+// column j needs one rsqrt (1/L_jj; L_jj = piv * rsqrt(piv)) shared by the
+// column scale, then a rank-1 update spread over 128 threads.  L^{-1} is
+// built by 2 x 2 block recursion: the 16 x 16 diagonal inverses by forward
+// substitution in two warps at once, then -C^{-1} (B A^{-1}) as two small GEMMs.
+__global__ void __launch_bounds__(128)
+k_potrf_diag32x4(double* A, int K, int j0, int w, int nb, double* Linv, int* flag) {
+    constexpr int LD = 33;
+    __shared__ double L[32 * LD];   // column-major: L[c*LD + r]
+    __shared__ double X[32 * LD];   // L^{-1}, column-major
+    __shared__ double T[16 * 17];
+    __shared__ double rinv[32], ldiag[32];
+    __shared__ int bad;
+    const int tid = threadIdx.x;
+    if (tid == 0) bad = 0;
+    for (int idx = tid; idx < 32 * 32; idx += 128) {
+        const int c = idx / 32, r = idx % 32;
+        double v = (r == c) ? 1.0 : 0.0;
+        if (r < w && c < w && r >= c) v = A[(int64_t)(j0 + c) * K + j0 + r];
+        L[c * LD + r] = v;
+        X[c * LD + r] = 0.0;
     }
-    int bad = 0;
-#pragma unroll
+    __syncthreads();
     for (int j = 0; j < 32; ++j) {
-        double piv = __shfl_sync(0xffffffffu, a[j], j);
+        double piv = L[j * LD + j];
         if (!(piv > 0.0) || !isfinite(piv)) {
-            bad = 1;
+            if (tid == 0) bad = 1;
             piv = 1.0;
         }
-        const double ljj = sqrt(piv);
-        const double lij = (lane > j) ? a[j] / ljj : (lane == j ? ljj : 0.0);
-        a[j] = lij;
-#pragma unroll
-        for (int k = j + 1; k < 32; ++k) {
-            const double lkj = __shfl_sync(0xffffffffu, lij, k);
-            if (lane >= k) a[k] = fma(-lij, lkj, a[k]);
+        const double ri = rsqrt(piv);
+        if (tid == 0) {
+            rinv[j] = ri;
+            ldiag[j] = piv * ri;    // L_jj; the stored diagonal is read by no later step
+        }
+        if (tid > j && tid < 32) L[j * LD + tid] *= ri;
+        __syncthreads();
+        const int m = 31 - j;
+        for (int idx = tid; idx < m * m; idx += 128) {
+            const int c = j + 1 + idx / m, r = j + 1 + idx % m;
+            if (r >= c) L[c * LD + r] = fma(-L[j * LD + r], L[j * LD + c], L[c * LD + r]);
+        }
+        __syncthreads();
+    }
+    // diagonal 16 x 16 inverses: warp 0 -> rows/cols 0..15, warp 1 -> 16..31 (lane = column)
+    if (tid < 64 && (tid & 31) < 16) {
+        const int o = (tid >> 5) * 16, c = o + (tid & 31);
+        for (int r = c; r < o + 16; ++r) {
+            double s = (r == c) ? 1.0 : 0.0;
+            for (int k = c; k < r; ++k) s = fma(-L[k * LD + r], X[c * LD + k], s);
+            X[c * LD + r] = s * rinv[r];
         }
     }
-    // x = column `lane` of L^{-1}: solve L x = e_lane by forward substitution
-    double x[32];
-#pragma unroll
-    for (int r = 0; r < 32; ++r) {
-        double s = (r == lane) ? 1.0 : 0.0;
-#pragma unroll
-        for (int k = 0; k < r; ++k) s = fma(-__shfl_sync(0xffffffffu, a[k], r), x[k], s);
-        x[r] = s / __shfl_sync(0xffffffffu, a[r], r);
+    __syncthreads();
+    // T = B A^{-1}   (B = L[16..31][0..15], A^{-1} = X[0..15][0..15])
+    for (int idx = tid; idx < 256; idx += 128) {
+        const int r = idx / 16, c = idx % 16;
+        double s = 0.0;
+        for (int k = c; k < 16; ++k) s = fma(L[k * LD + 16 + r], X[c * LD + k], s);
+        T[r * 17 + c] = s;
     }
-#pragma unroll
-    for (int k = 0; k < 32; ++k)
-        if (lane < w && k < w && k <= lane) A[(int64_t)(j0 + k) * K + j0 + lane] = a[k];
-#pragma unroll
-    for (int r = 0; r < 32; ++r)
-        if (r < nb) Linv[(size_t)lane * nb + r] = (lane < w && r < w) ? x[r] : 0.0;
-    for (int r = 32; r < nb; ++r) Linv[(size_t)lane * nb + r] = 0.0;
-    for (int c = 32 + lane; c < nb; c += 32)
-        for (int r = 0; r < nb; ++r) Linv[(size_t)c * nb + r] = 0.0;
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, (int)FL_CHOL_SCHUR);
+    __syncthreads();
+    // X[16..31][0..15] = -C^{-1} T
+    for (int idx = tid; idx < 256; idx += 128) {
+        const int r = idx / 16, c = idx % 16;
+        double s = 0.0;
+        for (int k = 0; k <= r; ++k) s = fma(X[(16 + k) * LD + 16 + r], T[k * 17 + c], s);
+        X[c * LD + 16 + r] = -s;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < 32 * 32; idx += 128) {
+        const int c = idx / 32, r = idx % 32;
+        if (r < w && c < w && r >= c) A[(int64_t)(j0 + c) * K + j0 + r] = (r == c) ? ldiag[c] : L[c * LD + r];
+    }
+    for (int idx = tid; idx < nb * nb; idx += 128) {
+        const int c = idx / nb, r = idx % nb;
+        Linv[idx] = (r < w && c < w) ? X[c * LD + r] : 0.0;
+    }
+    if (tid == 0 && bad) atomicOr(flag, (int)FL_CHOL_SCHUR);
 }
 
 // b[j0 .. j0+w) <- L_jj^{-1} b[j0 .. j0+w)   (Linv column-major, leading dim nb)
@@ -192,7 +221,7 @@ __global__ void k_vec_copy(int K, const double* __restrict__ a, double* out) {
 void launch_potrf_diag(cudaStream_t st, double* A, int K, int j0, int nb, double* Linv, int* flag) {
     const int w = (K - j0 < nb) ? K - j0 : nb;
     if (w <= 32) {
-        k_potrf_diag_warp<<<1, 32, 0, st>>>(A, K, j0, w, nb, Linv, flag);
+        k_potrf_diag32x4<<<1, 128, 0, st>>>(A, K, j0, w, nb, Linv, flag);
         return;
     }
     const size_t sm = (size_t)2 * w * (w + 1) * sizeof(double);

@@ -82,57 +82,59 @@ __global__ void k_schur_pack32(int n, int tpad, const int32_t* __restrict__ term
 }
 
 // ------------------------------------------------------------- FP32 Cholesky
-// Diagonal w x w block of the FP32 matrix (column-major lower view), factored in
-// FP64 arithmetic; writes L back in FP32 and L^{-1} (column-major, ld nb) in FP32.
+// Diagonal w x w block (w <= 128) of the FP32 matrix (column-major lower view),
+// factored in FP32 (it only seeds the preconditioner; FP64 PCG fixes the
+// rest); writes L back and L^{-1} (column-major, ld nb).
 __global__ void __launch_bounds__(kThreads)
 k_potrf_diag32(float* A, int K, int j0, int w, int nb, float* Linv, int* flag) {
-    extern __shared__ double sm[];
+    extern __shared__ float smf[];
     const int ld = w + 1;
-    double* L = sm;
-    double* I = sm + (size_t)w * ld;
+    float* L = smf;
+    float* I = smf + (size_t)w * ld;
+    __shared__ float rinv[128], ldiag[128];
     __shared__ int bad;
     if (threadIdx.x == 0) bad = 0;
     for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
         const int j = idx / w, i = idx % w;
-        L[j * ld + i] = (i >= j) ? (double)A[(int64_t)(j0 + j) * K + j0 + i] : 0.0;
+        L[j * ld + i] = (i >= j) ? A[(int64_t)(j0 + j) * K + j0 + i] : 0.f;
     }
     __syncthreads();
     for (int j = 0; j < w; ++j) {
-        if (threadIdx.x == 0) {
-            double d = L[j * ld + j];
-            if (!(d > 0.0) || !isfinite(d)) {
-                bad = 1;
-                d = 1.0;
-            }
-            L[j * ld + j] = sqrt(d);
+        float piv = L[j * ld + j];
+        if (!(piv > 0.f) || !isfinite(piv)) {
+            if (threadIdx.x == 0) bad = 1;
+            piv = 1.f;
         }
-        __syncthreads();
-        const double piv = L[j * ld + j];
-        for (int i = j + 1 + threadIdx.x; i < w; i += blockDim.x) L[j * ld + i] /= piv;
+        const float ri = 1.f / sqrtf(piv);
+        if (threadIdx.x == 0) {
+            rinv[j] = ri;
+            ldiag[j] = piv * ri;
+        }
+        for (int i = j + 1 + threadIdx.x; i < w; i += blockDim.x) L[j * ld + i] *= ri;
         __syncthreads();
         const int m = w - j - 1;
         for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
             const int c = j + 1 + idx / m, r = j + 1 + idx % m;
-            if (r >= c) L[c * ld + r] -= L[j * ld + r] * L[j * ld + c];
+            if (r >= c) L[c * ld + r] = fmaf(-L[j * ld + r], L[j * ld + c], L[c * ld + r]);
         }
         __syncthreads();
     }
     for (int c = threadIdx.x; c < w; c += blockDim.x) {
-        for (int r = 0; r < c; ++r) I[c * ld + r] = 0.0;
+        for (int r = 0; r < c; ++r) I[c * ld + r] = 0.f;
         for (int r = c; r < w; ++r) {
-            double s = (r == c) ? 1.0 : 0.0;
-            for (int k = c; k < r; ++k) s -= L[k * ld + r] * I[c * ld + k];
-            I[c * ld + r] = s / L[r * ld + r];
+            float s = (r == c) ? 1.f : 0.f;
+            for (int k = c; k < r; ++k) s = fmaf(-L[k * ld + r], I[c * ld + k], s);
+            I[c * ld + r] = s * rinv[r];
         }
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
         const int j = idx / w, i = idx % w;
-        if (i >= j) A[(int64_t)(j0 + j) * K + j0 + i] = (float)L[j * ld + i];
+        if (i >= j) A[(int64_t)(j0 + j) * K + j0 + i] = (i == j) ? ldiag[j] : L[j * ld + i];
     }
     for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
         const int j = idx / nb, i = idx % nb;
-        Linv[idx] = (j < w && i < w) ? (float)I[j * ld + i] : 0.f;
+        Linv[idx] = (j < w && i < w) ? I[j * ld + i] : 0.f;
     }
     if (threadIdx.x == 0 && bad) atomicOr(flag, (int)FL_CHOL_SCHUR);
 }
@@ -363,7 +365,7 @@ void launch_schur_pack32(cudaStream_t st, psdp_ctx* c) {
 
 void launch_potrf_diag32(cudaStream_t st, float* A, int K, int j0, int nb, float* Linv, int* flag) {
     const int w = (K - j0 < nb) ? K - j0 : nb;
-    const size_t sm = (size_t)2 * w * (w + 1) * sizeof(double);
+    const size_t sm = (size_t)2 * w * (w + 1) * sizeof(float);
     k_potrf_diag32<<<1, kThreads, sm, st>>>(A, K, j0, w, nb, Linv, flag);
 }
 
