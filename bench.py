@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-runs", type=int, default=2)
     ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--mixed", type=int, default=1, help="also measure the mixed-precision path")
+    ap.add_argument("--mixed-steps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -116,6 +118,48 @@ def oracle_steps(A, w, nsteps):
         ipm.newton_step(prob, st, ipm.Options())
         times.append(time.perf_counter() - t0)
     return times
+
+
+def measure_mixed(bd, synth, name, device, nsteps):
+    """Mixed-precision Newton steps/s (from the cold start, CUDA events around
+    each step on the library's stream) and the full time-to-certificate."""
+    import torch
+    w = synth.WORKLOADS[name]
+    A = synth.system(w["n"], w["l"], w["s"], 0)
+    stream = torch.cuda.current_stream()
+    opts = bd.psdp_default_opts(stream=stream.cuda_stream, device=device, precision=1)
+    h = bd.psdp_setup(w["n"], w["l"], w["d_p"], w["d1"], A, opts)
+    try:
+        X0, Z0, y0 = bd.psdp_get_iterate(h)
+        ms = []
+        fallback = 0.0
+        for i in range(nsteps + 1):
+            bd.psdp_load_iterate(h, X0, Z0, y0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s, info = bd.psdp_step(h)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if s != 0:
+                raise RuntimeError(f"mixed step: {bd.STATUS[s]}")
+            fallback = max(fallback, info[13])
+            if i > 0:                      # the first step captures the graph
+                ms.append(e0.elapsed_time(e1))
+        work = bd.psdp_work(h)
+    finally:
+        bd.psdp_destroy(h)
+    t0 = time.perf_counter()
+    with bd.Solver(A, w["d_p"], w["d1"], device=device, precision=1) as s:
+        status, iters, info = s.solve()
+        verdict, _, _ = s.certify()
+        bd.psdp_get_P(s.h)
+    t1 = time.perf_counter()
+    return {"workload": f"n={w['n']} l={w['l']} d_p={w['d_p']} d1=d2={w['d1']} s={w['s']} seed=0",
+            "ms_per_step": sum(ms) / len(ms), "steps_per_s": 1e3 * len(ms) / sum(ms),
+            "time_to_certificate_s": t1 - t0, "newton_steps": iters, "status": status, "verdict": verdict,
+            "relgap": info["relgap"], "fp64_fallback": bool(info["fallback"] or fallback),
+            "pcg_iterations_last_step": info["refine_sweeps"], "schur_flops_per_step": work["schur_flops"],
+            "chol_flops_per_step": work["chol_flops"]}
 
 
 def run_reference(args):
@@ -256,6 +300,17 @@ def run_ours(args):
     except Exception:
         pass
 
+    # ---- mixed precision (3xTF32 tensor cores + FP64 PCG) on the mid and large workloads
+    mixed = {}
+    if args.mixed:
+        for wl in ("mid", "large"):
+            try:
+                mixed[wl] = measure_mixed(bd, synth, wl, local, args.mixed_steps)
+            except Exception as exc:   # report, do not lose the main line
+                mixed[wl] = {"error": str(exc)[:200]}
+        if "mid" in mixed and "ms_per_step" in mixed["mid"]:
+            mixed["mid"]["speedup_vs_plain_fp64_step"] = (tot_ms / args.steps) / mixed["mid"]["ms_per_step"]
+
     # ---- CPU oracle baseline on a bounded sample
     ct = oracle_steps(A, w, args.cpu_steps)
     cpu = {"value": (len(ct) / sum(ct)) if ct else None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -274,6 +329,7 @@ def run_ours(args):
             "e2e": {"value": (iters / t_job) if iters else None, "unit": UNIT, "h2d_bytes_per_step": A.nbytes / max(iters, 1),
                     "d2h_bytes_per_step": (pbytes + 16 * 8 * iters) / max(iters, 1),
                     "time_to_certificate_s": t_job, "newton_steps": iters, "status": status, "verdict": verdict},
+            "mixed": mixed,
             "gpu_launches": int(work["kernels_per_step"]) * args.steps,
             "clocks": clk.summary(),
             "work": {"schur_flops_per_step": work["schur_flops"], "chol_flops_per_step": work["chol_flops"],
