@@ -146,6 +146,15 @@ def measure_mixed(bd, synth, name, device, nsteps):
             if i > 0:                      # the first step captures the graph
                 ms.append(e0.elapsed_time(e1))
         work = bd.psdp_work(h)
+        # per-kernel breakdown from CUDA events inside the (re-captured) step graph
+        bd.psdp_profile_enable(h, True)
+        bd.psdp_load_iterate(h, X0, Z0, y0)
+        bd.psdp_step(h)
+        bd.psdp_profile_reset(h)
+        bd.psdp_load_iterate(h, X0, Z0, y0)
+        bd.psdp_step(h)
+        prof = bd.psdp_profile_get(h)
+        bd.psdp_profile_enable(h, False)
     finally:
         bd.psdp_destroy(h)
     t0 = time.perf_counter()
@@ -159,7 +168,8 @@ def measure_mixed(bd, synth, name, device, nsteps):
             "time_to_certificate_s": t1 - t0, "newton_steps": iters, "status": status, "verdict": verdict,
             "relgap": info["relgap"], "fp64_fallback": bool(info["fallback"] or fallback),
             "pcg_iterations_last_step": info["refine_sweeps"], "schur_flops_per_step": work["schur_flops"],
-            "chol_flops_per_step": work["chol_flops"]}
+            "chol_flops_per_step": work["chol_flops"],
+            "kernels_ms_per_step": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in prof.items()}}
 
 
 def run_reference(args):

@@ -110,6 +110,27 @@ psdp_status psdp_step(psdp_ctx* c, double* info);
  * or max_iter (EMAXITER).  iters/info may be NULL. */
 psdp_status psdp_solve(psdp_ctx* c, int* iters, double* info);
 
+/* Solve many independent instances together (no counterpart in the paper, whose
+ * parallelism is over the blocks of one instance).  Every unfinished instance's
+ * captured Newton-step graph becomes one branch of a single batch graph, launched
+ * once per interior-point iteration; instances that meet their stopping rule
+ * drop out (the batch graph is rebuilt once a quarter of its branches are done).
+ * All contexts must be distinct, on one device, with use_graph = 1 and profiling
+ * off.  status[i] / iters[i] (may be NULL) receive what psdp_solve would return
+ * for instance i.  The function's own result is PSDP_OK unless the batch itself
+ * could not run (EINVAL, ECUDA, ENOMEM). */
+psdp_status psdp_solve_batch(psdp_ctx** ctx, int count, psdp_status* status, int* iters);
+
+/* Pick the fastest Newton-step configuration for this instance shape by timing
+ * one step of each candidate from the current iterate (restored afterwards):
+ * 0 = FP64, 1 = mixed precision with 64-column FP32 Cholesky panels (SYRK tiles
+ * of depth 64), 2 = mixed with 128-column panels.  With cache_path non-NULL the
+ * result is looked up in / appended to that text file, keyed by
+ * (n, l, d_p, d1, d2, d_a).  The choice is applied to the context.
+ * choice and ms3 (per-candidate step times in ms, -1 if read from the cache)
+ * may be NULL. */
+psdp_status psdp_autotune(psdp_ctx* c, const char* cache_path, int* choice, double* ms3);
+
 /* Certificate of Theorems 1-2 from the current y: P_h = smat(y_h) (Root step 4);
  * every P-side coefficient sum_h beta_{h,gamma} P_h (Eq. LMI_3) and every negated
  * Lyapunov coefficient -sum_h (H^T P_h + P_h H) (Eq. LMI_4) must have its smallest

@@ -28,7 +28,8 @@ EXPORTS = ("psdp_default_opts", "psdp_setup", "psdp_sizes", "psdp_step", "psdp_s
            "psdp_grid_check", "psdp_get_P", "psdp_get_y", "psdp_get_tables", "psdp_load_iterate",
            "psdp_get_iterate", "psdp_get_schur", "psdp_apply_BT", "psdp_apply_B", "psdp_profile_enable",
            "psdp_profile_reset", "psdp_profile_get", "psdp_work", "psdp_stream", "psdp_fp64_peak",
-           "psdp_destroy", "psdp_strerror", "psdp_tc_gemm_check", "psdp_get_schur_mixed")
+           "psdp_destroy", "psdp_strerror", "psdp_tc_gemm_check", "psdp_get_schur_mixed",
+           "psdp_solve_batch", "psdp_autotune")
 
 
 class Opts(C.Structure):
@@ -82,6 +83,8 @@ def _lib():
             "psdp_strerror": (C.c_char_p, [C.c_int]),
             "psdp_tc_gemm_check": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp]),
             "psdp_get_schur_mixed": (C.c_int, [vp, vp]),
+            "psdp_solve_batch": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+            "psdp_autotune": (C.c_int, [vp, C.c_char_p, C.POINTER(C.c_int), dp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -270,6 +273,23 @@ def psdp_tc_gemm_check(A: np.ndarray, B: np.ndarray, split: int = 1) -> np.ndarr
     _check(_lib().psdp_tc_gemm_check(M, N, K, dtype, split, A.ctypes.data, B.ctypes.data, C_.ctypes.data),
            "psdp_tc_gemm_check")
     return C_.T
+
+
+def psdp_solve_batch(handles) -> tuple[list[str], list[int]]:
+    n = len(handles)
+    arr = (C.c_void_p * n)(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    st = (C.c_int * n)()
+    it = (C.c_int * n)()
+    _check(_lib().psdp_solve_batch(arr, n, st, it), "psdp_solve_batch")
+    return [STATUS[s] for s in st], list(it)
+
+
+def psdp_autotune(h, cache_path: str | None = None) -> tuple[int, np.ndarray]:
+    ch = C.c_int(-1)
+    ms = np.zeros(3)
+    _check(_lib().psdp_autotune(h, cache_path.encode() if cache_path else None, C.byref(ch), _dp(ms)),
+           "psdp_autotune")
+    return ch.value, ms
 
 
 def psdp_destroy(h):

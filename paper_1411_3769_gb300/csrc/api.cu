@@ -613,13 +613,9 @@ psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psd
     return PSDP_OK;
 }
 
-// Capture (once) and launch the Newton-step graph of the given precision.
-psdp_status launch_step(psdp_ctx* c, bool mixed) {
+// Capture (once) the Newton-step graph of the given precision.
+psdp_status ensure_graph(psdp_ctx* c, bool mixed) {
     if (!mixed) TRY(alloc_fp64(c));
-    if (!c->opt.use_graph) {
-        enqueue_step(c, mixed);
-        return PSDP_OK;
-    }
     cudaGraph_t& g = mixed ? c->graph32 : c->graph;
     cudaGraphExec_t& ge = mixed ? c->graph_exec32 : c->graph_exec;
     bool& have = mixed ? c->have_graph32 : c->have_graph;
@@ -640,15 +636,24 @@ psdp_status launch_step(psdp_ctx* c, bool mixed) {
         }
         c->kernels_per_step = nk;
     }
-    if (cudaGraphLaunch(ge, c->stream) != cudaSuccess) return PSDP_ECUDA;
     return PSDP_OK;
 }
 
-psdp_status step_impl(psdp_ctx* c, double* info) {
-    cudaSetDevice(c->device);
-    const bool mixed = c->mixed && !c->mixed_failed;
-    TRY(launch_step(c, mixed));
-    TRY(sync_check(c));
+// Launch one Newton step of the given precision on the context's stream.
+psdp_status launch_step(psdp_ctx* c, bool mixed) {
+    if (!c->opt.use_graph) {
+        if (!mixed) TRY(alloc_fp64(c));
+        enqueue_step(c, mixed);
+        return PSDP_OK;
+    }
+    TRY(ensure_graph(c, mixed));
+    if (cudaGraphLaunch(mixed ? c->graph_exec32 : c->graph_exec, c->stream) != cudaSuccess) return PSDP_ECUDA;
+    return PSDP_OK;
+}
+
+// After a step of the given precision completed: FP64 fallback of a missed
+// mixed step, flag -> status, info for the caller.
+psdp_status finish_step(psdp_ctx* c, bool mixed, double* info) {
     prof_collect(c, mixed);
     int flag = *c->h_flag;
     if (mixed && (flag & (FL_MIXED | FL_CHOL_SCHUR)) && !(flag & (FL_CHOL_BLOCK | FL_TIMEOUT))) {
@@ -675,6 +680,25 @@ psdp_status step_impl(psdp_ctx* c, double* info) {
     c->iters += 1;
     if (info) memcpy(info, c->h_info, PSDP_INFO_LEN * sizeof(double));
     return PSDP_OK;
+}
+
+psdp_status step_impl(psdp_ctx* c, double* info) {
+    cudaSetDevice(c->device);
+    const bool mixed = c->mixed && !c->mixed_failed;
+    TRY(launch_step(c, mixed));
+    TRY(sync_check(c));
+    return finish_step(c, mixed, info);
+}
+
+// Stopping rule after a successful step: PSDP_OK when the relative gap and both
+// relative residuals are <= eps, PSDP_EUNBOUNDED on a primal ray, else
+// PSDP_ESTATE meaning "keep iterating".
+psdp_status converged(const psdp_ctx* c, const double* inf) {
+    const double eps = c->opt.eps;
+    if (inf[2] <= eps && inf[3] <= eps && inf[4] <= eps) return PSDP_OK;
+    const double trX = inf[9];
+    if (trX > 1e8 && inf[10] / trX < 1e-6 && inf[0] / trX > 1e-8) return PSDP_EUNBOUNDED;
+    return PSDP_ESTATE;
 }
 
 void invalidate_graph(psdp_ctx* c) {
@@ -744,21 +768,9 @@ psdp_status psdp_solve(psdp_ctx* c, int* iters, double* info) {
     int it = 0;
     for (; it < c->opt.max_iter; ++it) {
         psdp_status r = psdp_step(c, inf);
-        if (r != PSDP_OK) {
+        if (r == PSDP_OK) r = converged(c, inf);
+        if (r != PSDP_ESTATE) {
             s = r;
-            ++it;
-            break;
-        }
-        const double eps = c->opt.eps;
-        if (inf[2] <= eps && inf[3] <= eps && inf[4] <= eps) {
-            s = PSDP_OK;
-            ++it;
-            break;
-        }
-        // primal ray: X grows without bound along B(X) ~ 0 with tr(CX) > 0
-        const double trX = inf[9];
-        if (trX > 1e8 && inf[10] / trX < 1e-6 && inf[0] / trX > 1e-8) {
-            s = PSDP_EUNBOUNDED;
             ++it;
             break;
         }
@@ -766,6 +778,170 @@ psdp_status psdp_solve(psdp_ctx* c, int* iters, double* info) {
     if (iters) *iters = it;
     if (info) memcpy(info, c->h_info, PSDP_INFO_LEN * sizeof(double));
     return s;
+}
+
+psdp_status psdp_solve_batch(psdp_ctx** v, int count, psdp_status* status, int* iters) {
+    if (!v || count < 1) return PSDP_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        if (!v[i] || v[i]->device != v[0]->device || !v[i]->opt.use_graph || v[i]->prof_on) return PSDP_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (v[j] == v[i]) return PSDP_EINVAL;
+    }
+    try {
+        cudaSetDevice(v[0]->device);
+        std::vector<psdp_status> st(count, PSDP_EMAXITER);
+        std::vector<int> it(count, 0), built;
+        std::vector<char> done(count, 0), frozen(count, 0);
+        cudaStream_t bs;
+        if (cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) != cudaSuccess) return PSDP_ECUDA;
+        cudaGraphExec_t exec = nullptr;
+        const int frozen_flag = FL_FROZEN;
+        psdp_status err = PSDP_OK;
+        int remaining = count;
+        bool rebuild = true;
+        while (remaining > 0 && err == PSDP_OK) {
+            if (rebuild) {
+                // one graph whose branches are the step graphs of all unfinished instances
+                if (exec) cudaGraphExecDestroy(exec);
+                exec = nullptr;
+                built.clear();
+                cudaGraph_t parent;
+                cudaGraphCreate(&parent, 0);
+                for (int i = 0; i < count && err == PSDP_OK; ++i) {
+                    if (done[i]) continue;
+                    psdp_ctx* c = v[i];
+                    const bool mixed = c->mixed && !c->mixed_failed;
+                    if ((err = ensure_graph(c, mixed)) != PSDP_OK) break;
+                    cudaGraphNode_t node;
+                    if (cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, mixed ? c->graph32 : c->graph) !=
+                        cudaSuccess)
+                        err = PSDP_ECUDA;
+                    built.push_back(i);
+                }
+                if (err == PSDP_OK && cudaGraphInstantiate(&exec, parent, 0) != cudaSuccess) err = PSDP_ECUDA;
+                cudaGraphDestroy(parent);
+                if (err != PSDP_OK) break;
+                for (int i : built) frozen[i] = 0;
+                rebuild = false;
+            }
+            if (cudaGraphLaunch(exec, bs) != cudaSuccess || cudaStreamSynchronize(bs) != cudaSuccess) {
+                err = PSDP_ECUDA;
+                break;
+            }
+            int newly = 0, in_graph_frozen = 0;
+            for (int i : built) {
+                if (frozen[i]) {
+                    ++in_graph_frozen;
+                    continue;
+                }
+                psdp_ctx* c = v[i];
+                const bool mixed = c->mixed && !c->mixed_failed;
+                double inf[PSDP_INFO_LEN];
+                psdp_status r = finish_step(c, mixed, inf);
+                if (mixed && c->mixed_failed) rebuild = true;       // its graph branch changed precision
+                ++it[i];
+                if (r == PSDP_OK) r = converged(c, inf);
+                if (r == PSDP_ESTATE && it[i] >= c->opt.max_iter) r = PSDP_EMAXITER;
+                if (r != PSDP_ESTATE) {
+                    st[i] = r;
+                    done[i] = 1;
+                    frozen[i] = 1;
+                    --remaining;
+                    ++newly;
+                    // a frozen instance keeps running inside the graph until the next
+                    // rebuild, but its update kernel sees the flag and leaves the iterate
+                    cudaMemcpyAsync(c->d_flag, &frozen_flag, sizeof(int), cudaMemcpyHostToDevice, c->stream);
+                    cudaStreamSynchronize(c->stream);
+                }
+            }
+            if ((newly + in_graph_frozen) * 4 >= (int)built.size()) rebuild = true;
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        for (int i = 0; i < count; ++i) {
+            cudaMemsetAsync(v[i]->d_flag, 0, sizeof(int), v[i]->stream);
+            cudaStreamSynchronize(v[i]->stream);
+            if (status) status[i] = st[i];
+            if (iters) iters[i] = it[i];
+        }
+        cudaStreamDestroy(bs);
+        cudaGetLastError();
+        return err;
+    } catch (...) {
+        return PSDP_ENOMEM;
+    }
+}
+
+psdp_status psdp_autotune(psdp_ctx* c, const char* cache_path, int* choice, double* ms_out) {
+    if (!c) return PSDP_EINVAL;
+    cudaSetDevice(c->device);
+    // candidates: 0 = FP64, 1 = mixed with 64-column FP32 panels, 2 = mixed with 128-column panels
+    char key[128];
+    snprintf(key, sizeof key, "n=%d l=%d d_p=%d d1=%d d2=%d d_a=%d", c->n, c->l, c->d_p, c->d1, c->d2, c->d_a);
+    int best = -1;
+    double ms[3] = {-1.0, -1.0, -1.0};
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "r")) {
+            char line[256];
+            while (fgets(line, sizeof line, f)) {
+                int ch = -1;
+                char* bar = strchr(line, '|');
+                if (bar && (size_t)(bar - line) == strlen(key) && strncmp(line, key, strlen(key)) == 0 &&
+                    sscanf(bar + 1, "%d %lf %lf %lf", &ch, &ms[0], &ms[1], &ms[2]) >= 1)
+                    best = ch;
+            }
+            fclose(f);
+        }
+    }
+    if (best < 0) {
+        // time one Newton step per candidate from the current iterate, which is restored after each
+        const size_t nb = (size_t)c->nblk * c->n2;
+        std::vector<double> X(nb), Z(nb), y(c->K);
+        TRY(psdp_get_iterate(c, X.data(), Z.data(), y.data()));
+        const bool was_mixed = c->mixed;
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        for (int cand = 0; cand < 3; ++cand) {
+            const bool mixed = cand > 0;
+            if (mixed && !c->d_Om32) TRY(alloc_mixed(c));
+            c->nb32 = (cand == 1) ? 64 : 128;
+            invalidate_graph(c);
+            float total = 0.f;
+            for (int rep = 0; rep < 2; ++rep) {
+                TRY(psdp_load_iterate(c, X.data(), Z.data(), y.data()));
+                cudaEventRecord(a, c->stream);
+                TRY(launch_step(c, mixed));
+                cudaEventRecord(b, c->stream);
+                TRY(sync_check(c));
+                cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream);
+                float t = 0.f;
+                cudaEventElapsedTime(&t, a, b);
+                if (rep == 1) total = t;   // the first repetition captures the graph
+            }
+            ms[cand] = total;
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        best = 0;
+        for (int cand = 1; cand < 3; ++cand)
+            if (ms[cand] < ms[best]) best = cand;
+        c->mixed = was_mixed;
+        TRY(psdp_load_iterate(c, X.data(), Z.data(), y.data()));
+        if (cache_path) {
+            if (FILE* f = fopen(cache_path, "a")) {
+                fprintf(f, "%s|%d %.4f %.4f %.4f\n", key, best, ms[0], ms[1], ms[2]);
+                fclose(f);
+            }
+        }
+    }
+    if (best > 0 && !c->d_Om32) TRY(alloc_mixed(c));
+    c->mixed = best > 0;
+    c->mixed_failed = false;
+    c->nb32 = (best == 1) ? 64 : 128;
+    invalidate_graph(c);
+    if (choice) *choice = best;
+    if (ms_out) memcpy(ms_out, ms, sizeof ms);
+    return PSDP_OK;
 }
 
 psdp_status psdp_certify(psdp_ctx* c, int* verdict, double* minP, double* maxL) {

@@ -38,6 +38,7 @@ enum FlagBits {
     FL_NAN = 4,
     FL_TIMEOUT = 8,
     FL_MIXED = 16,     // mixed-precision solve did not reach its residual target
+    FL_FROZEN = 32,    // finished batch member: its graph branch runs but leaves the iterate
 };
 
 struct ProfSite {
