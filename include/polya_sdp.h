@@ -203,6 +203,25 @@ void* psdp_stream(psdp_ctx* c);
  * Errors: EINVAL on bad sizes/flags, ETIMEOUT if a bounded device wait expired. */
 psdp_status psdp_tc_gemm_check(int M, int N, int K, int dtype, int split, const void* A, const void* B, float* C);
 
+/* Allocation-free variant of psdp_tc_gemm_check (dtype 0); the paper has no
+ * counterpart.  For callers that cannot allocate device memory where they need
+ * the product: code inside a CUDA graph capture in global mode, allocator or
+ * pool callbacks, hosts with a fixed device budget.
+ *  A: DEVICE pointer, M x K float32 row-major;  B: DEVICE pointer, N x K;
+ *  C: DEVICE pointer receiving D = A B^T column-major (C[n*M + m]), M*N floats;
+ *  split: 1 (TF32) or 3 (3xTF32);  stream: cudaStream_t (NULL = legacy stream).
+ * The scratch (padded, TF32-split copies of A and B) is one static device array
+ * of 8 MiB + 256 B that every GPU loading the library holds until exit, so
+ * (M + N) * Kpad must not exceed 2^20, Kpad = K rounded up to 64: larger sizes
+ * give EINVAL.  Nothing is allocated: no cudaMalloc/cudaFree, no allocating
+ * library routine.  The first call on a device resolves the array's device
+ * address and sets the GEMM kernel's shared-memory limit: make it before any
+ * stream capture.  Every call shares the array and the call returns after the
+ * product is complete on `stream`; calls that overlap on the GPU (other host
+ * threads, other streams) race.  Errors: EINVAL, ECUDA, ETIMEOUT (bounded wait). */
+psdp_status psdp_tc_gemm_noalloc(int M, int N, int K, int split, const float* A, const float* B, float* C,
+                                 void* stream);
+
 /* Measure this GPU's FP64 FMA throughput with a short dependent-chain kernel;
  * *tflops receives FP64 TFLOP/s (2 flops per FMA). */
 psdp_status psdp_fp64_peak(int device, double* tflops);

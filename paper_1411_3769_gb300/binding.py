@@ -29,7 +29,7 @@ EXPORTS = ("psdp_default_opts", "psdp_setup", "psdp_sizes", "psdp_step", "psdp_s
            "psdp_get_iterate", "psdp_get_schur", "psdp_apply_BT", "psdp_apply_B", "psdp_profile_enable",
            "psdp_profile_reset", "psdp_profile_get", "psdp_work", "psdp_stream", "psdp_fp64_peak",
            "psdp_destroy", "psdp_strerror", "psdp_tc_gemm_check", "psdp_get_schur_mixed",
-           "psdp_solve_batch", "psdp_autotune")
+           "psdp_tc_gemm_noalloc", "psdp_solve_batch", "psdp_autotune")
 
 
 class Opts(C.Structure):
@@ -83,6 +83,7 @@ def _lib():
             "psdp_strerror": (C.c_char_p, [C.c_int]),
             "psdp_tc_gemm_check": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp]),
             "psdp_get_schur_mixed": (C.c_int, [vp, vp]),
+            "psdp_tc_gemm_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]),
             "psdp_solve_batch": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
             "psdp_autotune": (C.c_int, [vp, C.c_char_p, C.POINTER(C.c_int), dp]),
         }
@@ -273,6 +274,12 @@ def psdp_tc_gemm_check(A: np.ndarray, B: np.ndarray, split: int = 1) -> np.ndarr
     _check(_lib().psdp_tc_gemm_check(M, N, K, dtype, split, A.ctypes.data, B.ctypes.data, C_.ctypes.data),
            "psdp_tc_gemm_check")
     return C_.T
+
+
+def psdp_tc_gemm_noalloc(M: int, N: int, K: int, split: int, A_ptr: int, B_ptr: int, C_ptr: int,
+                         stream: int = 0) -> int:
+    """Device pointers in and out; returns the status code (no allocation inside)."""
+    return _lib().psdp_tc_gemm_noalloc(M, N, K, split, A_ptr, B_ptr, C_ptr, stream or None)
 
 
 def psdp_solve_batch(handles) -> tuple[list[str], list[int]]:
