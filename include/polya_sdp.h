@@ -148,6 +148,36 @@ psdp_status psdp_grid_check(psdp_ctx* c, int N, double* minP, double* maxQ);
 psdp_status psdp_get_P(psdp_ctx* c, double* P);
 psdp_status psdp_get_y(psdp_ctx* c, double* y);
 
+/* Warm start (no counterpart in the paper, whose start is X = Z = I, y = 0):
+ * y = y0 (K doubles), X_gamma = xscale[gamma] I ((L+M) positive doubles; NULL
+ * means 1), and Z_gamma = B^T(y0)_gamma - C_gamma lifted by a multiple of I so
+ * that its smallest eigenvalue is at least theta / xscale[gamma] (theta > 0),
+ * which keeps the start strictly interior.  Resets the iteration count.
+ * Errors: EINVAL for non-finite y0, non-positive scalings or theta. */
+psdp_status psdp_set_start(psdp_ctx* c, const double* y0, const double* xscale, double theta);
+
+/* The learned warm-start network (no counterpart in the paper): a three-layer
+ * ReLU MLP n_in -> width -> width -> n_out whose products all run on the tensor
+ * cores with BF16 operands and FP32 accumulation; Adam on FP32 master weights.
+ * Host arrays are row-major float32 batches (one sample per row). */
+typedef struct psdp_mlp psdp_mlp;
+/* n_in, width, max_batch multiples of 8; He-normal weights from `seed`. */
+psdp_status psdp_mlp_create(int n_in, int width, int n_out, int max_batch, uint64_t seed, int device, psdp_mlp** out);
+void psdp_mlp_destroy(psdp_mlp* m);
+/* Parameters as one float32 array W1 (width x n_in), b1, W2, b2, W3 (n_out x width), b3;
+ * *count receives its length.  get / set may be NULL. */
+psdp_status psdp_mlp_params(psdp_mlp* m, float* get, const float* set, int64_t* count);
+/* Loss mean((Y - T)^2) and its gradients (layout of psdp_mlp_params) on one batch
+ * of B <= max_batch raw (unstandardised) samples: the gradient-check hook. */
+psdp_status psdp_mlp_grads(psdp_mlp* m, const float* X, const float* T, int B, float* loss, float* grads);
+/* Adam training on n samples for `epochs` passes of batches of B (multiple of 8):
+ * inputs and targets are standardised per feature with statistics of this set,
+ * kept for psdp_mlp_predict; *final_loss = mean standardised loss of the last epoch. */
+psdp_status psdp_mlp_train(psdp_mlp* m, const float* X, const float* T, int n, int epochs, int B, float lr,
+                           uint64_t seed, float* final_loss);
+/* Y (n x n_out) in target units. */
+psdp_status psdp_mlp_predict(psdp_mlp* m, const float* X, int n, float* Y);
+
 /* The integer Polya tables: beta (L0 x L, row h) and c (L0 x M x N_a) with
  * H_{h,gamma} = sum_lambda c[h][gamma][lambda] A_lambda. */
 psdp_status psdp_get_tables(psdp_ctx* c, int32_t* beta, int32_t* cH);

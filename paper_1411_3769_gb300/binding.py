@@ -29,7 +29,8 @@ EXPORTS = ("psdp_default_opts", "psdp_setup", "psdp_sizes", "psdp_step", "psdp_s
            "psdp_get_iterate", "psdp_get_schur", "psdp_apply_BT", "psdp_apply_B", "psdp_profile_enable",
            "psdp_profile_reset", "psdp_profile_get", "psdp_work", "psdp_stream", "psdp_fp64_peak",
            "psdp_destroy", "psdp_strerror", "psdp_tc_gemm_check", "psdp_get_schur_mixed",
-           "psdp_tc_gemm_noalloc", "psdp_solve_batch", "psdp_autotune")
+           "psdp_tc_gemm_noalloc", "psdp_solve_batch", "psdp_autotune", "psdp_set_start", "psdp_mlp_create",
+           "psdp_mlp_destroy", "psdp_mlp_params", "psdp_mlp_grads", "psdp_mlp_train", "psdp_mlp_predict")
 
 
 class Opts(C.Structure):
@@ -86,6 +87,14 @@ def _lib():
             "psdp_tc_gemm_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]),
             "psdp_solve_batch": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
             "psdp_autotune": (C.c_int, [vp, C.c_char_p, C.POINTER(C.c_int), dp]),
+            "psdp_set_start": (C.c_int, [vp, dp, dp, C.c_double]),
+            "psdp_mlp_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int, C.POINTER(vp)]),
+            "psdp_mlp_destroy": (None, [vp]),
+            "psdp_mlp_params": (C.c_int, [vp, vp, vp, C.POINTER(C.c_int64)]),
+            "psdp_mlp_grads": (C.c_int, [vp, vp, vp, C.c_int, C.POINTER(C.c_float), vp]),
+            "psdp_mlp_train": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_float, C.c_uint64,
+                                         C.POINTER(C.c_float)]),
+            "psdp_mlp_predict": (C.c_int, [vp, vp, C.c_int, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -297,6 +306,63 @@ def psdp_autotune(h, cache_path: str | None = None) -> tuple[int, np.ndarray]:
     _check(_lib().psdp_autotune(h, cache_path.encode() if cache_path else None, C.byref(ch), _dp(ms)),
            "psdp_autotune")
     return ch.value, ms
+
+
+def psdp_set_start(h, y0: np.ndarray, xscale: np.ndarray | None, theta: float):
+    y0 = np.ascontiguousarray(y0, dtype=np.float64)
+    xs = None if xscale is None else np.ascontiguousarray(xscale, dtype=np.float64)
+    _check(_lib().psdp_set_start(h, _dp(y0), _dp(xs) if xs is not None else None, theta), "psdp_set_start")
+
+
+def _fp(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def psdp_mlp_create(n_in: int, width: int, n_out: int, max_batch: int, seed: int = 0, device: int = 0):
+    h = C.c_void_p()
+    _check(_lib().psdp_mlp_create(n_in, width, n_out, max_batch, seed, device, C.byref(h)), "psdp_mlp_create")
+    return h
+
+
+def psdp_mlp_destroy(h):
+    if h:
+        _lib().psdp_mlp_destroy(h)
+
+
+def psdp_mlp_params(h, set_to: np.ndarray | None = None) -> np.ndarray:
+    cnt = C.c_int64(0)
+    _check(_lib().psdp_mlp_params(h, None, None, C.byref(cnt)), "psdp_mlp_params")
+    out = np.zeros(cnt.value, dtype=np.float32)
+    src = None if set_to is None else np.ascontiguousarray(set_to, dtype=np.float32)
+    _check(_lib().psdp_mlp_params(h, _fp(out), _fp(src) if src is not None else None, None), "psdp_mlp_params")
+    return out
+
+
+def psdp_mlp_grads(h, X: np.ndarray, T: np.ndarray) -> tuple[float, np.ndarray]:
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    T = np.ascontiguousarray(T, dtype=np.float32)
+    cnt = C.c_int64(0)
+    _check(_lib().psdp_mlp_params(h, None, None, C.byref(cnt)), "psdp_mlp_params")
+    g = np.zeros(cnt.value, dtype=np.float32)
+    loss = C.c_float(0.0)
+    _check(_lib().psdp_mlp_grads(h, _fp(X), _fp(T), X.shape[0], C.byref(loss), _fp(g)), "psdp_mlp_grads")
+    return float(loss.value), g
+
+
+def psdp_mlp_train(h, X: np.ndarray, T: np.ndarray, epochs: int, batch: int, lr: float, seed: int = 0) -> float:
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    T = np.ascontiguousarray(T, dtype=np.float32)
+    loss = C.c_float(0.0)
+    _check(_lib().psdp_mlp_train(h, _fp(X), _fp(T), X.shape[0], epochs, batch, lr, seed, C.byref(loss)),
+           "psdp_mlp_train")
+    return float(loss.value)
+
+
+def psdp_mlp_predict(h, X: np.ndarray, n_out: int) -> np.ndarray:
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    Y = np.zeros((X.shape[0], n_out), dtype=np.float32)
+    _check(_lib().psdp_mlp_predict(h, _fp(X), X.shape[0], _fp(Y)), "psdp_mlp_predict")
+    return Y
 
 
 def psdp_destroy(h):

@@ -1040,6 +1040,25 @@ psdp_status psdp_load_iterate(psdp_ctx* c, const double* X, const double* Z, con
     return refresh(c);
 }
 
+psdp_status psdp_set_start(psdp_ctx* c, const double* y0, const double* xscale, double theta) {
+    if (!c || !y0 || !(theta > 0.0) || !std::isfinite(theta)) return PSDP_EINVAL;
+    for (int k = 0; k < c->K; ++k)
+        if (!std::isfinite(y0[k])) return PSDP_EINVAL;
+    if (xscale)
+        for (int g = 0; g < c->nblk; ++g)
+            if (!(xscale[g] > 0.0) || !std::isfinite(xscale[g])) return PSDP_EINVAL;
+    cudaSetDevice(c->device);
+    cudaStream_t st = c->stream;
+    cudaMemcpyAsync(c->d_y, y0, (size_t)c->K * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (xscale) cudaMemcpyAsync(c->d_tstep, xscale, (size_t)c->nblk * sizeof(double), cudaMemcpyHostToDevice, st);
+    launch_bt(st, c, c->d_y, c->d_T1);
+    launch_block_mineig(st, c->nblk, c->n, c->d_T1, 1.0, c->d_part);
+    launch_start_fix(st, c, c->d_T1, c->d_part, xscale ? c->d_tstep : nullptr, theta);
+    c->iters = 0;
+    c->mixed_failed = false;
+    return refresh(c);
+}
+
 psdp_status psdp_get_iterate(psdp_ctx* c, double* X, double* Z, double* y) {
     if (!c) return PSDP_EINVAL;
     cudaSetDevice(c->device);

@@ -106,10 +106,11 @@ k_potrf_diag32x4(double* A, int K, int j0, int w, int nb, double* Linv, int* fla
         }
         if (tid > j && tid < 32) L[j * LD + tid] *= ri;
         __syncthreads();
-        const int m = 31 - j;
-        for (int idx = tid; idx < m * m; idx += 128) {
-            const int c = j + 1 + idx / m, r = j + 1 + idx % m;
-            if (r >= c) L[c * LD + r] = fma(-L[j * LD + r], L[j * LD + c], L[c * LD + r]);
+        // trailing lower triangle: the four warps take columns, lanes take rows
+        for (int c = j + 1 + (tid >> 5); c < 32; c += 4) {
+            const double ljc = L[j * LD + c];
+            const int r = tid & 31;
+            if (r >= c) L[c * LD + r] = fma(-L[j * LD + r], ljc, L[c * LD + r]);
         }
         __syncthreads();
     }

@@ -112,22 +112,57 @@ k_potrf_diag32(float* A, int K, int j0, int w, int nb, float* Linv, int* flag) {
         }
         for (int i = j + 1 + threadIdx.x; i < w; i += blockDim.x) L[j * ld + i] *= ri;
         __syncthreads();
-        const int m = w - j - 1;
-        for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-            const int c = j + 1 + idx / m, r = j + 1 + idx % m;
-            if (r >= c) L[c * ld + r] = fmaf(-L[j * ld + r], L[j * ld + c], L[c * ld + r]);
+        // trailing lower triangle: warps take columns, lanes take rows
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int c = j + 1 + wid; c < w; c += nw) {
+            const float ljc = L[j * ld + c];
+            for (int r = c + lane; r < w; r += 32) L[c * ld + r] = fmaf(-L[j * ld + r], ljc, L[c * ld + r]);
         }
         __syncthreads();
     }
-    for (int c = threadIdx.x; c < w; c += blockDim.x) {
-        for (int r = 0; r < c; ++r) I[c * ld + r] = 0.f;
-        for (int r = c; r < w; ++r) {
-            float s = (r == c) ? 1.f : 0.f;
-            for (int k = c; k < r; ++k) s = fmaf(-L[k * ld + r], I[c * ld + k], s);
-            I[c * ld + r] = s * rinv[r];
+    // L^{-1} by 32 x 32 blocks: diagonal blocks by forward substitution (one
+    // thread per column, all blocks at once), then block row i of column j from
+    // X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj, one block diagonal per level.
+    for (int idx = threadIdx.x; idx < w * ld; idx += blockDim.x) I[idx] = 0.f;
+    __syncthreads();
+    const int nbk = (w + 31) / 32;
+    if (threadIdx.x < nbk * 32) {
+        const int d = threadIdx.x >> 5, c = threadIdx.x;
+        const int hi = min(w, d * 32 + 32);
+        if (c < w) {
+            for (int r = c; r < hi; ++r) {
+                float s = (r == c) ? 1.f : 0.f;
+                for (int k = c; k < r; ++k) s = fmaf(-L[k * ld + r], I[c * ld + k], s);
+                I[c * ld + r] = s * rinv[r];
+            }
         }
     }
     __syncthreads();
+    __shared__ float Tb[3][32][33];
+    for (int lev = 1; lev < nbk; ++lev) {
+        const int npair = nbk - lev;
+        for (int idx = threadIdx.x; idx < npair * 1024; idx += blockDim.x) {
+            const int q = idx >> 10, e = idx & 1023, rr = e >> 5, cc = e & 31;
+            const int bj = q, bi = q + lev;
+            const int r = bi * 32 + rr, c = bj * 32 + cc;
+            float s = 0.f;
+            if (r < w && c < w)
+                for (int k = c; k < bi * 32; ++k) s = fmaf(L[k * ld + r], I[c * ld + k], s);
+            Tb[q][rr][cc] = s;
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < npair * 1024; idx += blockDim.x) {
+            const int q = idx >> 10, e = idx & 1023, rr = e >> 5, cc = e & 31;
+            const int bi = q + lev;
+            const int r = bi * 32 + rr, c = q * 32 + cc;
+            if (r < w && c < w) {
+                float s = 0.f;
+                for (int k = 0; k <= rr; ++k) s = fmaf(I[(bi * 32 + k) * ld + r], Tb[q][k][cc], s);
+                I[c * ld + r] = -s;
+            }
+        }
+        __syncthreads();
+    }
     for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
         const int j = idx / w, i = idx % w;
         if (i >= j) A[(int64_t)(j0 + j) * K + j0 + i] = (i == j) ? ldiag[j] : L[j * ld + i];

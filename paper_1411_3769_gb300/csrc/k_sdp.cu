@@ -536,6 +536,23 @@ __global__ void k_grid_build(int l, int n, int Nt, int L0, int Na, int N, int64_
     }
 }
 
+// Warm start: Z_g = (B^T(y0) - C)_g + max(0, theta / x_g - lambda_min) I (the
+// block's smallest eigenvalue is eig[2g]), X_g = x_g I.
+__global__ void k_start_fix(int nb, int n, const double* __restrict__ cdiag, const double* __restrict__ BTy,
+                            const double* __restrict__ eig, const double* __restrict__ xs, double theta, double* X,
+                            double* Z) {
+    const int64_t n2 = (int64_t)n * n, total = n2 * nb;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int g = (int)(t / n2), e = (int)(t % n2);
+        const bool diag = (e / n == e % n);
+        const double x = xs ? xs[g] : 1.0;
+        const double lam = eig[2 * g] - cdiag[g];
+        const double shift = fmax(0.0, theta / x - lam);
+        Z[t] = BTy[t] - (diag ? cdiag[g] - shift : 0.0);
+        X[t] = diag ? x : 0.0;
+    }
+}
+
 int grid_for(int64_t total) {
     int64_t b = (total + kThreads - 1) / kThreads;
     if (b > 65535 * 8) b = 65535 * 8;
@@ -658,6 +675,12 @@ void launch_schur_gather32(cudaStream_t st, psdp_ctx* c, int p0, int np, const f
     dim3 g(c->Nt, np);
     k_schur_gather<float><<<g, kThreads, sm, st>>>(c->n, c->Nt, c->K, p0, c->d_pair_a, c->d_pair_b, c->d_svec, T,
                                                    Om);
+}
+
+void launch_start_fix(cudaStream_t st, psdp_ctx* c, const double* BTy, const double* eig, const double* xs,
+                      double theta) {
+    k_start_fix<<<grid_for((int64_t)c->nblk * c->n2), kThreads, 0, st>>>(c->nblk, c->n, c->d_cdiag, BTy, eig, xs,
+                                                                        theta, c->d_X, c->d_Z);
 }
 
 void launch_certify_finalize(cudaStream_t st, int count, int n, const double* eig, int L, double* out) {

@@ -207,14 +207,27 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtens
         }
     }
     __syncwarp();
-    // epilogue: every warp drains its 32 TMEM lanes (rows m0 + 32*warp + lane)
+    // epilogue: every warp drains its 32 TMEM lanes (rows m0 + 32*warp + lane).
+    // With beta != 0 the thread's 128 old C values are loaded before waiting for
+    // the accumulator, so their latency overlaps the tail of the main loop
+    // instead of being paid once per column.
+    const int m = m0 + 32 * warp + lane;
+    float* Cb = C + (int64_t)b * c_batch;
+    float old[BN];
+#pragma unroll
+    for (int j = 0; j < BN; ++j) old[j] = 0.f;
+    if (beta != 0.f && m < M) {
+#pragma unroll
+        for (int j = 0; j < BN; ++j) {
+            const int n = n0 + j;
+            if (n < N) old[j] = Cb[(int64_t)n * ldc + m];
+        }
+    }
     bool ok = true;
     if (nk > 0) ok = mbar_wait(accb, 0, flag);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int m = m0 + 32 * warp + lane;
-    float* Cb = C + (int64_t)b * c_batch;
     if (ok) {
-#pragma unroll 1
+#pragma unroll
         for (int c0 = 0; c0 < BN; c0 += 16) {
             uint32_t r[16];
             if (nk > 0) {
@@ -227,12 +240,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtens
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int n = n0 + c0 + j;
-                    if (n < N) {
-                        float* p = Cb + (int64_t)n * ldc + m;
-                        float v = alpha * __uint_as_float(r[j]);
-                        if (beta != 0.f) v += beta * (*p);
-                        *p = v;
-                    }
+                    if (n < N) Cb[(int64_t)n * ldc + m] = alpha * __uint_as_float(r[j]) + beta * old[c0 + j];
                 }
             }
         }

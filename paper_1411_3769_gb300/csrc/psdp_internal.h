@@ -212,6 +212,11 @@ void init_attrs_linalg(int smem_max);
 void init_attrs_sdp(int smem_max);
 void init_attrs_dense(int smem_max);
 
+// warm start: X_g = xs_g I, Z_g = B^T(y0)_g - C_g lifted to lambda_min >= theta / xs_g
+// (eig[2g] = lambda_min of B^T(y0)_g, computed beforehand)
+void launch_start_fix(cudaStream_t st, psdp_ctx* c, const double* BTy, const double* eig, const double* xs,
+                      double theta);
+
 // certificate / grid
 void launch_certify_finalize(cudaStream_t st, int count, int n, const double* eig, int L, double* out);
 void launch_grid_build(cudaStream_t st, psdp_ctx* c, int N, int64_t first, int cnt, double* P, double* Aal);

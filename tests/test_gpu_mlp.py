@@ -1,0 +1,102 @@
+"""BF16 tensor-core MLP against the FP64 oracle MLP, and the learned warm start.
+
+Gradient tolerance: the GPU multiplies BF16 operands (8 significant bits) and
+rounds each hidden activation and back-propagated gradient to BF16 before the
+next product, so per-tensor relative errors of a few 2^-8 are expected: bound
+3e-2 in the Frobenius norm, against the oracle fed the same BF16-rounded
+weights and inputs.  The warm start must keep every verdict of the cold solve
+and, on average, take fewer interior-point iterations.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bd():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1411_3769_gb300 import build
+    build.build()
+    from paper_1411_3769_gb300 import binding
+    binding._lib()
+    return binding
+
+
+def _bf16(x):
+    u = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _unflat(flat, sizes):
+    out, off = [], 0
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        W = flat[off:off + a * b].reshape(b, a)
+        off += a * b
+        bb = flat[off:off + b]
+        off += b
+        out.append([W, bb])
+    return out
+
+
+@pytest.mark.parametrize("sizes,B", [((16, 32, 32, 10), 8), ((64, 128, 128, 37), 40)])
+def test_gradients_match_oracle(bd, sizes, B):
+    n_in, width, _, n_out = sizes
+    h = bd.psdp_mlp_create(n_in, width, n_out, max(B, 8), seed=3)
+    try:
+        rng = np.random.default_rng(4)
+        X = rng.normal(size=(B, n_in)).astype(np.float32)
+        T = rng.normal(size=(B, n_out)).astype(np.float32)
+        flat = bd.psdp_mlp_params(h).astype(np.float64)
+        loss, g = bd.psdp_mlp_grads(h, X, T)
+        params = _unflat(flat, sizes)
+        for p in params:
+            p[0] = _bf16(p[0])
+        Y, cache = omlp.forward(params, _bf16(X))
+        ref = omlp.backward(params, cache, Y, T.astype(np.float64))
+        assert abs(loss - omlp.loss(Y, T)) <= 3e-2 * omlp.loss(Y, T)
+        gp = _unflat(g.astype(np.float64), sizes)
+        for (gw, gb), (rw, rb) in zip(gp, ref):
+            assert np.linalg.norm(gw - rw) <= 3e-2 * np.linalg.norm(rw) + 1e-6
+            assert np.linalg.norm(gb - rb) <= 3e-2 * np.linalg.norm(rb) + 1e-6
+    finally:
+        bd.psdp_mlp_destroy(h)
+
+
+def test_training_reduces_loss(bd):
+    rng = np.random.default_rng(5)
+    Wt = rng.normal(size=(24, 16))
+    X = rng.normal(size=(512, 16)).astype(np.float32)
+    T = np.tanh(X @ Wt.T).astype(np.float32)
+    h = bd.psdp_mlp_create(16, 64, 24, 64, seed=1)
+    try:
+        l1 = bd.psdp_mlp_train(h, X, T, epochs=1, batch=64, lr=1e-3)
+        l2 = bd.psdp_mlp_train(h, X, T, epochs=60, batch=64, lr=1e-3)
+        assert l2 < 0.3 * l1
+        Y = bd.psdp_mlp_predict(h, X[:50], 24)
+        assert np.mean((Y - T[:50]) ** 2) < 0.3 * np.mean(T[:50] ** 2)
+    finally:
+        bd.psdp_mlp_destroy(h)
+
+
+def test_warm_start_keeps_verdicts_and_saves_iterations(bd):
+    from paper_1411_3769_gb300 import warmstart as ws
+    n, l, d_p, d1 = 6, 2, 1, 1
+    train_sys = ws.draw(96, n, l, (0.1, 0.8), base_seed=100)
+    test_sys = ws.draw(12, n, l, (0.1, 0.8), base_seed=900)
+    F, T, status, iters, verdicts = ws.solve_family(train_sys, d_p, d1)
+    ok = np.array([s == "OK" for s in status])
+    assert ok.sum() >= 48
+    m, loss = ws.train(F[ok], T[ok], width=128, epochs=300, batch=16, lr=1e-3)
+    try:
+        res = ws.evaluate(m, test_sys, d_p, d1)
+    finally:
+        bd.psdp_mlp_destroy(m)
+    assert res["verdicts_agree"]
+    assert res["warm_iters"] < res["cold_iters"]
