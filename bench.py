@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--mixed", type=int, default=1, help="also measure the mixed-precision path")
     ap.add_argument("--mixed-steps", type=int, default=5)
+    ap.add_argument("--extra", action="store_true", help="measure the batched and warm-start rows instead")
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--warm-train", type=int, default=1024)
+    ap.add_argument("--warm-test", type=int, default=64)
     return ap.parse_args()
 
 
@@ -170,6 +174,70 @@ def measure_mixed(bd, synth, name, device, nsteps):
             "pcg_iterations_last_step": info["refine_sweeps"], "schur_flops_per_step": work["schur_flops"],
             "chol_flops_per_step": work["chol_flops"],
             "kernels_ms_per_step": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in prof.items()}}
+
+
+def measure_batch(bd, synth, count, device, n_range=(8, 48), precision=1):
+    """Uneven instances drawn like the batched workload (n ~ U{8..48}, l ~ U{2,3,4},
+    d_p ~ U{1,2}, d1 ~ U{1..4}, s ~ U[0.05, 3]) solved together in one batch graph
+    per iteration; set-up, solve and certificates all timed."""
+    inst = synth.batch_instances(count, base_seed=1000, n_range=n_range)
+    t0 = time.perf_counter()
+    hs = [bd.psdp_setup(d["n"], d["l"], d["d_p"], d["d1"], d["A"],
+                        bd.psdp_default_opts(precision=precision, device=device)) for d in inst]
+    t1 = time.perf_counter()
+    try:
+        status, iters = bd.psdp_solve_batch(hs)
+        t2 = time.perf_counter()
+        verdicts = [bd.psdp_certify(h)[0] for h in hs]
+        t3 = time.perf_counter()
+    finally:
+        for h in hs:
+            bd.psdp_destroy(h)
+    Ks = [polya_K(d) for d in inst]
+    return {"instances": count, "n_range": list(n_range), "precision": "mixed" if precision else "fp64",
+            "newton_steps_total": int(sum(iters)), "steps_per_s": sum(iters) / (t2 - t1),
+            "setup_s": t1 - t0, "solve_s": t2 - t1, "certify_s": t3 - t2, "time_to_all_certificates_s": t3 - t0,
+            "certified": int(sum(verdicts)), "status_counts": {s: status.count(s) for s in sorted(set(status))},
+            "K_max": max(Ks), "K_mean": float(np.mean(Ks))}
+
+
+def polya_K(d):
+    from math import comb
+    return comb(d["d_p"] + d["l"] - 1, d["l"] - 1) * d["n"] * (d["n"] + 1) // 2
+
+
+def measure_warm(bd, n_train, n_test, device):
+    """Learned warm start on the n=32, l=3, d_p=2, d1=3 family, s ~ U[0.1, 1.5]."""
+    from paper_1411_3769_gb300 import warmstart as ws
+    n, l, d_p, d1 = 32, 3, 2, 3
+    t0 = time.perf_counter()
+    train_sys = ws.draw(n_train, n, l, (0.1, 1.5), base_seed=5000)
+    test_sys = ws.draw(n_test, n, l, (0.1, 1.5), base_seed=9000)
+    F, T, status, iters, verdicts = ws.solve_family(train_sys, d_p, d1)
+    t1 = time.perf_counter()
+    ok = np.array([s == "OK" for s in status])
+    m, loss = ws.train(F[ok], T[ok], width=1024, epochs=200, batch=64, lr=1e-3)
+    t2 = time.perf_counter()
+    try:
+        res = ws.evaluate(m, test_sys, d_p, d1)
+    finally:
+        bd.psdp_mlp_destroy(m)
+    res.update(train_instances=int(ok.sum()), train_generate_s=t1 - t0, train_s=t2 - t1, final_train_loss=loss,
+               family="n=32 l=3 d_p=2 d1=d2=3 s~U[0.1,1.5]")
+    return res
+
+
+def run_extra(args):
+    """Batched and learned-warm-start rows (minutes of GPU time; not the default line)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1411_3769_gb300 import build
+    build.build()
+    from paper_1411_3769_gb300 import binding as bd
+    from paper_1411_3769_gb300 import synth
+    out = {"batch": measure_batch(bd, synth, args.batch_count, 0)}
+    out["warm_start"] = measure_warm(bd, args.warm_train, args.warm_test, 0)
+    print(json.dumps(out), flush=True)
 
 
 def run_reference(args):
@@ -353,6 +421,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.extra:
+        run_extra(args)
     else:
         run_ours(args)
 

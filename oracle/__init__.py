@@ -16,6 +16,8 @@ Polya's Theorem" (IEEE TAC 2013):
                  Sec. IV-A and Algorithm 2, with the Schur complement computed
                  from its definition (literal) or from the block formula.
 * ``certify`` -- the stability certificate of Theorems 1 and 2.
+* ``mlp``     -- the FP64 reference of the learned warm-start network (not in
+                 the paper): a three-layer ReLU MLP, MSE loss and Adam.
 
 Every floating-point computation is numpy float64.  The oracle shares no code
 with the CUDA library; the only module both sides use is the seeded input

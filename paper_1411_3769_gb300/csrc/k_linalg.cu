@@ -102,47 +102,64 @@ k_bgemm(int n, int count, const double* __restrict__ A, const int32_t* __restric
 
 // ------------------------------------------------------------------ TN GEMM
 // C[r][c] = alpha * sum_k A[k*lda + r] * B[k*ldb + c] + beta * C[r*ldc + c]
-constexpr int TM = 64, TK = 16;
+// Tiles of TM x TN outputs on a 16 x 16 thread grid (micro-tiles of
+// TM/16 x TN/16), k-slabs of 16 double-buffered through shared memory.  With
+// beta != 0 the old C values are loaded before the main loop.
+constexpr int TK = 16;
 
+template <int TM, int TN>
 __global__ void __launch_bounds__(kThreads)
 k_gemm_tn(int m, int ncol, const double* __restrict__ A, int lda, const int32_t* __restrict__ a_off, int64_t a_stride,
           const double* __restrict__ B, int ldb, const int32_t* __restrict__ b_off, int64_t b_stride,
           const int32_t* __restrict__ kd, int kd_uniform, double* C, int ldc, int64_t c_stride,
           double alpha, double beta, int tri) {
+    constexpr int MI = TM / 16, NJ = TN / 16, QA = TK * TM / kThreads, QB = TK * TN / kThreads;
     const int tr = blockIdx.y, tcn = blockIdx.x;
-    if (tri && tcn < tr) return;
+    const int r0 = tr * TM, c0 = tcn * TN;
+    if (tri && c0 + TN <= r0) return;     // tile entirely above the diagonal of the [r][c] view
     const int bz = blockIdx.z;
     const double* Ab = A + (a_off ? (int64_t)a_off[bz] : bz * a_stride);
     const double* Bb = B + (b_off ? (int64_t)b_off[bz] : bz * b_stride);
     double* Cb = C + bz * c_stride;
     const int K = kd ? kd[bz] : kd_uniform;
-    const int r0 = tr * TM, c0 = tcn * TM;
     __shared__ double As[2][TK][TM];
-    __shared__ double Bs[2][TK][TM];
+    __shared__ double Bs[2][TK][TN];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    double acc[4][4];
+    double acc[MI][NJ], old[MI][NJ];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < MI; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-    // each thread stages 4 elements of A and 4 of B per k-slab
-    double ra[4], rb[4];
+        for (int j = 0; j < NJ; ++j) {
+            acc[i][j] = 0.0;
+            old[i][j] = 0.0;
+            const int r = r0 + ty + 16 * i, cc = c0 + tx + 16 * j;
+            if (beta != 0.0 && r < m && cc < ncol) old[i][j] = Cb[(int64_t)r * ldc + cc];
+        }
+    double ra[QA], rb[QB];
     auto fetch = [&](int k0) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < QA; ++q) {
             const int idx = threadIdx.x + q * kThreads;
-            const int kk = idx / TM, rr = idx % TM;
-            const int k = k0 + kk;
+            const int kk = idx / TM, rr = idx % TM, k = k0 + kk;
             ra[q] = (k < K && r0 + rr < m) ? Ab[(int64_t)k * lda + r0 + rr] : 0.0;
-            rb[q] = (k < K && c0 + rr < ncol) ? Bb[(int64_t)k * ldb + c0 + rr] : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < QB; ++q) {
+            const int idx = threadIdx.x + q * kThreads;
+            const int kk = idx / TN, cc = idx % TN, k = k0 + kk;
+            rb[q] = (k < K && c0 + cc < ncol) ? Bb[(int64_t)k * ldb + c0 + cc] : 0.0;
         }
     };
     auto stash = [&](int buf) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < QA; ++q) {
             const int idx = threadIdx.x + q * kThreads;
             As[buf][idx / TM][idx % TM] = ra[q];
-            Bs[buf][idx / TM][idx % TM] = rb[q];
+        }
+#pragma unroll
+        for (int q = 0; q < QB; ++q) {
+            const int idx = threadIdx.x + q * kThreads;
+            Bs[buf][idx / TN][idx % TN] = rb[q];
         }
     };
     int buf = 0;
@@ -156,31 +173,26 @@ k_gemm_tn(int m, int ncol, const double* __restrict__ A, int lda, const int32_t*
         if (more) fetch(k0 + TK);
 #pragma unroll
         for (int kk = 0; kk < TK; ++kk) {
-            double a[4], b[4];
+            double a[MI], b[NJ];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][ty + 16 * i];
+            for (int i = 0; i < MI; ++i) a[i] = As[buf][kk][ty + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[buf][kk][tx + 16 * j];
+            for (int j = 0; j < NJ; ++j) b[j] = Bs[buf][kk][tx + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < MI; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < NJ; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
         if (more) stash(buf ^ 1);
         __syncthreads();
         buf ^= 1;
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < MI; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < NJ; ++j) {
             const int r = r0 + ty + 16 * i, cc = c0 + tx + 16 * j;
-            if (r < m && cc < ncol) {
-                double* p = Cb + (int64_t)r * ldc + cc;
-                double v = alpha * acc[i][j];
-                if (beta != 0.0) v += beta * (*p);
-                *p = v;
-            }
+            if (r < m && cc < ncol) Cb[(int64_t)r * ldc + cc] = alpha * acc[i][j] + beta * old[i][j];
         }
 }
 
@@ -472,9 +484,23 @@ void launch_gemm_tn(cudaStream_t st, int m, int ncol, int batch, const double* A
                     const int32_t* kd, int kd_uniform, double* C, int ldc, int64_t c_stride, double alpha,
                     double beta, int tri) {
     if (m <= 0 || ncol <= 0 || batch <= 0) return;
-    dim3 grid((ncol + TM - 1) / TM, (m + TM - 1) / TM, batch);
-    k_gemm_tn<<<grid, kThreads, 0, st>>>(m, ncol, A, lda, a_off, a_stride, B, ldb, b_off, b_stride, kd, kd_uniform,
-                                         C, ldc, c_stride, alpha, beta, tri);
+    // 64 x 64 tiles when they give a few waves over the SMs; thinner or smaller
+    // problems (panel TRSM with 32 rows, the last trailing updates) take
+    // 32 x 16 / 32 x 32 tiles so more SMs share the work
+    const int64_t big = (int64_t)((ncol + 63) / 64) * ((m + 63) / 64) * batch / (tri ? 2 : 1);
+    if (m <= 32) {
+        dim3 grid((ncol + 15) / 16, (m + 31) / 32, batch);
+        k_gemm_tn<32, 16><<<grid, kThreads, 0, st>>>(m, ncol, A, lda, a_off, a_stride, B, ldb, b_off, b_stride, kd,
+                                                     kd_uniform, C, ldc, c_stride, alpha, beta, tri);
+    } else if (big < 2 * 152) {
+        dim3 grid((ncol + 31) / 32, (m + 31) / 32, batch);
+        k_gemm_tn<32, 32><<<grid, kThreads, 0, st>>>(m, ncol, A, lda, a_off, a_stride, B, ldb, b_off, b_stride, kd,
+                                                     kd_uniform, C, ldc, c_stride, alpha, beta, tri);
+    } else {
+        dim3 grid((ncol + 63) / 64, (m + 63) / 64, batch);
+        k_gemm_tn<64, 64><<<grid, kThreads, 0, st>>>(m, ncol, A, lda, a_off, a_stride, B, ldb, b_off, b_stride, kd,
+                                                     kd_uniform, C, ldc, c_stride, alpha, beta, tri);
+    }
 }
 
 void launch_block_chol_inv(cudaStream_t st, int nb, int n, const double* Z, double* Y, int* flag) {

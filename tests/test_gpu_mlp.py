@@ -1,11 +1,14 @@
 """BF16 tensor-core MLP against the FP64 oracle MLP, and the learned warm start.
 
-Gradient tolerance: the GPU multiplies BF16 operands (8 significant bits) and
-rounds each hidden activation and back-propagated gradient to BF16 before the
-next product, so per-tensor relative errors of a few 2^-8 are expected: bound
-3e-2 in the Frobenius norm, against the oracle fed the same BF16-rounded
-weights and inputs.  The warm start must keep every verdict of the cold solve
-and, on average, take fewer interior-point iterations.
+Gradient tolerances.  The GPU multiplies BF16 operands (8 significant bits)
+and rounds each hidden activation and back-propagated gradient to BF16 before
+the next product.  (1) Against a reference that rounds at exactly those
+points (FP64 otherwise) only the FP32 accumulation order differs: bound 1e-3
+per tensor in the Frobenius norm.  (2) Against the plain FP64 oracle fed the
+same BF16-rounded weights and inputs the roundings themselves show: a few
+2^-8 per element, amplified by cancellation in the sums over the batch (3.2 %
+observed on the 64-128-128-37 net): bound 6e-2.
+The warm start must keep every verdict of the cold solve and, on average, take fewer interior-point iterations.
 """
 
 import numpy as np
@@ -32,6 +35,26 @@ def _bf16(x):
     u = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
     u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _faithful(params, X, T):
+    """Forward/backward in FP64 with BF16 rounding where the GPU rounds."""
+    H = [_bf16(X)]
+    Z = []
+    for i, (W, b) in enumerate(params):
+        z = H[-1] @ _bf16(W).T + b
+        Z.append(z)
+        if i < len(params) - 1:
+            H.append(_bf16(np.maximum(z, 0.0)))
+    g = 2.0 * (Z[-1] - T) / T.size
+    grads = [None] * len(params)
+    for i in range(len(params) - 1, -1, -1):
+        gb = g.sum(axis=0)
+        gq = _bf16(g)
+        grads[i] = [gq.T @ H[i], gb]
+        if i > 0:
+            g = (gq @ _bf16(params[i][0])) * (Z[i - 1] > 0.0)
+    return grads
 
 
 def _unflat(flat, sizes):
@@ -63,8 +86,12 @@ def test_gradients_match_oracle(bd, sizes, B):
         assert abs(loss - omlp.loss(Y, T)) <= 3e-2 * omlp.loss(Y, T)
         gp = _unflat(g.astype(np.float64), sizes)
         for (gw, gb), (rw, rb) in zip(gp, ref):
-            assert np.linalg.norm(gw - rw) <= 3e-2 * np.linalg.norm(rw) + 1e-6
-            assert np.linalg.norm(gb - rb) <= 3e-2 * np.linalg.norm(rb) + 1e-6
+            assert np.linalg.norm(gw - rw) <= 6e-2 * np.linalg.norm(rw) + 1e-6
+            assert np.linalg.norm(gb - rb) <= 6e-2 * np.linalg.norm(rb) + 1e-6
+        fa = _faithful(_unflat(flat, sizes), X.astype(np.float64), T.astype(np.float64))
+        for (gw, gb), (rw, rb) in zip(gp, fa):
+            assert np.linalg.norm(gw - rw) <= 1e-3 * np.linalg.norm(rw) + 1e-7
+            assert np.linalg.norm(gb - rb) <= 1e-3 * np.linalg.norm(rb) + 1e-7
     finally:
         bd.psdp_mlp_destroy(h)
 
