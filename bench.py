@@ -40,7 +40,7 @@ NOMINAL_FP64_TFLOPS = 1.25
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-runs", type=int, default=2)
@@ -63,8 +63,72 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+class NvmlSampler:
+    """SM clock, power and clock-event reasons read through NVML (read-only
+    queries) every 10 ms on a thread; selects the GPU by its PCI bus id."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, device: int):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        ok = False
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(device)
+            bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0".encode()
+            ok = self.lib.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(self.h)) == 0
+        except Exception:
+            ok = False
+        if not ok and self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(device), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("no NVML handle")
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.reasons_fn = fn
+        mx = ctypes.c_uint()
+        self.max_mhz = mx.value if self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0 else None
+        self.rows = []
+        self.stop = threading.Event()
+
+    def _poll(self):
+        ct = self.ct
+        mhz, mw, rs = ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        while not self.stop.is_set():
+            a = self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(mhz))
+            b = self.lib.nvmlDeviceGetPowerUsage(self.h, ct.byref(mw))
+            c = self.reasons_fn(self.h, ct.byref(rs))
+            if a == 0:
+                self.rows.append((mhz.value, mw.value / 1000.0 if b == 0 else None, rs.value if c == 0 else 0))
+            time.sleep(0.01)
+
+    def __enter__(self):
+        self.t = threading.Thread(target=self._poll, daemon=True)
+        self.t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self.stop.set()
+        self.t.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unavailable"], "source": "nvml"}
+        sm = [r[0] for r in self.rows]
+        pw = [r[1] for r in self.rows if r[1] is not None]
+        reasons = sorted({name for r in self.rows for bit, name in self.REASONS.items() if r[2] & bit})
+        return {"sm_mhz": statistics.median(sm), "sm_min_mhz": min(sm), "sm_max_mhz": self.max_mhz,
+                "power_w_median": statistics.median(pw) if pw else None, "reasons": reasons,
+                "samples": len(self.rows), "source": "nvml, 10 ms"}
+
+
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """Clocks and throttle reasons during a timed region: NVML when it loads,
+    else nvidia-smi every 200 ms."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -74,8 +138,14 @@ class ClockSampler:
         self.device = device
         self.rows = []
         self.proc = None
+        self.nvml = None
 
     def __enter__(self):
+        try:
+            self.nvml = NvmlSampler(self.device).__enter__()
+            return self
+        except Exception:
+            self.nvml = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -93,6 +163,8 @@ class ClockSampler:
                 self.rows.append(parts)
 
     def __exit__(self, *exc):
+        if self.nvml:
+            self.nvml.__exit__(*exc)
         if self.proc:
             self.proc.terminate()
             try:
@@ -101,6 +173,8 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        if self.nvml:
+            return self.nvml.summary()
         if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
         sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
@@ -108,7 +182,24 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(self.rows), "source": "nvidia-smi, 200 ms"}
+
+
+def chol_flops(K, nb):
+    """Algorithmic flops of one FP64 Cholesky by kernel: panel solves, updates of
+    the next panel's rows (upper part only) and bulk trailing updates."""
+    out = {"trsm": 0.0, "next": 0.0, "bulk": 0.0}
+    for j0 in range(0, K, nb):
+        wd = min(nb, K - j0)
+        rest = K - j0 - wd
+        if rest <= 0:
+            break
+        w2 = min(nb, rest)
+        out["trsm"] += 2.0 * rest * wd * wd
+        out["next"] += 2.0 * wd * (w2 * rest - w2 * (w2 - 1) / 2)
+        r = rest - w2
+        out["bulk"] += float(r) * (r + 1) * wd
+    return out
 
 
 def oracle_steps(A, w, nsteps):
@@ -130,25 +221,29 @@ def measure_mixed(bd, synth, name, device, nsteps):
     import torch
     w = synth.WORKLOADS[name]
     A = synth.system(w["n"], w["l"], w["s"], 0)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()
     opts = bd.psdp_default_opts(stream=stream.cuda_stream, device=device, precision=1)
     h = bd.psdp_setup(w["n"], w["l"], w["d_p"], w["d1"], A, opts)
     try:
         X0, Z0, y0 = bd.psdp_get_iterate(h)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
         ms = []
         fallback = 0.0
-        for i in range(nsteps + 1):
-            bd.psdp_load_iterate(h, X0, Z0, y0)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            s, info = bd.psdp_step(h)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            if s != 0:
-                raise RuntimeError(f"mixed step: {bd.STATUS[s]}")
-            fallback = max(fallback, info[13])
-            if i > 0:                      # the first step captures the graph
-                ms.append(e0.elapsed_time(e1))
+        with ClockSampler(device) as clk:
+            for i in range(nsteps + 1):
+                bd.psdp_load_iterate(h, X0, Z0, y0)
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s, info = bd.psdp_step(h)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if s != 0:
+                    raise RuntimeError(f"mixed step: {bd.STATUS[s]}")
+                fallback = max(fallback, info[13])
+                if i > 0:                      # the first step captures the graph
+                    ms.append(e0.elapsed_time(e1))
         work = bd.psdp_work(h)
         # per-kernel breakdown from CUDA events inside the (re-captured) step graph
         bd.psdp_profile_enable(h, True)
@@ -172,7 +267,7 @@ def measure_mixed(bd, synth, name, device, nsteps):
             "time_to_certificate_s": t1 - t0, "newton_steps": iters, "status": status, "verdict": verdict,
             "relgap": info["relgap"], "fp64_fallback": bool(info["fallback"] or fallback),
             "pcg_iterations_last_step": info["refine_sweeps"], "schur_flops_per_step": work["schur_flops"],
-            "chol_flops_per_step": work["chol_flops"],
+            "chol_flops_per_step": work["chol_flops"], "clocks": clk.summary(),
             "kernels_ms_per_step": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in prof.items()}}
 
 
@@ -280,7 +375,8 @@ def run_ours(args):
 
     w = WORKLOAD
     A = synth.system(w["n"], w["l"], w["s"], w["seed"] + rank)
-    stream = torch.cuda.current_stream()
+    # one stream for the library, the L2 flush and the timing events
+    stream = torch.cuda.Stream()
     opts = bd.psdp_default_opts(stream=stream.cuda_stream, device=local)
     h = bd.psdp_setup(w["n"], w["l"], w["d_p"], w["d1"], A, opts)
     X0, Z0, y0 = bd.psdp_get_iterate(h)
@@ -288,7 +384,8 @@ def run_ours(args):
 
     def one_step(timed):
         bd.psdp_load_iterate(h, X0, Z0, y0)
-        flush.zero_()
+        with torch.cuda.stream(stream):
+            flush.zero_()
         if timed:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -302,9 +399,6 @@ def run_ours(args):
 
     for _ in range(max(args.warmup, 3)):
         one_step(False)
-    bd.psdp_profile_enable(h, True)
-    one_step(False)             # re-capture the graph with profiling events
-    bd.psdp_profile_reset(h)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -313,9 +407,20 @@ def run_ours(args):
         torch.cuda.synchronize()
     ms = [a.elapsed_time(b) for a, b in evs]
     tot_ms = sum(ms)
-    prof = bd.psdp_profile_get(h)
     work = bd.psdp_work(h)
     sizes = bd.psdp_sizes(h)
+    # second timed region with a CUDA event pair around every kernel of the
+    # step graph (re-captured with the events): per-kernel durations for the
+    # roofline; the events themselves slow the step, so `value` comes from the
+    # region above
+    bd.psdp_profile_enable(h, True)
+    one_step(False)
+    bd.psdp_profile_reset(h)
+    torch.cuda.synchronize()
+    evs_p = [one_step(True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    prof_ms = sum(a.elapsed_time(b) for a, b in evs_p)
+    prof = bd.psdp_profile_get(h)
     bd.psdp_profile_enable(h, False)
     if dist:
         t = torch.tensor([tot_ms], device="cuda")
@@ -344,30 +449,23 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (from the live CUDA events)
     pk, pk_kind = peaks()
     fp64_peak = pk["bf16_tflops"] * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
-    K, nb = sizes["K"], 64
-    syrk_flops = trsm_flops = 0.0
-    for j0 in range(0, K, nb):
-        wdt = min(nb, K - j0)
-        rest = K - j0 - wdt
-        if rest <= 0:
-            break
-        syrk_flops += rest * (rest + 1) * wdt
-        trsm_flops += 2.0 * rest * wdt * wdt
+    cf = chol_flops(sizes["K"], work["nb_chol"])
     kern = {}
-    for name, flops_per_step in (("schur_gemm", work["schur_flops"]), ("chol_syrk_gemm", syrk_flops),
-                                 ("chol_trsm_gemm", trsm_flops)):
+    for name, flops_per_step in (("schur_gemm", work["schur_flops"]), ("chol_syrk_gemm", cf["bulk"]),
+                                 ("chol_syrk_next", cf["next"]), ("chol_trsm_gemm", cf["trsm"])):
         if name in prof and prof[name][0] > 0:
             launches, tms = prof[name]
             per_step_launches = launches / args.steps
             avg_ms = tms / launches
             kern[name] = {"launches_per_step": per_step_launches, "avg_ms": avg_ms,
                           "tflops": flops_per_step / per_step_launches / (avg_ms * 1e-3) / 1e12,
-                          "share_of_step": tms / tot_ms}
+                          "share_of_step": tms / prof_ms}
     for name in ("chol_potrf_diag", "dense_solve", "schur_operands", "schur_gather", "block_chol_inv",
                  "block_maxstep"):
         if name in prof and prof[name][0] > 0:
             kern[name] = {"launches_per_step": prof[name][0] / args.steps, "avg_ms": prof[name][1] / prof[name][0],
-                          "share_of_step": prof[name][1] / tot_ms}
+                          "share_of_step": prof[name][1] / prof_ms}
+    kern["_profiled_ms_per_step"] = prof_ms / args.steps
     dom = max(("schur_gemm", "chol_syrk_gemm"), key=lambda k: kern.get(k, {}).get("share_of_step", 0))
     ach = kern.get(dom, {}).get("tflops")
     roof = {"kernel": "k_gemm_tn (" + dom + ")", "bound": "fp64", "achieved": ach,

@@ -217,8 +217,10 @@ psdp_status psdp_profile_get(psdp_ctx* c, int max_entries, char* names, int64_t*
  * flops over the non-zero (pair, block) terms, out[1] = Cholesky flops K^3/3,
  * out[2] = Schur terms in the contraction (sum over block pairs), out[3] = dense
  * Schur flops (every block for every pair), out[4] = kernel launches in one
- * captured Newton step (0 before the first graph-mode step). */
-psdp_status psdp_work(const psdp_ctx* c, double* out5);
+ * captured Newton step (0 before the first graph-mode step), out[5] = panel
+ * width of the FP64 Cholesky, out[6] = panel width of the FP32 Cholesky of the
+ * mixed-precision step. */
+psdp_status psdp_work(const psdp_ctx* c, double* out7);
 
 /* The CUDA stream the context runs on (cudaStream_t as void*). */
 void* psdp_stream(psdp_ctx* c);

@@ -256,10 +256,10 @@ def psdp_profile_get(h, max_entries: int = 64) -> dict:
 
 
 def psdp_work(h) -> dict:
-    out = np.zeros(5)
+    out = np.zeros(7)
     _check(_lib().psdp_work(h, _dp(out)), "psdp_work")
     return dict(schur_flops=out[0], chol_flops=out[1], schur_terms=out[2], schur_dense_flops=out[3],
-                kernels_per_step=int(out[4]))
+                kernels_per_step=int(out[4]), nb_chol=int(out[5]), nb_chol32=int(out[6]))
 
 
 def psdp_stream(h) -> int:

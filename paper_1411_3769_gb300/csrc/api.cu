@@ -10,12 +10,12 @@
 #include "psdp_internal.h"
 
 void dense_cholesky(cudaStream_t st, double* A, int K, int nb, double* Linv, int* flag);
-void dense_solve(cudaStream_t st, const double* A, int K, int nb, const double* Linv, double* partial, double* x);
 void launch_vec_copy(cudaStream_t st, int K, const double* a, double* out);
 void launch_cdiag(cudaStream_t st, psdp_ctx* c);
 void init_attrs_linalg(int smem_max);
 void init_attrs_sdp(int smem_max);
 void init_attrs_dense(int smem_max);
+void init_attrs_trsv(int smem_max);
 
 namespace {
 
@@ -53,29 +53,31 @@ int prof_name_id(psdp_ctx* c, const char* name) {
 
 // Inside a stream capture an event record must be an external node to be
 // timeable after each replay of the graph.
-void record_event(psdp_ctx* c, cudaEvent_t e) {
+void record_event(cudaStream_t st, cudaEvent_t e) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    cudaStreamIsCapturing(c->stream, &cs);
+    cudaStreamIsCapturing(st, &cs);
     if (cs == cudaStreamCaptureStatusActive)
-        cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal);
+        cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
     else
-        cudaEventRecord(e, c->stream);
+        cudaEventRecord(e, st);
 }
 
-int prof_begin(psdp_ctx* c, const char* name) {
+int prof_begin(psdp_ctx* c, const char* name, cudaStream_t st) {
     if (!c->prof_on || !c->prof_cur || c->prof_pool_used + 2 > c->prof_pool_limit) return -1;
     ProfSite s;
     s.name_id = prof_name_id(c, name);
     s.a = c->prof_pool[c->prof_pool_used++];
     s.b = c->prof_pool[c->prof_pool_used++];
-    record_event(c, s.a);
+    s.st = st;
+    record_event(st, s.a);
     c->prof_cur->push_back(s);
     return (int)c->prof_cur->size() - 1;
 }
 
 void prof_end(psdp_ctx* c, int site) {
     if (site < 0) return;
-    record_event(c, (*c->prof_cur)[site].b);
+    const ProfSite& s = (*c->prof_cur)[site];
+    record_event(s.st, s.b);
 }
 
 void prof_collect(psdp_ctx* c, bool mixed) {
@@ -93,7 +95,8 @@ void prof_collect(psdp_ctx* c, bool mixed) {
 struct ProfScope {
     psdp_ctx* c;
     int site;
-    ProfScope(psdp_ctx* cc, const char* name) : c(cc), site(prof_begin(cc, name)) {}
+    ProfScope(psdp_ctx* cc, const char* name) : c(cc), site(prof_begin(cc, name, cc->stream)) {}
+    ProfScope(psdp_ctx* cc, const char* name, cudaStream_t st) : c(cc), site(prof_begin(cc, name, st)) {}
     ~ProfScope() { prof_end(c, site); }
 };
 
@@ -119,36 +122,61 @@ void enqueue_schur(psdp_ctx* c) {
     }
 }
 
+// `to` waits for the work enqueued on `from` so far (a graph edge under capture).
+void stream_dep(cudaStream_t from, cudaStream_t to, cudaEvent_t e) {
+    cudaEventRecord(e, from);
+    cudaStreamWaitEvent(to, e, 0);
+}
+
 // Omega = L L^T in place (column-major lower view of the row-major upper
 // triangle), right-looking with panels of nb_chol columns; the diagonal-block
-// inverses are kept for the triangular solves.
+// inverses are kept for the triangular solves.  Look-ahead of depth one: the
+// panel factor, the panel solve and the update of the next panel's rows run on
+// the high-priority stream `crit`, and the update of the rest of the trailing
+// matrix on the main stream, so panel p+1 is factored while the bulk of
+// update p is still running.  Per panel p (rows/columns >= j0 + w trailing):
+//   crit: potrf(p), trsm(p) | wait bulk(p-1) | next-rows update(p)
+//   main: wait trsm(p) | bulk update(p) of the rows below the next panel
+// Both updates read only panel p; they write disjoint rows.
 void enqueue_cholesky(psdp_ctx* c) {
-    cudaStream_t st = c->stream;
+    cudaStream_t st = c->stream, cs = c->crit;
     const int K = c->K, nb = c->nb_chol;
     double* A = c->d_Om;
+    stream_dep(st, cs, c->ev_fork);
     for (int j0 = 0, p = 0; j0 < K; j0 += nb, ++p) {
         const int w = std::min(nb, K - j0);
         double* Lp = c->d_Linv + (size_t)p * nb * nb;
         {
-            ProfScope q(c, "chol_potrf_diag");
-            launch_potrf_diag(st, A, K, j0, nb, Lp, c->d_flag);
+            ProfScope q(c, "chol_potrf_diag", cs);
+            launch_potrf_diag(cs, A, K, j0, nb, Lp, c->d_flag);
         }
         const int rest = K - j0 - w;
         if (rest <= 0) break;
         double* panel = A + (int64_t)j0 * K + j0 + w;
         {
             // panel <- panel L_jj^{-T}:  C[k][i] = sum_m Linv(k,m) P(i,m)
-            ProfScope q(c, "chol_trsm_gemm");
-            launch_gemm_tn(st, w, rest, 1, Lp, nb, nullptr, 0, panel, K, nullptr, 0, nullptr, w, panel, K, 0, 1.0,
+            ProfScope q(c, "chol_trsm_gemm", cs);
+            launch_gemm_tn(cs, w, rest, 1, Lp, nb, nullptr, 0, panel, K, nullptr, 0, nullptr, w, panel, K, 0, 1.0,
                            0.0, 0);
         }
+        const int w2 = std::min(nb, rest);
+        double* T = A + (int64_t)(j0 + w) * K + j0 + w;     // trailing matrix, leading dimension K
+        stream_dep(cs, st, c->ev_join);                     // main: after trsm(p)
+        stream_dep(st, cs, c->ev_fork);                     // crit: after bulk(p-1)
         {
-            // trailing lower triangle -= P P^T
-            ProfScope q(c, "chol_syrk_gemm");
-            launch_gemm_tn(st, rest, rest, 1, panel, K, nullptr, 0, panel, K, nullptr, 0, nullptr, w,
-                           A + (int64_t)(j0 + w) * K + j0 + w, K, 0, -1.0, 1.0, 1);
+            // rows [0, w2) of the trailing upper triangle -= P[:, :w2]^T P
+            ProfScope q(c, "chol_syrk_next", cs);
+            launch_gemm_tn(cs, w2, rest, 1, panel, K, nullptr, 0, panel, K, nullptr, 0, nullptr, w, T, K, 0, -1.0,
+                           1.0, 1);
+        }
+        if (rest > w2) {
+            // rows [w2, rest) of the trailing upper triangle -= P[:, w2:]^T P[:, w2:]
+            ProfScope q(c, "chol_syrk_gemm", st);
+            launch_gemm_tn(st, rest - w2, rest - w2, 1, panel + w2, K, nullptr, 0, panel + w2, K, nullptr, 0,
+                           nullptr, w, T + (int64_t)w2 * K + w2, K, 0, -1.0, 1.0, 1);
         }
     }
+    stream_dep(cs, st, c->ev_join);
 }
 
 // ----------------------------------------------------------- mixed precision
@@ -187,34 +215,62 @@ void enqueue_schur_mixed(psdp_ctx* c) {
 }
 
 // FP32 Cholesky of Omega32: diagonal blocks in FP64 arithmetic, panel TRSM on
-// CUDA cores, trailing update as a 3xTF32 tensor-core SYRK.
+// CUDA cores, trailing update as a 3xTF32 tensor-core SYRK, with the same
+// depth-one look-ahead as the FP64 factorisation.  The packed panel (hi, lo) is
+// double-buffered by panel parity: trsm(p+1) writes one buffer while the bulk
+// update p still reads the other (update p-1, the last reader of the buffer
+// trsm(p+1) overwrites, finished before the next-rows update p).
 void enqueue_cholesky_mixed(psdp_ctx* c) {
-    cudaStream_t st = c->stream;
+    cudaStream_t st = c->stream, cs = c->crit;
     const int K = c->K, nb = c->nb32;
     float* A = c->d_Om32;
+    stream_dep(st, cs, c->ev_fork);
     for (int j0 = 0, p = 0; j0 < K; j0 += nb, ++p) {
         const int w = std::min(nb, K - j0);
         float* Lp = c->d_Linv32 + (size_t)p * nb * nb;
         {
-            ProfScope q(c, "chol32_potrf_diag");
-            launch_potrf_diag32(st, A, K, j0, nb, Lp, c->d_flag);
+            ProfScope q(c, "chol32_potrf_diag", cs);
+            launch_potrf_diag32(cs, A, K, j0, nb, Lp, c->d_flag);
         }
         const int rest = K - j0 - w;
         if (rest <= 0) break;
+        float* phi = c->d_Pt_hi + (size_t)(p & 1) * K * nb;
+        float* plo = c->d_Pt_lo + (size_t)(p & 1) * K * nb;
         {
-            ProfScope q(c, "chol32_trsm");
-            launch_trsm32_pack(st, A, K, j0, nb, Lp, c->d_Pt_hi, c->d_Pt_lo);
+            ProfScope q(c, "chol32_trsm", cs);
+            launch_trsm32_pack(cs, A, K, j0, nb, Lp, phi, plo);
         }
-        CUtensorMap hi, lo;
-        if (!tc_make_map(&hi, c->d_Pt_hi, false, w, rest, 1, nb, 0, 128) ||
-            !tc_make_map(&lo, c->d_Pt_lo, false, w, rest, 1, nb, 0, 128))
-            continue;
+        const int w2 = std::min(nb, rest);
+        float* T = A + (int64_t)(j0 + w) * K + j0 + w;
+        CUtensorMap hi, lo, hi2, lo2, hib, lob;
+        bool ok = tc_make_map(&hi, phi, false, w, rest, 1, nb, 0, 128) &&
+                  tc_make_map(&lo, plo, false, w, rest, 1, nb, 0, 128) &&
+                  tc_make_map(&hi2, phi, false, w, w2, 1, nb, 0, 128) &&
+                  tc_make_map(&lo2, plo, false, w, w2, 1, nb, 0, 128);
+        if (rest > w2)
+            ok = ok && tc_make_map(&hib, phi + (size_t)w2 * nb, false, w, rest - w2, 1, nb, 0, 128) &&
+                 tc_make_map(&lob, plo + (size_t)w2 * nb, false, w, rest - w2, 1, nb, 0, 128);
+        if (!ok) {
+            // cannot happen for the sizes setup accepts; report a failed factor
+            // rather than leave a silently wrong one (low byte of the flag)
+            cudaMemsetAsync(c->d_flag, FL_CHOL_SCHUR, 1, cs);
+            break;
+        }
+        stream_dep(cs, st, c->ev_join);                     // main: after trsm(p)
+        stream_dep(st, cs, c->ev_fork);                     // crit: after bulk(p-1)
         {
-            ProfScope q(c, "chol32_syrk_tc");
-            launch_tc_gemm(st, false, 3, hi, hi, &lo, &lo, rest, rest, 1, 0, nullptr, w,
-                           A + (int64_t)(j0 + w) * K + j0 + w, K, 0, -1.f, 1.f, 1, c->d_flag);
+            // rows [0, w2) of the trailing upper triangle (C[n][m], n < w2, m >= n)
+            ProfScope q(c, "chol32_syrk_next", cs);
+            launch_tc_gemm(cs, false, 3, hi, hi2, &lo, &lo2, rest, w2, 1, 0, nullptr, w, T, K, 0, -1.f, 1.f, 1,
+                           c->d_flag);
+        }
+        if (rest > w2) {
+            ProfScope q(c, "chol32_syrk_tc", st);
+            launch_tc_gemm(st, false, 3, hib, hib, &lob, &lob, rest - w2, rest - w2, 1, 0, nullptr, w,
+                           T + (int64_t)w2 * K + w2, K, 0, -1.f, 1.f, 1, c->d_flag);
         }
     }
+    stream_dep(cs, st, c->ev_join);
 }
 
 // x <- Omega^{-1} b by conjugate gradients in FP64 with the matrix-free product
@@ -226,7 +282,8 @@ void enqueue_pcg(psdp_ctx* c, double* b) {
     const int* done = c->d_pcg_done;
     ProfScope p(c, "pcg_solve");
     launch_pcg_init(st, K, b, c->d_pcg_x, c->d_pcg_r, c->d_pcg_state, c->d_pcg_done);
-    launch_precond32(st, c->d_Om32, K, c->nb32, c->d_Linv32, c->d_z32, c->d_part32, c->d_pcg_r, c->d_pcg_z, done);
+    launch_precond32_flag(st, c->d_Om32, K, c->nb32, c->d_Linv32, c->d_z32, c->d_pcg_r, c->d_pcg_z, c->d_trsv_sync,
+                          c->d_flag, done);
     launch_pcg_start(st, K, c->d_pcg_r, c->d_pcg_z, c->d_pcg_p, c->d_pcg_state, done);
     for (int it = 0; it < c->pcg_max; ++it) {
         launch_bt(st, c, c->d_pcg_p, c->d_M1, done);
@@ -235,7 +292,8 @@ void enqueue_pcg(psdp_ctx* c, double* b) {
         launch_b(st, c, c->d_M1, c->d_pcg_q, 0.0, done);
         launch_pcg_alpha(st, K, c->d_pcg_p, c->d_pcg_q, c->d_pcg_x, c->d_pcg_r, c->d_pcg_state, c->d_pcg_done,
                          c->pcg_tol);
-        launch_precond32(st, c->d_Om32, K, c->nb32, c->d_Linv32, c->d_z32, c->d_part32, c->d_pcg_r, c->d_pcg_z, done);
+        launch_precond32_flag(st, c->d_Om32, K, c->nb32, c->d_Linv32, c->d_z32, c->d_pcg_r, c->d_pcg_z,
+                              c->d_trsv_sync, c->d_flag, done);
         launch_pcg_beta(st, K, c->d_pcg_r, c->d_pcg_z, c->d_pcg_p, c->d_pcg_state, done);
     }
     launch_pcg_finish(st, K, c->d_pcg_x, b, c->d_pcg_state, done, c->d_flag, c->pcg_fail, c->d_info + 12);
@@ -280,7 +338,7 @@ void enqueue_step(psdp_ctx* c, bool mixed) {
     } else {
         enqueue_cholesky(c);
         ProfScope p(c, "dense_solve");
-        dense_solve(st, c->d_Om, c->K, c->nb_chol, c->d_Linv, c->d_rhs, c->d_dyh);
+        launch_solve_fp64(st, c->d_Om, c->K, c->nb_chol, c->d_Linv, c->d_dyh, c->d_trsv_sync, c->d_flag);
     }
     // predictor directions
     launch_bt(st, c, c->d_dyh, c->d_T2);
@@ -297,7 +355,7 @@ void enqueue_step(psdp_ctx* c, bool mixed) {
         enqueue_pcg(c, c->d_dyb);
     } else {
         ProfScope p(c, "dense_solve");
-        dense_solve(st, c->d_Om, c->K, c->nb_chol, c->d_Linv, c->d_rhs, c->d_dyb);
+        launch_solve_fp64(st, c->d_Om, c->K, c->nb_chol, c->d_Linv, c->d_dyb, c->d_trsv_sync, c->d_flag);
     }
     // corrector directions and totals
     launch_bt(st, c, c->d_dyb, c->d_T2);
@@ -350,13 +408,16 @@ void free_ctx(psdp_ctx* c) {
                     c->d_term_desc, c->d_term_w, c->d_uv_idx, c->d_prod_idx, c->d_U, c->d_V, c->d_Aop, c->d_Bop,
                     c->d_Tbuf, c->d_Om, c->d_Linv, c->d_grid, c->d_svec, c->d_cert, c->d_term_off_t,
                     c->d_opA_hi, c->d_opA_lo, c->d_opB_hi, c->d_opB_lo, c->d_prodA, c->d_prodB, c->d_T32,
-                    c->d_Om32, c->d_Linv32, c->d_Pt_hi, c->d_Pt_lo, c->d_z32, c->d_part32, c->d_pcg_x, c->d_pcg_r,
+                    c->d_Om32, c->d_Linv32, c->d_Pt_hi, c->d_Pt_lo, c->d_z32, c->d_part32, c->d_trsv_sync, c->d_pcg_x, c->d_pcg_r,
                     c->d_pcg_z, c->d_pcg_p, c->d_pcg_q, c->d_pcg_state, c->d_pcg_done, c->d_M1, c->d_M2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_info) cudaFreeHost(c->h_info);
     if (c->h_flag) cudaFreeHost(c->h_flag);
     for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->crit) cudaStreamDestroy(c->crit);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     cudaGetLastError();
     delete c;
@@ -491,8 +552,8 @@ psdp_status alloc_mixed(psdp_ctx* c) {
     const int nb = c->nb32, npanel = (c->K + nb - 1) / nb;
     TRY(dalloc(&c->d_Om32, K * K));
     TRY(dalloc(&c->d_Linv32, (size_t)npanel * nb * nb));
-    TRY(dalloc(&c->d_Pt_hi, K * nb));
-    TRY(dalloc(&c->d_Pt_lo, K * nb));
+    TRY(dalloc(&c->d_Pt_hi, 2 * K * nb));   // double-buffered by panel parity
+    TRY(dalloc(&c->d_Pt_lo, 2 * K * nb));
     TRY(dalloc(&c->d_z32, K));
     TRY(dalloc(&c->d_part32, (size_t)nb * (K / 2048 + 2)));
     double** vecs[] = {&c->d_pcg_x, &c->d_pcg_r, &c->d_pcg_z, &c->d_pcg_p, &c->d_pcg_q};
@@ -536,6 +597,7 @@ psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psd
     init_attrs_dense(smem_max);
     init_attrs_tc(smem_max);
     init_attrs_mixed(smem_max);
+    init_attrs_trsv(smem_max);
     cudaGetLastError();
 
     psdp_ctx* c = new (std::nothrow) psdp_ctx();
@@ -553,6 +615,16 @@ psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psd
     } else {
         if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { free_ctx(c); return PSDP_ECUDA; }
         c->own_stream = true;
+    }
+    {
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (cudaStreamCreateWithPriority(&c->crit, cudaStreamNonBlocking, hi) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            free_ctx(c);
+            return PSDP_ECUDA;
+        }
     }
     psdp_status s = PSDP_OK;
     auto fail = [&](psdp_status e) { free_ctx(c); return e; };
@@ -577,7 +649,7 @@ psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psd
     if ((s = dalloc(&c->d_rhs, rhs_len)) || (s = dalloc(&c->d_part, (size_t)4 * (c->nblk + 1))) ||
         (s = dalloc(&c->d_tstep, (size_t)2 * c->nblk)) || (s = dalloc(&c->d_scal, SC_COUNT)) ||
         (s = dalloc(&c->d_info, PSDP_INFO_LEN)) || (s = dalloc(&c->d_flag, 1)) || (s = dalloc(&c->d_cert, 4)) ||
-        (s = dalloc(&c->d_svec, (size_t)2 * Nt)))
+        (s = dalloc(&c->d_svec, (size_t)2 * Nt)) || (s = dalloc(&c->d_trsv_sync, trsv_sync_words((int)K, 32))))
         return fail(s);
     if (cudaMallocHost((void**)&c->h_info, PSDP_INFO_LEN * sizeof(double)) != cudaSuccess ||
         cudaMallocHost((void**)&c->h_flag, sizeof(int)) != cudaSuccess) {
@@ -1183,6 +1255,8 @@ psdp_status psdp_work(const psdp_ctx* c, double* out) {
     out[2] = (double)c->nterms;
     out[3] = c->flops_schur_dense;
     out[4] = (double)c->kernels_per_step;
+    out[5] = (double)c->nb_chol;
+    out[6] = (double)c->nb32;
     return PSDP_OK;
 }
 

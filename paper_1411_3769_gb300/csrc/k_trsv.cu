@@ -1,0 +1,356 @@
+// Blocked triangular sweeps with the dense Cholesky factor of the Schur
+// complement (Sec. IV-A, the two solves of every Newton step; with the FP32
+// factor, the preconditioner of the mixed-precision path), one launch per sweep.
+//
+// Factor layout (both precisions): Omega is K x K row-major and the factor is
+// kept in its upper triangle, A[j*K + i] = L(i, j) for i >= j, with the inverse
+// of every W x W diagonal block in Linv[p][k*W + r] = Linv_p(r, k).
+//
+// One CTA per block row.  A CTA takes a ticket from an atomic counter and
+// solves block row `ticket` (forward) or `npanel-1-ticket` (backward), so it
+// only waits for CTAs that took earlier tickets, i.e. CTAs that are already
+// running: the sweep cannot deadlock whatever the residency.  While it waits it
+// applies every block that is already solved; each thread's running sum runs
+// over a fixed index sequence however the solved blocks arrive, so the result
+// is bit-reproducible.  A finished block is published with a release store of
+// its ready flag; readers acquire the flag and read the solved values through
+// L2.  Every wait is bounded (2 s without progress): the CTA sets FL_TIMEOUT
+// and finishes with what it has, so its dependants finish too.
+//
+// sync: [0] forward ticket, [1] backward ticket, [2, 2+npanel) forward ready
+// flags, [2+npanel, 2+2*npanel) backward ready flags; zeroed before each solve.
+#include "psdp_internal.h"
+
+namespace {
+
+constexpr int TT = 256;
+constexpr long long kWaitNs = 2000000000LL;
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ long long gtimer() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
+
+// V contiguous elements from a 16-byte aligned address (V = 1: one element)
+template <typename T, int V>
+__device__ __forceinline__ void load_vec(const T* p, T* o) {
+    if constexpr (V == 1) {
+        o[0] = *p;
+    } else if constexpr (sizeof(T) == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    } else {
+        const double2 v = *reinterpret_cast<const double2*>(p);
+        o[0] = v.x; o[1] = v.y;
+    }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void load_vec_cg(const T* p, T* o) {
+    if constexpr (V == 1) {
+        o[0] = __ldcg(p);
+    } else if constexpr (sizeof(T) == 4) {
+        const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    } else {
+        const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+        o[0] = v.x; o[1] = v.y;
+    }
+}
+
+template <typename T>
+size_t trsv_smem(int W) { return ((size_t)W * W + (size_t)(TT / W) * W + W) * sizeof(T); }
+
+// Shared wait step: thread 0 decides (progress resets the clock; 2 s without
+// progress sets FL_TIMEOUT), every thread gets the same answer.
+__device__ __forceinline__ bool wait_gives_up(long long& t0, int* flag, int* s_abort) {
+    if (threadIdx.x == 0) {
+        const long long now = gtimer();
+        if (t0 == 0) t0 = now;
+        if (now - t0 > kWaitNs) {
+            atomicOr(flag, (int)FL_TIMEOUT);
+            *s_abort = 1;
+        }
+    }
+    __syncthreads();
+    const bool give_up = *s_abort != 0;
+    if (!give_up) __nanosleep(128);
+    return give_up;
+}
+
+// Forward sweep L z = b.  Block row p: z_p = Linv_p (b_p - sum_{q<p} L_pq z_q),
+// L_pq(r, k) = A[(qW + k) K + pW + r].  b from bin (FP64) when given, else x.
+// Off-diagonal part: thread (c, g) owns columns [cV, cV+V) of the block row and
+// the rows j = qW + g + G t of every solved block q, U rows in flight.
+template <typename T, int W, int V>
+__global__ void __launch_bounds__(TT)
+k_trsv_fwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, const double* __restrict__ bin, T* x,
+           unsigned* sync, int* flag, const int* skip) {
+    if (skip && *skip) return;
+    constexpr int R = W / V, G = TT / R, RPB = W / G, U = RPB < 8 ? RPB : 8;
+    constexpr int G2 = TT / W;
+    static_assert(TT % R == 0 && W % G == 0 && RPB % U == 0, "thread layout");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* Ls = reinterpret_cast<T*>(smraw);   // [W][W]  Ls[k*W + r] = Linv_p(r, k)
+    T* red = Ls + W * W;                   // [G2][W], reused as [W] partial sums below
+    T* acc = red + G2 * W;                 // [W]
+    __shared__ int s_ticket, s_first, s_abort;
+    __shared__ T s_off[G][W];
+    unsigned* ready = sync + 2;
+    if (threadIdx.x == 0) {
+        s_ticket = (int)atomicAdd(&sync[0], 1u);
+        s_abort = 0;
+    }
+    __syncthreads();
+    const int p = s_ticket, j0 = p * W, w = min(W, K - j0);
+    const T* Lp = Linv + (size_t)p * W * W;
+    for (int i = threadIdx.x; i < W * W; i += TT) Ls[i] = Lp[i];
+    const int c = (threadIdx.x % R) * V, g = threadIdx.x / R;
+    T part[U][V];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int v = 0; v < V; ++v) part[u][v] = T(0);
+    int qd = 0;                 // blocks [0, qd) applied
+    long long t0 = 0;
+    while (qd < p) {
+        if (threadIdx.x == 0) s_first = p;
+        __syncthreads();
+        for (int q = qd + threadIdx.x; q < p; q += TT)
+            if (ld_acquire(ready + q) == 0u) atomicMin(&s_first, q);
+        __syncthreads();
+        const int qe = s_first;
+        __syncthreads();
+        if (qe == qd) {
+            if (wait_gives_up(t0, flag, &s_abort)) break;
+            continue;
+        }
+        t0 = 0;
+        if (c < w) {
+            for (int q = qd; q < qe; ++q) {
+                const int jb = q * W + g;
+#pragma unroll
+                for (int ta = 0; ta < RPB; ta += U) {
+                    T a[U][V], xv[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int j = jb + G * (ta + u);
+                        load_vec<T, V>(A + (int64_t)j * K + j0 + c, a[u]);
+                        xv[u] = ldcg(x + j);
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+#pragma unroll
+                        for (int v = 0; v < V; ++v) part[u][v] = fma(a[u][v], xv[u], part[u][v]);
+                }
+            }
+        }
+        qd = qe;
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        T sum = T(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u) sum += part[u][v];
+        s_off[g][c + v] = sum;
+    }
+    __syncthreads();
+    if (threadIdx.x < W) {
+        const int rr = threadIdx.x;
+        T sum = T(0);
+#pragma unroll
+        for (int gg = 0; gg < G; ++gg) sum += s_off[gg][rr];
+        acc[rr] = (rr < w) ? (T)(bin ? bin[j0 + rr] : (double)ldcg(x + j0 + rr)) - sum : T(0);
+    }
+    __syncthreads();
+    // z_p[r] = sum_{k <= r} Linv_p(r, k) acc[k], k = g2 (mod G2)
+    const int r = threadIdx.x % W, g2 = threadIdx.x / W;
+    T sum = T(0);
+    if (r < w)
+        for (int k = g2; k <= r; k += G2) sum = fma(Ls[k * W + r], acc[k], sum);
+    red[g2 * W + r] = sum;
+    __syncthreads();
+    if (threadIdx.x < w) {
+        T z = T(0);
+#pragma unroll
+        for (int gg = 0; gg < G2; ++gg) z += red[gg * W + threadIdx.x];
+        x[j0 + threadIdx.x] = z;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) st_release(ready + p, 1u);
+}
+
+// Backward sweep L^T x = z.  Block row p: x_p = Linv_p^T (z_p - sum_{q>p} L_qp^T x_q),
+// (L_qp^T x_q)[k] = sum_{i in block q} A[(pW + k) K + i] x_i.  x holds z on entry;
+// the FP64 copy of the result also goes to xout when given.  Off-diagonal part:
+// R threads share a row (V columns each, W / (R V) segments per block), thread
+// row group g owns rows k = g + G t.
+template <typename T, int W, int V>
+__global__ void __launch_bounds__(TT)
+k_trsv_bwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, T* x, double* xout, unsigned* sync, int* flag,
+           const int* skip) {
+    if (skip && *skip) return;
+    constexpr int R = (W / V < 32) ? W / V : 32, G = TT / R, RPB = W / G, SEG = W / (R * V);
+    constexpr int G2 = TT / W;
+    static_assert(32 % R == 0 && W % G == 0 && W % (R * V) == 0, "thread layout");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* Ls = reinterpret_cast<T*>(smraw);
+    T* red = Ls + W * W;
+    T* acc = red + G2 * W;
+    __shared__ int s_ticket, s_last, s_abort;
+    const int npanel = (K + W - 1) / W;
+    unsigned* ready = sync + 2 + npanel;
+    if (threadIdx.x == 0) {
+        s_ticket = (int)atomicAdd(&sync[1], 1u);
+        s_abort = 0;
+    }
+    __syncthreads();
+    const int p = npanel - 1 - s_ticket, j0 = p * W, w = min(W, K - j0);
+    const T* Lp = Linv + (size_t)p * W * W;
+    for (int i = threadIdx.x; i < W * W; i += TT) Ls[i] = Lp[i];
+    const int cl = (threadIdx.x % R) * V, g = threadIdx.x / R;
+    T part[RPB];
+#pragma unroll
+    for (int t = 0; t < RPB; ++t) part[t] = T(0);
+    int qd = npanel;            // blocks [qd, npanel) applied
+    long long t0 = 0;
+    while (qd > p + 1) {
+        if (threadIdx.x == 0) s_last = p;
+        __syncthreads();
+        for (int q = p + 1 + threadIdx.x; q < qd; q += TT)
+            if (ld_acquire(ready + q) == 0u) atomicMax(&s_last, q);
+        __syncthreads();
+        const int qe = s_last + 1;   // blocks [qe, qd) are solved
+        __syncthreads();
+        if (qe == qd) {
+            if (wait_gives_up(t0, flag, &s_abort)) break;
+            continue;
+        }
+        t0 = 0;
+        // blocks in descending order, segments ascending inside a block
+        for (int q = qd - 1; q >= qe; --q) {
+#pragma unroll
+            for (int sg = 0; sg < SEG; ++sg) {
+                const int i = q * W + sg * R * V + cl;
+                if (i < K) {           // K is a multiple of V: the whole vector is inside
+                    T xv[V];
+                    load_vec_cg<T, V>(x + i, xv);
+#pragma unroll
+                    for (int t = 0; t < RPB; ++t) {
+                        const int k = g + G * t;
+                        if (k < w) {
+                            T a[V];
+                            load_vec<T, V>(A + (int64_t)(j0 + k) * K + i, a);
+#pragma unroll
+                            for (int v = 0; v < V; ++v) part[t] = fma(a[v], xv[v], part[t]);
+                        }
+                    }
+                }
+            }
+        }
+        qd = qe;
+    }
+#pragma unroll
+    for (int t = 0; t < RPB; ++t) {
+        T v = part[t];
+#pragma unroll
+        for (int o = R / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        const int k = g + G * t;
+        if ((threadIdx.x % R) == 0) acc[k] = (k < w) ? ldcg(x + j0 + k) - v : T(0);
+    }
+    __syncthreads();
+    // x_p[k] = sum_{r >= k} Linv_p(r, k) acc[r], r = g2 (mod G2)
+    const int k = threadIdx.x % W, g2 = threadIdx.x / W;
+    T s = T(0);
+    if (k < w)
+        for (int rr = g2; rr < w; rr += G2)
+            if (rr >= k) s = fma(Ls[k * W + rr], acc[rr], s);
+    red[g2 * W + k] = s;
+    __syncthreads();
+    if (threadIdx.x < w) {
+        T z = T(0);
+#pragma unroll
+        for (int gg = 0; gg < G2; ++gg) z += red[gg * W + threadIdx.x];
+        x[j0 + threadIdx.x] = z;
+        if (xout) xout[j0 + threadIdx.x] = (double)z;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) st_release(ready + p, 1u);
+}
+
+template <typename T, int W>
+void set_attrs(int smem_max) {
+    const size_t need = trsv_smem<T>(W);
+    if ((int)need > 40 * 1024 && (int)need + 16 * 1024 <= smem_max) {
+        cudaFuncSetAttribute(k_trsv_fwd<T, W, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+        cudaFuncSetAttribute(k_trsv_bwd<T, W, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+        constexpr int V = 16 / sizeof(T);
+        cudaFuncSetAttribute(k_trsv_fwd<T, W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+        cudaFuncSetAttribute(k_trsv_bwd<T, W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+    }
+}
+
+// Both sweeps; 16-byte loads when every row of A starts on a 16-byte boundary.
+template <typename T, int W>
+void sweeps(cudaStream_t st, const T* A, int K, const T* Linv, const double* bin, T* x, double* xout,
+            unsigned* sync, int* flag, const int* skip) {
+    constexpr int V = 16 / sizeof(T);
+    const int npanel = (K + W - 1) / W;
+    const size_t sm = trsv_smem<T>(W);
+    cudaMemsetAsync(sync, 0, (size_t)(2 + 2 * npanel) * sizeof(unsigned), st);
+    const bool vec = (K % V == 0) && ((uintptr_t)A % 16 == 0) && ((uintptr_t)x % 16 == 0);
+    if (vec) {
+        k_trsv_fwd<T, W, V><<<npanel, TT, sm, st>>>(A, K, Linv, bin, x, sync, flag, skip);
+        k_trsv_bwd<T, W, V><<<npanel, TT, sm, st>>>(A, K, Linv, x, xout, sync, flag, skip);
+    } else {
+        k_trsv_fwd<T, W, 1><<<npanel, TT, sm, st>>>(A, K, Linv, bin, x, sync, flag, skip);
+        k_trsv_bwd<T, W, 1><<<npanel, TT, sm, st>>>(A, K, Linv, x, xout, sync, flag, skip);
+    }
+}
+
+}  // namespace
+
+size_t trsv_sync_words(int K, int nb) { return (size_t)2 + 2 * (size_t)((K + nb - 1) / nb); }
+
+void init_attrs_trsv(int smem_max) {
+    set_attrs<double, 32>(smem_max);
+    set_attrs<float, 64>(smem_max);
+    set_attrs<float, 128>(smem_max);
+}
+
+// x <- Omega^{-1} x with the FP64 factor (panel width 32).
+bool launch_solve_fp64(cudaStream_t st, const double* A, int K, int nb, const double* Linv, double* x,
+                       unsigned* sync, int* flag) {
+    if (nb != 32) return false;
+    sweeps<double, 32>(st, A, K, Linv, nullptr, x, nullptr, sync, flag, nullptr);
+    return true;
+}
+
+// z <- M^{-1} r with M = L L^T the FP32 factor (panel width 64 or 128); the
+// sweeps run in FP32 in z32, r and z are FP64.  Nothing runs when *skip != 0.
+bool launch_precond32_flag(cudaStream_t st, const float* A, int K, int nb, const float* Linv, float* z32,
+                           const double* r, double* z, unsigned* sync, int* flag, const int* skip) {
+    if (nb == 128)
+        sweeps<float, 128>(st, A, K, Linv, r, z32, z, sync, flag, skip);
+    else if (nb == 64)
+        sweeps<float, 64>(st, A, K, Linv, r, z32, z, sync, flag, skip);
+    else
+        return false;
+    return true;
+}

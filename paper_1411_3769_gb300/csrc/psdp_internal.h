@@ -44,6 +44,7 @@ enum FlagBits {
 struct ProfSite {
     int name_id;
     cudaEvent_t a, b;
+    cudaStream_t st;    // stream the two events are recorded on
 };
 
 struct psdp_ctx {
@@ -54,6 +55,10 @@ struct psdp_ctx {
     int device;
     cudaStream_t stream;
     bool own_stream;
+    // high-priority stream for the Cholesky critical path (panel factor, panel
+    // solve, next-panel update) and the events that fork/join it with `stream`
+    cudaStream_t crit = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     // ----- host copies of the tables
     std::vector<int32_t> beta;   // [L0][L]
@@ -97,6 +102,7 @@ struct psdp_ctx {
     int pairs_per_chunk = 1;
     double *d_Om = nullptr;           // [K][K] row-major, upper triangle authoritative
     double *d_Linv = nullptr;         // diagonal-block inverses of the dense factor [npanel][nb][nb]
+    unsigned *d_trsv_sync = nullptr;  // tickets and ready flags of the triangular sweeps
     int nb_chol = 32;
     double flops_schur = 0, flops_chol = 0, flops_schur_dense = 0;
 
@@ -240,6 +246,14 @@ void launch_schur_gather32(cudaStream_t st, psdp_ctx* c, int p0, int np, const f
 void launch_potrf_diag32(cudaStream_t st, float* A, int K, int j0, int nb, float* Linv, int* flag);
 void launch_trsm32_pack(cudaStream_t st, float* A, int K, int j0, int nb, const float* Linv, float* PtHi,
                         float* PtLo);
+// Triangular sweeps with the dense factor (one launch per sweep, flag-synchronised
+// block rows).  sync needs trsv_sync_words(K, nb) words; false for an
+// unsupported panel width (FP64: 32; FP32: 64, 128).
+size_t trsv_sync_words(int K, int nb);
+bool launch_solve_fp64(cudaStream_t st, const double* A, int K, int nb, const double* Linv, double* x,
+                       unsigned* sync, int* flag);
+bool launch_precond32_flag(cudaStream_t st, const float* A, int K, int nb, const float* Linv, float* z32,
+                           const double* r, double* z, unsigned* sync, int* flag, const int* skip);
 void launch_precond32(cudaStream_t st, const float* A, int K, int nb, const float* Linv, float* z32, float* partial,
                       const double* r, double* z, const int* skip);
 void launch_pcg_init(cudaStream_t st, int K, const double* b, double* x, double* r, double* s, int* done);
