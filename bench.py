@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--mixed", type=int, default=1, help="also measure the mixed-precision path")
     ap.add_argument("--mixed-steps", type=int, default=5)
+    ap.add_argument("--fp64-large", type=int, default=1, help="time one plain FP64 step of the large workload")
+    ap.add_argument("--mixed-workloads", default="mid,large")
     ap.add_argument("--extra", action="store_true", help="measure the batched and warm-start rows instead")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--warm-train", type=int, default=1024)
@@ -271,6 +273,29 @@ def measure_mixed(bd, synth, name, device, nsteps):
             "kernels_ms_per_step": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in prof.items()}}
 
 
+def measure_fp64_step(bd, synth, name, device):
+    """One plain FP64 Newton step of a workload from the cold start (CUDA events
+    on the library's stream; the step is also the graph capture, a few ms of
+    host work against seconds of device work at the large size)."""
+    import torch
+    w = synth.WORKLOADS[name]
+    A = synth.system(w["n"], w["l"], w["s"], 0)
+    stream = torch.cuda.Stream()
+    h = bd.psdp_setup(w["n"], w["l"], w["d_p"], w["d1"], A,
+                      bd.psdp_default_opts(stream=stream.cuda_stream, device=device, precision=0))
+    try:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s, info = bd.psdp_step(h)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if s != 0:
+            raise RuntimeError(f"fp64 step: {bd.STATUS[s]}")
+        return e0.elapsed_time(e1)
+    finally:
+        bd.psdp_destroy(h)
+
+
 def measure_batch(bd, synth, count, device, n_range=(8, 48), precision=1):
     """Uneven instances drawn like the batched workload (n ~ U{8..48}, l ~ U{2,3,4},
     d_p ~ U{1,2}, d1 ~ U{1..4}, s ~ U[0.05, 3]) solved together in one batch graph
@@ -479,13 +504,20 @@ def run_ours(args):
     # ---- mixed precision (3xTF32 tensor cores + FP64 PCG) on the mid and large workloads
     mixed = {}
     if args.mixed:
-        for wl in ("mid", "large"):
+        for wl in [x for x in args.mixed_workloads.split(",") if x]:
             try:
                 mixed[wl] = measure_mixed(bd, synth, wl, local, args.mixed_steps)
             except Exception as exc:   # report, do not lose the main line
                 mixed[wl] = {"error": str(exc)[:200]}
         if "mid" in mixed and "ms_per_step" in mixed["mid"]:
             mixed["mid"]["speedup_vs_plain_fp64_step"] = (tot_ms / args.steps) / mixed["mid"]["ms_per_step"]
+        if args.fp64_large and "ms_per_step" in mixed.get("large", {}):
+            try:
+                f64 = measure_fp64_step(bd, synth, "large", local)
+                mixed["large"]["plain_fp64_ms_per_step"] = f64
+                mixed["large"]["speedup_vs_plain_fp64_step"] = f64 / mixed["large"]["ms_per_step"]
+            except Exception as exc:
+                mixed["large"]["plain_fp64_error"] = str(exc)[:200]
 
     # ---- CPU oracle baseline on a bounded sample
     ct = oracle_steps(A, w, args.cpu_steps)

@@ -235,6 +235,16 @@ void* psdp_stream(psdp_ctx* c);
  * Errors: EINVAL on bad sizes/flags, ETIMEOUT if a bounded device wait expired. */
 psdp_status psdp_tc_gemm_check(int M, int N, int K, int dtype, int split, const void* A, const void* B, float* C);
 
+/* Self-test of the persistent tcgen05 update used for the FP32 Cholesky trailing
+ * update (no counterpart in the paper).  A: M x K, B: N x K row-major float32;
+ * C: M x N column-major (C[n*M + m]), in/out.  On every 128 x 128 tile (mt, nt)
+ * with mt >= nt when tri (all tiles otherwise): C <- C - A B^T, the product in
+ * TF32 (split 1) or 3xTF32 (split 3); other tiles are left as they are.  ctas =
+ * persistent CTAs (>= 1; fewer CTAs walk more tiles each).  Allocates its own
+ * scratch.  Errors: EINVAL on bad sizes, ETIMEOUT if a bounded wait expired. */
+psdp_status psdp_tc_gemm_persist_check(int M, int N, int K, int split, int tri, int ctas, const float* A,
+                                       const float* B, float* C);
+
 /* Allocation-free variant of psdp_tc_gemm_check (dtype 0); the paper has no
  * counterpart.  For callers that cannot allocate device memory where they need
  * the product: code inside a CUDA graph capture in global mode, allocator or

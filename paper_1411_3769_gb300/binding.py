@@ -28,7 +28,7 @@ EXPORTS = ("psdp_default_opts", "psdp_setup", "psdp_sizes", "psdp_step", "psdp_s
            "psdp_grid_check", "psdp_get_P", "psdp_get_y", "psdp_get_tables", "psdp_load_iterate",
            "psdp_get_iterate", "psdp_get_schur", "psdp_apply_BT", "psdp_apply_B", "psdp_profile_enable",
            "psdp_profile_reset", "psdp_profile_get", "psdp_work", "psdp_stream", "psdp_fp64_peak",
-           "psdp_destroy", "psdp_strerror", "psdp_tc_gemm_check", "psdp_get_schur_mixed",
+           "psdp_destroy", "psdp_strerror", "psdp_tc_gemm_check", "psdp_tc_gemm_persist_check", "psdp_get_schur_mixed",
            "psdp_tc_gemm_noalloc", "psdp_solve_batch", "psdp_autotune", "psdp_set_start", "psdp_mlp_create",
            "psdp_mlp_destroy", "psdp_mlp_params", "psdp_mlp_grads", "psdp_mlp_train", "psdp_mlp_predict")
 
@@ -83,6 +83,8 @@ def _lib():
             "psdp_destroy": (None, [vp]),
             "psdp_strerror": (C.c_char_p, [C.c_int]),
             "psdp_tc_gemm_check": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp]),
+            "psdp_tc_gemm_persist_check": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp,
+                                                     vp]),
             "psdp_get_schur_mixed": (C.c_int, [vp, vp]),
             "psdp_tc_gemm_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]),
             "psdp_solve_batch": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
@@ -282,6 +284,19 @@ def psdp_tc_gemm_check(A: np.ndarray, B: np.ndarray, split: int = 1) -> np.ndarr
     C_ = np.zeros((N, M), dtype=np.float32)
     _check(_lib().psdp_tc_gemm_check(M, N, K, dtype, split, A.ctypes.data, B.ctypes.data, C_.ctypes.data),
            "psdp_tc_gemm_check")
+    return C_.T
+
+
+def psdp_tc_gemm_persist_check(A: np.ndarray, B: np.ndarray, C0: np.ndarray, split: int = 3, tri: int = 1,
+                               ctas: int = 152) -> np.ndarray:
+    """C0 - A B^T on the (lower-triangular when tri) 128 x 128 tiles by the persistent kernel; float32."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    M, K = A.shape
+    N = B.shape[0]
+    C_ = np.ascontiguousarray(np.asarray(C0, dtype=np.float32).T)    # [N][M]: C[n*M + m]
+    _check(_lib().psdp_tc_gemm_persist_check(M, N, K, split, tri, ctas, A.ctypes.data, B.ctypes.data,
+                                             C_.ctypes.data), "psdp_tc_gemm_persist_check")
     return C_.T
 
 

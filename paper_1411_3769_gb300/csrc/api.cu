@@ -214,8 +214,13 @@ void enqueue_schur_mixed(psdp_ctx* c) {
     }
 }
 
-// FP32 Cholesky of Omega32: diagonal blocks in FP64 arithmetic, panel TRSM on
-// CUDA cores, trailing update as a 3xTF32 tensor-core SYRK, with the same
+// SMs the persistent trailing update leaves free for the panel factor, the
+// panel solve and the next-rows update of the look-ahead.
+constexpr int kCritSms = 16;
+
+// FP32 Cholesky of Omega32: diagonal blocks factored and inverted in FP32 shared
+// memory, panel TRSM on CUDA cores, trailing update as a persistent 3xTF32
+// tensor-core SYRK (the next panel's rows by the one-tile-per-CTA form), with the same
 // depth-one look-ahead as the FP64 factorisation.  The packed panel (hi, lo) is
 // double-buffered by panel parity: trsm(p+1) writes one buffer while the bulk
 // update p still reads the other (update p-1, the last reader of the buffer
@@ -265,9 +270,10 @@ void enqueue_cholesky_mixed(psdp_ctx* c) {
                            c->d_flag);
         }
         if (rest > w2) {
+            // persistent CTAs leave a few SMs to the critical-path kernels
             ProfScope q(c, "chol32_syrk_tc", st);
-            launch_tc_gemm(st, false, 3, hib, hib, &lob, &lob, rest - w2, rest - w2, 1, 0, nullptr, w,
-                           T + (int64_t)w2 * K + w2, K, 0, -1.f, 1.f, 1, c->d_flag);
+            launch_tc_gemm_persist(st, 3, hib, hib, &lob, &lob, rest - w2, rest - w2, w, T + (int64_t)w2 * K + w2, K,
+                                   -1.f, 1.f, 1, std::max(1, c->num_sms - kCritSms), c->d_flag);
         }
     }
     stream_dep(cs, st, c->ev_join);
@@ -589,7 +595,8 @@ psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psd
     for (int64_t i = 0; i < Na * n * n; ++i)
         if (!std::isfinite(A[i])) return PSDP_EINVAL;
     if (cudaSetDevice(opt.device) != cudaSuccess) { cudaGetLastError(); return PSDP_ECUDA; }
-    int smem_max = 0;
+    int smem_max = 0, num_sms = 0;
+    cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, opt.device);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, opt.device);
     if ((size_t)2 * n * (n + 1) * sizeof(double) + 4 * n * sizeof(double) > (size_t)smem_max) return PSDP_EINVAL;
     init_attrs_linalg(smem_max);
@@ -607,6 +614,7 @@ psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psd
     c->nblk = (int)(L + M); c->n2 = n * n;
     c->opt = opt;
     c->device = opt.device;
+    c->num_sms = std::max(1, num_sms);
     c->mixed = opt.precision == PSDP_MIXED;
     c->flops_chol = (double)K * K * K / 3.0;
     if (opt.stream) {

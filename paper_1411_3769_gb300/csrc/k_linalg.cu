@@ -100,6 +100,42 @@ k_bgemm(int n, int count, const double* __restrict__ A, const int32_t* __restric
     }
 }
 
+// n <= 32: one CTA per product, one thread per output element and an exact
+// k loop, so no FP64 issue slot is spent on padding (a 32 x 32 tile over a
+// 20 x 20 product would issue 4x the useful DFMAs).
+__global__ void __launch_bounds__(1024)
+k_bgemm_small(int n, int count, const double* __restrict__ A, const int32_t* __restrict__ ia, int sa, int ta,
+              const double* __restrict__ B, const int32_t* __restrict__ ib, int sb, int tb,
+              double* C, const int32_t* __restrict__ ic, int sc, int tc, double alpha, double beta,
+              const int* skip) {
+    if (skip && *skip) return;
+    __shared__ double As[32][33];   // As[i][k] = op(A)(i, k)
+    __shared__ double Bs[32][33];   // Bs[k][j] = op(B)(k, j)
+    const int n2 = n * n, t = threadIdx.x;
+    const int i = t / n, j = t - (t / n) * n;
+    for (int e = blockIdx.x; e < count; e += gridDim.x) {
+        const double* Ae = A + (size_t)(ia ? ia[e] : e * sa) * n2;
+        const double* Be = B + (size_t)(ib ? ib[e] : e * sb) * n2;
+        double* Ce = C + (size_t)(ic ? ic[e] : e * sc) * n2;
+        for (int idx = t; idx < n2; idx += blockDim.x) {
+            const int r = idx / n, q = idx - (idx / n) * n;   // element (r, q) of the stored matrix
+            const double a = Ae[idx], b = Be[idx];
+            if (ta) As[q][r] = a; else As[r][q] = a;
+            if (tb) Bs[q][r] = b; else Bs[r][q] = b;
+        }
+        __syncthreads();
+        if (t < n2) {
+            double acc = 0.0;
+            for (int k = 0; k < n; ++k) acc = fma(As[i][k], Bs[k][j], acc);
+            const size_t o = tc ? (size_t)j * n + i : (size_t)i * n + j;
+            double val = alpha * acc;
+            if (beta != 0.0) val += beta * Ce[o];
+            Ce[o] = val;
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------------ TN GEMM
 // C[r][c] = alpha * sum_k A[k*lda + r] * B[k*ldb + c] + beta * C[r*ldc + c]
 // Tiles of TM x TN outputs on a 16 x 16 thread grid (micro-tiles of
@@ -474,6 +510,12 @@ void launch_bgemm(cudaStream_t st, int n, int count, const double* A, const int3
                   const double* B, const int32_t* ib, int sb, int tb, double* C, const int32_t* ic, int sc,
                   int tc, double alpha, double beta, const int* skip) {
     if (count <= 0) return;
+    if (n <= 32) {
+        const int threads = (n * n + 31) / 32 * 32;
+        k_bgemm_small<<<count < 65535 ? count : 65535, threads, 0, st>>>(n, count, A, ia, sa, ta, B, ib, sb, tb, C, ic,
+                                                                         sc, tc, alpha, beta, skip);
+        return;
+    }
     const int tiles = (n + BG - 1) / BG;
     dim3 grid(tiles * tiles, count < 65535 ? count : 65535);
     k_bgemm<<<grid, kThreads, 0, st>>>(n, count, A, ia, sa, ta, B, ib, sb, tb, C, ic, sc, tc, alpha, beta, skip);
@@ -491,6 +533,12 @@ void launch_gemm_tn(cudaStream_t st, int m, int ncol, int batch, const double* A
     if (m <= 32) {
         dim3 grid((ncol + 15) / 16, (m + 31) / 32, batch);
         k_gemm_tn<32, 16><<<grid, kThreads, 0, st>>>(m, ncol, A, lda, a_off, a_stride, B, ldb, b_off, b_stride, kd,
+                                                     kd_uniform, C, ldc, c_stride, alpha, beta, tri);
+    } else if (m == ncol && m % 80 == 0 && m % 64 != 0 && !tri) {
+        // square products whose side 80 divides and 64 does not (n^2 = 400 for
+        // n = 20): 80 x 80 tiles issue no DFMA on padding
+        dim3 grid(ncol / 80, m / 80, batch);
+        k_gemm_tn<80, 80><<<grid, kThreads, 0, st>>>(m, ncol, A, lda, a_off, a_stride, B, ldb, b_off, b_stride, kd,
                                                      kd_uniform, C, ldc, c_stride, alpha, beta, tri);
     } else if (big < 2 * 152) {
         dim3 grid((ncol + 31) / 32, (m + 31) / 32, batch);

@@ -18,6 +18,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "psdp_internal.h"
@@ -252,6 +253,198 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtens
     }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Tiles of one (optionally lower-triangular, tiles mt >= nt) M x N update,
+// column by column: nt ascending, mt ascending inside a column.
+struct TileWalk {
+    int MT, NT, tri, nt, off;
+    __device__ TileWalk(int M, int N, int tri_, int start)
+        : MT((M + BM - 1) / BM), NT((N + BN - 1) / BN), tri(tri_), nt(0), off(start) { settle(); }
+    __device__ int len(int c) const { return tri ? (MT > c ? MT - c : 0) : MT; }
+    __device__ void settle() {
+        while (nt < NT && off >= len(nt)) {
+            off -= len(nt);
+            ++nt;
+        }
+    }
+    __device__ bool valid() const { return nt < NT; }
+    __device__ int mt() const { return tri ? nt + off : off; }
+    __device__ void advance(int step) {
+        off += step;
+        settle();
+    }
+};
+
+// Persistent form of k_tc_gemm for one large update (batch 1): one CTA per SM
+// walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...  Warp 0 issues the
+// TMA loads, warp 1 the MMAs (and owns TMEM), warps 2-5 drain the accumulator.
+// Two TMEM accumulators of BN columns alternate between tiles, so the epilogue
+// of one tile (which reads and writes C in HBM) runs under the MMAs and loads of
+// the next.  Barriers: full/empty per stage (TMA <-> MMA), tfull/tempty per
+// accumulator (MMA <-> epilogue, tempty counts the four epilogue warps).
+template <int SPLIT, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+k_tc_gemm_persist(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
+                  const __grid_constant__ CUtensorMap mAlo, const __grid_constant__ CUtensorMap mBlo, int M, int N,
+                  int Kd, float* C, int64_t ldc, float alpha, float beta, int tri, int* flag) {
+    constexpr int STAGE_BYTES = (SPLIT == 3) ? 2 * (TILE_A + TILE_B) : (TILE_A + TILE_B);
+    constexpr int BK = 32;                        // TF32 elements per 128-byte row
+    constexpr int KSTEP_BYTES = 32;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t base_raw = smem_u32(smem_raw);
+    const uint32_t base = (base_raw + 1023u) & ~1023u;
+    uint8_t* gbase = smem_raw + (base - base_raw);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + STAGES * STAGE_BYTES);
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+    __shared__ int abort_flag;
+    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * STAGES;
+    const uint32_t tfull0 = full0 + 16 * STAGES, tempty0 = tfull0 + 16, drain = tfull0 + 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = (Kd + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull0 + 8 * b, 1);
+            mbar_init(tempty0 + 8 * b, 4);
+        }
+        mbar_init(drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(2 * BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_holder;
+
+    if (nk > 0 && warp == 0 && lane == 0) {
+        // TMA producer
+        int g = 0;
+        for (TileWalk t(M, N, tri, blockIdx.x); t.valid() && !*(volatile int*)&abort_flag; t.advance(gridDim.x)) {
+            const int m0 = t.mt() * BM, n0 = t.nt * BN;
+            for (int kt = 0; kt < nk; ++kt, ++g) {
+                const int s = g % STAGES;
+                if (g >= STAGES && !mbar_wait(empty0 + 8 * s, ((g / STAGES) - 1) & 1, flag)) {
+                    abort_flag = 1;
+                    break;
+                }
+                const uint32_t st = base + s * STAGE_BYTES;
+                const uint32_t fb = full0 + 8 * s;
+                mbar_expect_tx(fb, STAGE_BYTES);
+                tma_load_3d(st, &mA, fb, kt * BK, m0, 0);
+                tma_load_3d(st + TILE_A, &mB, fb, kt * BK, n0, 0);
+                if constexpr (SPLIT == 3) {
+                    tma_load_3d(st + TILE_A + TILE_B, &mAlo, fb, kt * BK, m0, 0);
+                    tma_load_3d(st + 2 * TILE_A + TILE_B, &mBlo, fb, kt * BK, n0, 0);
+                }
+            }
+        }
+        // every issued stage has landed before the CTA may exit
+        for (int q = (g > STAGES ? g - STAGES : 0); q < g; ++q) mbar_wait(full0 + 8 * (q % STAGES), (q / STAGES) & 1, flag);
+    } else if (nk > 0 && warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = make_idesc<false>();
+        int g = 0, i = 0;
+        bool issued = false;
+        for (TileWalk t(M, N, tri, blockIdx.x); t.valid() && !*(volatile int*)&abort_flag; t.advance(gridDim.x), ++i) {
+            const int b = i & 1;
+            const uint32_t tacc = tmem + (uint32_t)(b * BN);
+            if (i >= 2 && !mbar_wait(tempty0 + 8 * b, ((i >> 1) - 1) & 1, flag)) {
+                abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int kt = 0; kt < nk; ++kt, ++g) {
+                const int s = g % STAGES;
+                if (!mbar_wait(full0 + 8 * s, (g / STAGES) & 1, flag)) {
+                    abort_flag = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t st = base + s * STAGE_BYTES;
+                const uint32_t aH = st, bH = st + TILE_A;
+#pragma unroll
+                for (int kk = 0; kk < ROW_BYTES / KSTEP_BYTES; ++kk) {
+                    const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+                    mma<false>(tacc, sdesc(aH + kk * KSTEP_BYTES), sdesc(bH + kk * KSTEP_BYTES), idesc, acc);
+                    if constexpr (SPLIT == 3) {
+                        const uint32_t aL = st + TILE_A + TILE_B, bL = st + 2 * TILE_A + TILE_B;
+                        mma<false>(tacc, sdesc(aH + kk * KSTEP_BYTES), sdesc(bL + kk * KSTEP_BYTES), idesc, 1u);
+                        mma<false>(tacc, sdesc(aL + kk * KSTEP_BYTES), sdesc(bH + kk * KSTEP_BYTES), idesc, 1u);
+                    }
+                }
+                issued = true;
+                mma_commit(empty0 + 8 * s);
+            }
+            if (*(volatile int*)&abort_flag) break;
+            mma_commit(tfull0 + 8 * b);
+        }
+        // all MMAs complete before TMEM is released
+        if (issued) {
+            mma_commit(drain);
+            mbar_wait(drain, 0, flag);
+        }
+    } else if (warp >= 2) {
+        // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (rows m0 + 32*(w%4) + lane)
+        const int qd = warp & 3;
+        int i = 0;
+        for (TileWalk t(M, N, tri, blockIdx.x); t.valid(); t.advance(gridDim.x), ++i) {
+            const int b = i & 1;
+            const int m0 = t.mt() * BM, n0 = t.nt * BN;
+            const int m = m0 + 32 * qd + lane;
+            float old[BN];
+#pragma unroll
+            for (int j = 0; j < BN; ++j) old[j] = 0.f;
+            if (beta != 0.f && m < M) {
+#pragma unroll
+                for (int j = 0; j < BN; ++j) {
+                    const int n = n0 + j;
+                    if (n < N) old[j] = C[(int64_t)n * ldc + m];
+                }
+            }
+            // warp-uniform decision: the TMEM loads below are warp-collective
+            const bool ok = __all_sync(0xffffffffu, nk > 0 && mbar_wait(tfull0 + 8 * b, (i >> 1) & 1, flag));
+            if (!ok) {
+                if (nk > 0) abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                uint32_t r[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(b * BN + c0), r);
+                if (m < M) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int n = n0 + c0 + j;
+                        if (n < N) C[(int64_t)n * ldc + m] = alpha * __uint_as_float(r[j]) + beta * old[c0 + j];
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN));
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -269,6 +462,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
 template <bool BF16, int SPLIT, int STAGES>
 constexpr size_t smem_bytes() {
     return (size_t)STAGES * ((SPLIT == 3) ? 2 * (TILE_A + TILE_B) : (TILE_A + TILE_B)) + 1024 + 8 * (2 * STAGES + 1) + 16;
+}
+
+template <int SPLIT, int STAGES>
+constexpr size_t smem_bytes_persist() {
+    return (size_t)STAGES * ((SPLIT == 3) ? 2 * (TILE_A + TILE_B) : (TILE_A + TILE_B)) + 1024 +
+           8 * (2 * STAGES + 5) + 16;
 }
 
 }  // namespace
@@ -313,7 +512,30 @@ bool launch_tc_gemm(cudaStream_t st, bool bf16, int split, const CUtensorMap& A,
     return true;
 }
 
+// Persistent TF32 update of one M x N matrix (batch 1, maps with batch extent 1):
+// C[n*ldc + m] = alpha * sum_k A[m][k] B[n][k] + beta * C, lower-triangular tiles
+// only when tri.  ctas = number of persistent CTAs (at most the tile count).
+bool launch_tc_gemm_persist(cudaStream_t st, int split, const CUtensorMap& A, const CUtensorMap& B,
+                            const CUtensorMap* Alo, const CUtensorMap* Blo, int M, int N, int kd, float* C,
+                            int64_t ldc, float alpha, float beta, int tri, int ctas, int* flag) {
+    if (M <= 0 || N <= 0 || kd <= 0) return true;
+    const int64_t MT = (M + BM - 1) / BM, NT = (N + BN - 1) / BN;
+    int64_t tiles = 0;
+    for (int64_t c = 0; c < NT; ++c) tiles += tri ? std::max<int64_t>(0, MT - c) : MT;
+    if (tiles == 0) return true;
+    const int grid = (int)std::min<int64_t>(tiles, std::max(1, ctas));
+    if (split == 3)
+        k_tc_gemm_persist<3, 3><<<grid, 192, smem_bytes_persist<3, 3>(), st>>>(A, B, *Alo, *Blo, M, N, kd, C, ldc,
+                                                                              alpha, beta, tri, flag);
+    else
+        k_tc_gemm_persist<1, 4><<<grid, 192, smem_bytes_persist<1, 4>(), st>>>(A, B, A, B, M, N, kd, C, ldc, alpha,
+                                                                              beta, tri, flag);
+    return true;
+}
+
 void init_attrs_tc(int smem_optin) {
+    set_max_dynamic_smem((const void*)k_tc_gemm_persist<3, 3>, smem_optin);
+    set_max_dynamic_smem((const void*)k_tc_gemm_persist<1, 4>, smem_optin);
     set_max_dynamic_smem((const void*)k_tc_gemm<true, 1, 4>, smem_optin);
     set_max_dynamic_smem((const void*)k_tc_gemm<false, 3, 3>, smem_optin);
     set_max_dynamic_smem((const void*)k_tc_gemm<false, 1, 4>, smem_optin);
@@ -397,6 +619,57 @@ extern "C" psdp_status psdp_tc_gemm_check(int M, int N, int K, int dtype, int sp
     }
     for (void* p : {dA, dB, dAl, dBl, dAh, dBh, (void*)dC, (void*)dflag})
         if (p) cudaFree(p);
+    cudaStreamDestroy(st);
+    cudaGetLastError();
+    return s;
+}
+
+extern "C" psdp_status psdp_tc_gemm_persist_check(int M, int N, int K, int split, int tri, int ctas, const float* A,
+                                                  const float* B, float* C) {
+    if (M < 1 || N < 1 || K < 1 || !A || !B || !C || (split != 1 && split != 3) || ctas < 1) return PSDP_EINVAL;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    init_attrs_tc(optin);
+    const int kpad = (K + 31) / 32 * 32;   // 128-byte rows
+    float *dA = nullptr, *dB = nullptr, *dAl = nullptr, *dBl = nullptr, *dAh = nullptr, *dBh = nullptr, *dC = nullptr;
+    int* dflag = nullptr;
+    psdp_status s = PSDP_OK;
+    cudaStream_t st;
+    cudaStreamCreate(&st);
+    auto al = [&](float** q, size_t n) { if (cudaMalloc((void**)q, n * 4) != cudaSuccess) s = PSDP_ENOMEM; };
+    al(&dA, (size_t)M * kpad); al(&dB, (size_t)N * kpad); al(&dC, (size_t)M * N);
+    al(&dAh, (size_t)M * kpad); al(&dAl, (size_t)M * kpad); al(&dBh, (size_t)N * kpad); al(&dBl, (size_t)N * kpad);
+    if (cudaMalloc((void**)&dflag, 4) != cudaSuccess) s = PSDP_ENOMEM;
+    if (s == PSDP_OK) {
+        cudaMemset(dA, 0, (size_t)M * kpad * 4);
+        cudaMemset(dB, 0, (size_t)N * kpad * 4);
+        cudaMemset(dflag, 0, 4);
+        cudaMemcpy2D(dA, (size_t)kpad * 4, A, (size_t)K * 4, (size_t)K * 4, M, cudaMemcpyHostToDevice);
+        cudaMemcpy2D(dB, (size_t)kpad * 4, B, (size_t)K * 4, (size_t)K * 4, N, cudaMemcpyHostToDevice);
+        cudaMemcpy(dC, C, (size_t)M * N * 4, cudaMemcpyHostToDevice);
+        CUtensorMap mA, mB, mAl, mBl;
+        bool ok;
+        if (split == 3) {
+            launch_split_tf32(st, (int64_t)M * kpad, dA, dAh, dAl);
+            launch_split_tf32(st, (int64_t)N * kpad, dB, dBh, dBl);
+            ok = tc_make_map(&mA, dAh, false, K, M, 1, kpad, 0, 128) && tc_make_map(&mB, dBh, false, K, N, 1, kpad, 0, 128) &&
+                 tc_make_map(&mAl, dAl, false, K, M, 1, kpad, 0, 128) && tc_make_map(&mBl, dBl, false, K, N, 1, kpad, 0, 128);
+            if (ok) launch_tc_gemm_persist(st, 3, mA, mB, &mAl, &mBl, M, N, K, dC, M, -1.f, 1.f, tri, ctas, dflag);
+        } else {
+            ok = tc_make_map(&mA, dA, false, K, M, 1, kpad, 0, 128) && tc_make_map(&mB, dB, false, K, N, 1, kpad, 0, 128);
+            if (ok) launch_tc_gemm_persist(st, 1, mA, mB, nullptr, nullptr, M, N, K, dC, M, -1.f, 1.f, tri, ctas, dflag);
+        }
+        if (!ok) s = PSDP_ECUDA;
+        int flag = 0;
+        if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) s = PSDP_ECUDA;
+        cudaMemcpy(&flag, dflag, 4, cudaMemcpyDeviceToHost);
+        if (flag) s = PSDP_ETIMEOUT;
+        if (s == PSDP_OK) cudaMemcpy(C, dC, (size_t)M * N * 4, cudaMemcpyDeviceToHost);
+    }
+    for (float* q : {dA, dB, dAl, dBl, dAh, dBh, dC})
+        if (q) cudaFree(q);
+    if (dflag) cudaFree(dflag);
     cudaStreamDestroy(st);
     cudaGetLastError();
     return s;

@@ -53,6 +53,7 @@ struct psdp_ctx {
     int L0, L, M, Na, Nt, K, nblk, n2;
     psdp_opts opt;
     int device;
+    int num_sms = 1;
     cudaStream_t stream;
     bool own_stream;
     // high-priority stream for the Cholesky critical path (panel factor, panel
@@ -238,6 +239,9 @@ bool launch_tc_gemm(cudaStream_t st, bool bf16, int split, const CUtensorMap& A,
                     const int32_t* kd, int kd_uniform, float* C, int64_t ldc, int64_t c_batch, float alpha,
                     float beta, int tri, int* flag);
 void launch_split_tf32(cudaStream_t st, int64_t n, const float* x, float* hi, float* lo);
+bool launch_tc_gemm_persist(cudaStream_t st, int split, const CUtensorMap& A, const CUtensorMap& B,
+                            const CUtensorMap* Alo, const CUtensorMap* Blo, int M, int N, int kd, float* C,
+                            int64_t ldc, float alpha, float beta, int tri, int ctas, int* flag);
 void init_attrs_tc(int smem_optin);
 
 // mixed precision (k_mixed.cu)

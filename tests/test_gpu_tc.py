@@ -77,3 +77,32 @@ def test_bf16(bd, M, N, K):
     ref = Af @ Bf.T
     scale = np.abs(Af) @ np.abs(Bf).T
     assert np.all(np.abs(D - ref) <= K * 2.0 ** -23 * scale + 1e-6)
+
+
+@pytest.mark.parametrize("M,N,K,split,tri,ctas", [
+    (1000, 1000, 128, 3, 1, 152),   # trailing update shape, one tile per CTA at most
+    (1000, 1000, 128, 3, 1, 5),     # five CTAs walk 36 tiles: accumulator double buffer and stage ring wrap
+    (700, 128, 128, 3, 1, 3),       # next-panel strip (one tile column)
+    (300, 500, 100, 1, 0, 4),       # full update, ragged K and tiles, plain TF32
+    (257, 257, 64, 3, 1, 2),
+])
+def test_persistent_update(bd, M, N, K, split, tri, ctas):
+    """C - A B^T on the selected tiles; the tiles outside are untouched."""
+    rng = np.random.default_rng(M + 3 * K + ctas)
+    A = rng.normal(size=(M, K)).astype(np.float32)
+    B = rng.normal(size=(N, K)).astype(np.float32)
+    C0 = rng.normal(size=(M, N)).astype(np.float32)
+    out = bd.psdp_tc_gemm_persist_check(A, B, C0, split=split, tri=tri, ctas=ctas)
+    mt = (np.arange(M) // 128)[:, None]
+    nt = (np.arange(N) // 128)[None, :]
+    sel = (mt >= nt) if tri else np.ones((M, N), bool)
+    if split == 3:
+        prod = A.astype(np.float64) @ B.astype(np.float64).T
+        tol = 1e-5
+    else:
+        prod = _tf32(A).astype(np.float64) @ _tf32(B).astype(np.float64).T
+        tol = 4 * 2.0 ** -10
+    scale = np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64).T + np.abs(C0)
+    ref = C0.astype(np.float64) - prod
+    assert np.all(np.abs(out - ref)[sel] <= tol * scale[sel] + 1e-5)
+    assert np.array_equal(out[~sel], C0[~sel])
