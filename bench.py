@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--mixed-steps", type=int, default=5)
     ap.add_argument("--fp64-large", type=int, default=1, help="time one plain FP64 step of the large workload")
     ap.add_argument("--mixed-workloads", default="mid,large")
+    ap.add_argument("--extra-items", default="syrk,batch,warm")
+    ap.add_argument("--syrk-m", type=int, default=15000)
     ap.add_argument("--extra", action="store_true", help="measure the batched and warm-start rows instead")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--warm-train", type=int, default=1024)
@@ -347,16 +349,39 @@ def measure_warm(bd, n_train, n_test, device):
     return res
 
 
+def measure_syrk_probe(bd, M, K=128, ctas=152):
+    """The persistent 3xTF32 trailing update alone on an M x M lower-triangular
+    update of depth K (the shape of one FP32 Cholesky panel update), random
+    operands; CUDA events around the launch."""
+    rng = np.random.default_rng(3)
+    P = rng.standard_normal((M, K)).astype(np.float32)
+    C0 = np.zeros((M, M), dtype=np.float32)
+    _, ms = bd.psdp_tc_gemm_persist_check(P, P, C0, split=3, tri=1, ctas=ctas, timing=True)
+    T = (M + 127) // 128
+    tiles = T * (T + 1) // 2
+    c_bytes = tiles * 128 * 128 * 4 * 2            # C read + write per tile
+    flops = tiles * 2.0 * 128 * 128 * K            # useful product (the 3xTF32 split issues 3x)
+    return {"M": M, "K": K, "ctas": ctas, "tiles": tiles, "ms": ms, "c_traffic_gbs": c_bytes / (ms * 1e-3) / 1e9,
+            "useful_tflops": flops / (ms * 1e-3) / 1e12}
+
+
 def run_extra(args):
-    """Batched and learned-warm-start rows (minutes of GPU time; not the default line)."""
+    """Batched, learned-warm-start and kernel-probe rows (minutes of GPU time;
+    not the default line)."""
     import torch
     torch.cuda.set_device(0)
     from paper_1411_3769_gb300 import build
     build.build()
     from paper_1411_3769_gb300 import binding as bd
     from paper_1411_3769_gb300 import synth
-    out = {"batch": measure_batch(bd, synth, args.batch_count, 0)}
-    out["warm_start"] = measure_warm(bd, args.warm_train, args.warm_test, 0)
+    items = [x for x in args.extra_items.split(",") if x]
+    out = {}
+    if "syrk" in items:
+        out["syrk_probe"] = [measure_syrk_probe(bd, args.syrk_m, ctas=c) for c in (152, 136)]
+    if "batch" in items:
+        out["batch"] = measure_batch(bd, synth, args.batch_count, 0)
+    if "warm" in items:
+        out["warm_start"] = measure_warm(bd, args.warm_train, args.warm_test, 0)
     print(json.dumps(out), flush=True)
 
 

@@ -240,10 +240,11 @@ psdp_status psdp_tc_gemm_check(int M, int N, int K, int dtype, int split, const 
  * C: M x N column-major (C[n*M + m]), in/out.  On every 128 x 128 tile (mt, nt)
  * with mt >= nt when tri (all tiles otherwise): C <- C - A B^T, the product in
  * TF32 (split 1) or 3xTF32 (split 3); other tiles are left as they are.  ctas =
- * persistent CTAs (>= 1; fewer CTAs walk more tiles each).  Allocates its own
- * scratch.  Errors: EINVAL on bad sizes, ETIMEOUT if a bounded wait expired. */
+ * persistent CTAs (>= 1; fewer CTAs walk more tiles each).  ms (may be NULL)
+ * receives the kernel's duration from CUDA events around the launch.  Allocates
+ * its own scratch.  Errors: EINVAL on bad sizes, ETIMEOUT if a bounded wait expired. */
 psdp_status psdp_tc_gemm_persist_check(int M, int N, int K, int split, int tri, int ctas, const float* A,
-                                       const float* B, float* C);
+                                       const float* B, float* C, float* ms);
 
 /* Allocation-free variant of psdp_tc_gemm_check (dtype 0); the paper has no
  * counterpart.  For callers that cannot allocate device memory where they need

@@ -84,7 +84,7 @@ def _lib():
             "psdp_strerror": (C.c_char_p, [C.c_int]),
             "psdp_tc_gemm_check": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp]),
             "psdp_tc_gemm_persist_check": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp,
-                                                     vp]),
+                                                     vp, vp]),
             "psdp_get_schur_mixed": (C.c_int, [vp, vp]),
             "psdp_tc_gemm_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]),
             "psdp_solve_batch": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
@@ -288,16 +288,18 @@ def psdp_tc_gemm_check(A: np.ndarray, B: np.ndarray, split: int = 1) -> np.ndarr
 
 
 def psdp_tc_gemm_persist_check(A: np.ndarray, B: np.ndarray, C0: np.ndarray, split: int = 3, tri: int = 1,
-                               ctas: int = 152) -> np.ndarray:
-    """C0 - A B^T on the (lower-triangular when tri) 128 x 128 tiles by the persistent kernel; float32."""
+                               ctas: int = 152, timing: bool = False):
+    """C0 - A B^T on the (lower-triangular when tri) 128 x 128 tiles by the persistent kernel; float32.
+    With timing=True also returns the kernel's duration in ms."""
     A = np.ascontiguousarray(A, dtype=np.float32)
     B = np.ascontiguousarray(B, dtype=np.float32)
     M, K = A.shape
     N = B.shape[0]
     C_ = np.ascontiguousarray(np.asarray(C0, dtype=np.float32).T)    # [N][M]: C[n*M + m]
+    ms = np.zeros(1, dtype=np.float32)
     _check(_lib().psdp_tc_gemm_persist_check(M, N, K, split, tri, ctas, A.ctypes.data, B.ctypes.data,
-                                             C_.ctypes.data), "psdp_tc_gemm_persist_check")
-    return C_.T
+                                             C_.ctypes.data, ms.ctypes.data), "psdp_tc_gemm_persist_check")
+    return (C_.T, float(ms[0])) if timing else C_.T
 
 
 def psdp_tc_gemm_noalloc(M: int, N: int, K: int, split: int, A_ptr: int, B_ptr: int, C_ptr: int,

@@ -235,20 +235,29 @@ void enqueue_cholesky_mixed(psdp_ctx* c) {
         float* Lp = c->d_Linv32 + (size_t)p * nb * nb;
         {
             ProfScope q(c, "chol32_potrf_diag", cs);
-            launch_potrf_diag32(cs, A, K, j0, nb, Lp, c->d_flag);
+            launch_potrf_diag32(cs, A, K, j0, nb, Lp, c->d_Lt_hi, c->d_Lt_lo, c->d_flag);
         }
         const int rest = K - j0 - w;
         if (rest <= 0) break;
         float* phi = c->d_Pt_hi + (size_t)(p & 1) * K * nb;
         float* plo = c->d_Pt_lo + (size_t)(p & 1) * K * nb;
-        {
+        CUtensorMap pkh, pkl, lth, ltl;
+        bool ok = tc_make_map(&pkh, c->d_Pk_hi, false, w, rest, 1, nb, 0, 128) &&
+                  tc_make_map(&pkl, c->d_Pk_lo, false, w, rest, 1, nb, 0, 128) &&
+                  tc_make_map(&lth, c->d_Lt_hi, false, w, w, 1, nb, 0, 128) &&
+                  tc_make_map(&ltl, c->d_Lt_lo, false, w, w, 1, nb, 0, 128);
+        if (ok) {
+            // panel solve P L_jj^{-T} on the tensor cores (3xTF32): written back
+            // to Omega's panel rows and, as TF32 pairs, packed for the update
             ProfScope q(c, "chol32_trsm", cs);
-            launch_trsm32_pack(cs, A, K, j0, nb, Lp, phi, plo);
+            launch_pack_panel32(cs, A, K, j0, nb, c->d_Pk_hi, c->d_Pk_lo);
+            launch_tc_gemm(cs, false, 3, pkh, lth, &pkl, &ltl, rest, w, 1, 0, nullptr, w, A + (int64_t)j0 * K + j0 + w,
+                           K, 0, 1.f, 0.f, 0, c->d_flag, phi, plo, nb);
         }
         const int w2 = std::min(nb, rest);
         float* T = A + (int64_t)(j0 + w) * K + j0 + w;
         CUtensorMap hi, lo, hi2, lo2, hib, lob;
-        bool ok = tc_make_map(&hi, phi, false, w, rest, 1, nb, 0, 128) &&
+        ok = ok && tc_make_map(&hi, phi, false, w, rest, 1, nb, 0, 128) &&
                   tc_make_map(&lo, plo, false, w, rest, 1, nb, 0, 128) &&
                   tc_make_map(&hi2, phi, false, w, w2, 1, nb, 0, 128) &&
                   tc_make_map(&lo2, plo, false, w, w2, 1, nb, 0, 128);
@@ -414,7 +423,7 @@ void free_ctx(psdp_ctx* c) {
                     c->d_term_desc, c->d_term_w, c->d_uv_idx, c->d_prod_idx, c->d_U, c->d_V, c->d_Aop, c->d_Bop,
                     c->d_Tbuf, c->d_Om, c->d_Linv, c->d_grid, c->d_svec, c->d_cert, c->d_term_off_t,
                     c->d_opA_hi, c->d_opA_lo, c->d_opB_hi, c->d_opB_lo, c->d_prodA, c->d_prodB, c->d_T32,
-                    c->d_Om32, c->d_Linv32, c->d_Pt_hi, c->d_Pt_lo, c->d_z32, c->d_part32, c->d_trsv_sync, c->d_pcg_x, c->d_pcg_r,
+                    c->d_Om32, c->d_Linv32, c->d_Pt_hi, c->d_Pt_lo, c->d_z32, c->d_part32, c->d_trsv_sync, c->d_Pk_hi, c->d_Pk_lo, c->d_Lt_hi, c->d_Lt_lo, c->d_pcg_x, c->d_pcg_r,
                     c->d_pcg_z, c->d_pcg_p, c->d_pcg_q, c->d_pcg_state, c->d_pcg_done, c->d_M1, c->d_M2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -555,11 +564,16 @@ psdp_status alloc_mixed(psdp_ctx* c) {
     const size_t per_pair = n2 * n2 * sizeof(float);
     c->pairs_per_chunk32 = (int)std::max<size_t>(1, std::min<size_t>((size_t)c->npairs, ((size_t)2 << 30) / per_pair));
     TRY(dalloc(&c->d_T32, (size_t)c->pairs_per_chunk32 * n2 * n2));
-    const int nb = c->nb32, npanel = (c->K + nb - 1) / nb;
+    // sized for the widest panel the autotuner may pick (128), whatever nb32 is now
+    const int nb = std::max(c->nb32, 128), npanel = (c->K + 63) / 64;
     TRY(dalloc(&c->d_Om32, K * K));
-    TRY(dalloc(&c->d_Linv32, (size_t)npanel * nb * nb));
+    TRY(dalloc(&c->d_Linv32, (size_t)npanel * 64 * 64 + (size_t)((c->K + 127) / 128) * 128 * 128));
     TRY(dalloc(&c->d_Pt_hi, 2 * K * nb));   // double-buffered by panel parity
     TRY(dalloc(&c->d_Pt_lo, 2 * K * nb));
+    TRY(dalloc(&c->d_Pk_hi, K * nb));
+    TRY(dalloc(&c->d_Pk_lo, K * nb));
+    TRY(dalloc(&c->d_Lt_hi, nb * nb));
+    TRY(dalloc(&c->d_Lt_lo, nb * nb));
     TRY(dalloc(&c->d_z32, K));
     TRY(dalloc(&c->d_part32, (size_t)nb * (K / 2048 + 2)));
     double** vecs[] = {&c->d_pcg_x, &c->d_pcg_r, &c->d_pcg_z, &c->d_pcg_p, &c->d_pcg_q};

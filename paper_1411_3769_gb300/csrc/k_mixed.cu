@@ -86,7 +86,7 @@ __global__ void k_schur_pack32(int n, int tpad, const int32_t* __restrict__ term
 // factored in FP32 (it only seeds the preconditioner; FP64 PCG fixes the
 // rest); writes L back and L^{-1} (column-major, ld nb).
 __global__ void __launch_bounds__(kThreads)
-k_potrf_diag32(float* A, int K, int j0, int w, int nb, float* Linv, int* flag) {
+k_potrf_diag32(float* A, int K, int j0, int w, int nb, float* Linv, float* LtHi, float* LtLo, int* flag) {
     extern __shared__ float smf[];
     const int ld = w + 1;
     float* L = smf;
@@ -170,8 +170,40 @@ k_potrf_diag32(float* A, int K, int j0, int w, int nb, float* Linv, int* flag) {
     for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
         const int j = idx / nb, i = idx % nb;
         Linv[idx] = (j < w && i < w) ? I[j * ld + i] : 0.f;
+        // row-major copy split into TF32 (hi, lo): LtHi[k*nb + m] ~ Linv(k, m),
+        // the K-major right operand of the tensor-core panel solve
+        const float v = (j < w && i < w) ? I[i * ld + j] : 0.f;    // Linv(j, i)
+        uint32_t h;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
+        LtHi[idx] = __uint_as_float(h);
+        LtLo[idx] = v - __uint_as_float(h);
     }
     if (threadIdx.x == 0 && bad) atomicOr(flag, (int)FL_CHOL_SCHUR);
+}
+
+// Unsolved panel rows packed K-major as TF32 (hi, lo) pairs:
+// Pk[i][m] = P(i, m) = A[(j0 + m) K + j0 + w + i], i < rest, m < w (row length nb).
+__global__ void __launch_bounds__(256)
+k_pack_panel32(const float* __restrict__ A, int K, int j0, int w, int nb, float* PkHi, float* PkLo) {
+    __shared__ float t[32][33];
+    const int rest = K - j0 - w;
+    const int i0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 8 rows of 32
+    for (int r = ty; r < 32; r += 8) {
+        const int m = m0 + r, i = i0 + tx;
+        t[r][tx] = (m < w && i < rest) ? A[(int64_t)(j0 + m) * K + j0 + w + i] : 0.f;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int i = i0 + r, m = m0 + tx;
+        if (i < rest && m < w) {
+            const float v = t[tx][r];
+            uint32_t h;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
+            PkHi[(int64_t)i * nb + m] = __uint_as_float(h);
+            PkLo[(int64_t)i * nb + m] = v - __uint_as_float(h);
+        }
+    }
 }
 
 // Panel rows i in [j0+w, K): P'(i,k) = sum_{m<=k} P(i,m) Linv(k,m), written back
@@ -398,10 +430,19 @@ void launch_schur_pack32(cudaStream_t st, psdp_ctx* c) {
                                            c->d_opA_lo, c->d_opB_hi, c->d_opB_lo);
 }
 
-void launch_potrf_diag32(cudaStream_t st, float* A, int K, int j0, int nb, float* Linv, int* flag) {
+void launch_potrf_diag32(cudaStream_t st, float* A, int K, int j0, int nb, float* Linv, float* LtHi, float* LtLo,
+                         int* flag) {
     const int w = (K - j0 < nb) ? K - j0 : nb;
     const size_t sm = (size_t)2 * w * (w + 1) * sizeof(float);
-    k_potrf_diag32<<<1, kThreads, sm, st>>>(A, K, j0, w, nb, Linv, flag);
+    k_potrf_diag32<<<1, kThreads, sm, st>>>(A, K, j0, w, nb, Linv, LtHi, LtLo, flag);
+}
+
+void launch_pack_panel32(cudaStream_t st, const float* A, int K, int j0, int nb, float* PkHi, float* PkLo) {
+    const int w = (K - j0 < nb) ? K - j0 : nb;
+    const int rest = K - j0 - w;
+    if (rest <= 0) return;
+    dim3 grid((rest + 31) / 32, (w + 31) / 32);
+    k_pack_panel32<<<grid, 256, 0, st>>>(A, K, j0, w, nb, PkHi, PkLo);
 }
 
 void launch_trsm32_pack(cudaStream_t st, float* A, int K, int j0, int nb, const float* Linv, float* PtHi,

@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(128, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
           const __grid_constant__ CUtensorMap mAlo, const __grid_constant__ CUtensorMap mBlo, int M, int N, int b0,
           const int32_t* __restrict__ kd, int kd_uniform, float* C, int64_t ldc, int64_t c_batch, float alpha,
-          float beta, int tri, int* flag) {
+          float beta, int tri, int* flag, float* aux_hi, float* aux_lo, int aux_ld) {
     constexpr int STAGE_BYTES = (SPLIT == 3) ? 2 * (TILE_A + TILE_B) : (TILE_A + TILE_B);
     constexpr int BK = BF16 ? 64 : 32;            // elements per 128-byte row
     constexpr int KSTEP_BYTES = 32;               // bytes of K consumed by one MMA (K = 8 tf32 / 16 bf16)
@@ -238,10 +238,27 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtens
                 for (int j = 0; j < 16; ++j) r[j] = 0u;
             }
             if (m < M) {
+                float v[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int n = n0 + c0 + j;
-                    if (n < N) Cb[(int64_t)n * ldc + m] = alpha * __uint_as_float(r[j]) + beta * old[c0 + j];
+                    v[j] = alpha * __uint_as_float(r[j]) + beta * old[c0 + j];
+                    if (n < N) Cb[(int64_t)n * ldc + m] = v[j];
+                }
+                if (aux_hi) {
+                    // the same values as (hi, lo) TF32 pairs, row-major [m][n]
+                    // (the K-major operand layout of a following product)
+                    float* ph = aux_hi + (int64_t)m * aux_ld + n0 + c0;
+                    float* pl = aux_lo + (int64_t)m * aux_ld + n0 + c0;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        if (n0 + c0 + j < N) {
+                            uint32_t h;
+                            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v[j]));
+                            ph[j] = __uint_as_float(h);
+                            pl[j] = v[j] - __uint_as_float(h);
+                        }
+                    }
                 }
             }
         }
@@ -495,19 +512,21 @@ bool tc_make_map(CUtensorMap* map, const void* base, bool bf16, int64_t kdim, in
 bool launch_tc_gemm(cudaStream_t st, bool bf16, int split, const CUtensorMap& A, const CUtensorMap& B,
                     const CUtensorMap* Alo, const CUtensorMap* Blo, int M, int N, int batch, int b0,
                     const int32_t* kd, int kd_uniform, float* C, int64_t ldc, int64_t c_batch, float alpha,
-                    float beta, int tri, int* flag) {
+                    float beta, int tri, int* flag, float* aux_hi, float* aux_lo, int aux_ld) {
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
     if (grid.x == 0 || grid.y == 0 || batch <= 0) return true;
     if (bf16) {
         k_tc_gemm<true, 1, 4><<<grid, 128, smem_bytes<true, 1, 4>(), st>>>(A, B, A, B, M, N, b0, kd, kd_uniform, C,
-                                                                         ldc, c_batch, alpha, beta, tri, flag);
+                                                                         ldc, c_batch, alpha, beta, tri, flag,
+                                                                         aux_hi, aux_lo, aux_ld);
     } else if (split == 3) {
         k_tc_gemm<false, 3, 3><<<grid, 128, smem_bytes<false, 3, 3>(), st>>>(A, B, *Alo, *Blo, M, N, b0, kd,
                                                                            kd_uniform, C, ldc, c_batch, alpha, beta,
-                                                                           tri, flag);
+                                                                           tri, flag, aux_hi, aux_lo, aux_ld);
     } else {
         k_tc_gemm<false, 1, 4><<<grid, 128, smem_bytes<false, 1, 4>(), st>>>(A, B, A, B, M, N, b0, kd, kd_uniform, C,
-                                                                           ldc, c_batch, alpha, beta, tri, flag);
+                                                                           ldc, c_batch, alpha, beta, tri, flag,
+                                                                           aux_hi, aux_lo, aux_ld);
     }
     return true;
 }
@@ -625,7 +644,7 @@ extern "C" psdp_status psdp_tc_gemm_check(int M, int N, int K, int dtype, int sp
 }
 
 extern "C" psdp_status psdp_tc_gemm_persist_check(int M, int N, int K, int split, int tri, int ctas, const float* A,
-                                                  const float* B, float* C) {
+                                                  const float* B, float* C, float* ms) {
     if (M < 1 || N < 1 || K < 1 || !A || !B || !C || (split != 1 && split != 3) || ctas < 1) return PSDP_EINVAL;
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
@@ -655,11 +674,21 @@ extern "C" psdp_status psdp_tc_gemm_persist_check(int M, int N, int K, int split
             launch_split_tf32(st, (int64_t)N * kpad, dB, dBh, dBl);
             ok = tc_make_map(&mA, dAh, false, K, M, 1, kpad, 0, 128) && tc_make_map(&mB, dBh, false, K, N, 1, kpad, 0, 128) &&
                  tc_make_map(&mAl, dAl, false, K, M, 1, kpad, 0, 128) && tc_make_map(&mBl, dBl, false, K, N, 1, kpad, 0, 128);
-            if (ok) launch_tc_gemm_persist(st, 3, mA, mB, &mAl, &mBl, M, N, K, dC, M, -1.f, 1.f, tri, ctas, dflag);
         } else {
             ok = tc_make_map(&mA, dA, false, K, M, 1, kpad, 0, 128) && tc_make_map(&mB, dB, false, K, N, 1, kpad, 0, 128);
-            if (ok) launch_tc_gemm_persist(st, 1, mA, mB, nullptr, nullptr, M, N, K, dC, M, -1.f, 1.f, tri, ctas, dflag);
         }
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, st);
+        if (ok && split == 3) launch_tc_gemm_persist(st, 3, mA, mB, &mAl, &mBl, M, N, K, dC, M, -1.f, 1.f, tri, ctas, dflag);
+        if (ok && split == 1)
+            launch_tc_gemm_persist(st, 1, mA, mB, nullptr, nullptr, M, N, K, dC, M, -1.f, 1.f, tri, ctas, dflag);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        if (ms) cudaEventElapsedTime(ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
         if (!ok) s = PSDP_ECUDA;
         int flag = 0;
         if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) s = PSDP_ECUDA;

@@ -14,8 +14,12 @@
 // over a fixed index sequence however the solved blocks arrive, so the result
 // is bit-reproducible.  A finished block is published with a release store of
 // its ready flag; readers acquire the flag and read the solved values through
-// L2.  Every wait is bounded (2 s without progress): the CTA sets FL_TIMEOUT
-// and finishes with what it has, so its dependants finish too.
+// L2.  Warp 0 polls, the CTA synchronises once per batch of newly solved
+// blocks, and the tile of the last predecessor is in registers before the
+// wait, so the critical path per block is the flag latency, one W x W tile
+// product from registers and the diagonal-block product.  Every wait is
+// bounded (2 s without progress): the CTA sets FL_TIMEOUT and finishes with
+// what it has, so its dependants finish too.
 //
 // sync: [0] forward ticket, [1] backward ticket, [2, 2+npanel) forward ready
 // flags, [2+npanel, 2+2*npanel) backward ready flags; zeroed before each solve.
@@ -75,27 +79,109 @@ __device__ __forceinline__ void load_vec_cg(const T* p, T* o) {
 template <typename T>
 size_t trsv_smem(int W) { return ((size_t)W * W + (size_t)(TT / W) * W + W) * sizeof(T); }
 
-// Shared wait step: thread 0 decides (progress resets the clock; 2 s without
-// progress sets FL_TIMEOUT), every thread gets the same answer.
-__device__ __forceinline__ bool wait_gives_up(long long& t0, int* flag, int* s_abort) {
-    if (threadIdx.x == 0) {
-        const long long now = gtimer();
-        if (t0 == 0) t0 = now;
-        if (now - t0 > kWaitNs) {
-            atomicOr(flag, (int)FL_TIMEOUT);
-            *s_abort = 1;
+// Pairwise sum of v[0], v[stride], ..., v[(G-1) stride] in a fixed order (G a power of two).
+template <typename T, int G>
+__device__ __forceinline__ T tree_sum(const T* v, int stride) {
+    T b[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) b[g] = v[g * stride];
+#pragma unroll
+    for (int h = G / 2; h >= 1; h >>= 1)
+#pragma unroll
+        for (int i = 0; i < h; ++i) b[i] += b[i + h];
+    return b[0];
+}
+
+// Warp 0 polls the ready flags; returns (to every thread) the first unsolved
+// block at or after qd in [qd, p) (p if all are solved) once it is past qd, or
+// -1 after 2 s without progress (FL_TIMEOUT raised).  slot alternates between
+// calls so a slow warp still reading the previous answer is never overwritten.
+__device__ __forceinline__ int wait_prefix(const unsigned* ready, int qd, int p, int* flag, int* s_q, int slot) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        long long t0 = 0;
+        int qe;
+        for (;;) {
+            int first = p;
+            for (int q = qd + lane; q < p; q += 32)
+                if (ld_acquire(ready + q) == 0u) {
+                    first = q;
+                    break;
+                }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
+            if (first > qd) {
+                qe = first;
+                break;
+            }
+            int give_up = 0;
+            if (lane == 0) {
+                const long long now = gtimer();
+                if (t0 == 0) t0 = now;
+                if (now - t0 > kWaitNs) {
+                    atomicOr(flag, (int)FL_TIMEOUT);
+                    give_up = 1;
+                }
+            }
+            if (__shfl_sync(0xffffffffu, give_up, 0)) {
+                qe = -1;
+                break;
+            }
+            __nanosleep(64);
         }
+        if (lane == 0) s_q[slot] = qe;
     }
     __syncthreads();
-    const bool give_up = *s_abort != 0;
-    if (!give_up) __nanosleep(128);
-    return give_up;
+    return s_q[slot];
+}
+
+// Mirror image for the backward sweep: blocks (p, npanel) are solved from the
+// top down; returns qe < qd such that blocks [qe, qd) are solved and qe-1 is p
+// or unsolved, or -1 on timeout.
+__device__ __forceinline__ int wait_suffix(const unsigned* ready, int qd, int p, int* flag, int* s_q, int slot) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        long long t0 = 0;
+        int qe;
+        for (;;) {
+            int last = p;
+            for (int q = qd - 1 - lane; q > p; q -= 32)
+                if (ld_acquire(ready + q) == 0u) {
+                    last = q;
+                    break;
+                }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) last = max(last, __shfl_xor_sync(0xffffffffu, last, o));
+            if (last + 1 < qd) {
+                qe = last + 1;
+                break;
+            }
+            int give_up = 0;
+            if (lane == 0) {
+                const long long now = gtimer();
+                if (t0 == 0) t0 = now;
+                if (now - t0 > kWaitNs) {
+                    atomicOr(flag, (int)FL_TIMEOUT);
+                    give_up = 1;
+                }
+            }
+            if (__shfl_sync(0xffffffffu, give_up, 0)) {
+                qe = -1;
+                break;
+            }
+            __nanosleep(64);
+        }
+        if (lane == 0) s_q[slot] = qe;
+    }
+    __syncthreads();
+    return s_q[slot];
 }
 
 // Forward sweep L z = b.  Block row p: z_p = Linv_p (b_p - sum_{q<p} L_pq z_q),
 // L_pq(r, k) = A[(qW + k) K + pW + r].  b from bin (FP64) when given, else x.
 // Off-diagonal part: thread (c, g) owns columns [cV, cV+V) of the block row and
-// the rows j = qW + g + G t of every solved block q, U rows in flight.
+// the rows j = qW + g + G t of every solved block q, U rows in flight.  The
+// tile of block p-1, the last to be solved, is loaded before the first wait.
 template <typename T, int W, int V>
 __global__ void __launch_bounds__(TT)
 k_trsv_fwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, const double* __restrict__ bin, T* x,
@@ -106,56 +192,63 @@ k_trsv_fwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, const dou
     static_assert(TT % R == 0 && W % G == 0 && RPB % U == 0, "thread layout");
     extern __shared__ __align__(16) unsigned char smraw[];
     T* Ls = reinterpret_cast<T*>(smraw);   // [W][W]  Ls[k*W + r] = Linv_p(r, k)
-    T* red = Ls + W * W;                   // [G2][W], reused as [W] partial sums below
+    T* red = Ls + W * W;                   // [G2][W]
     T* acc = red + G2 * W;                 // [W]
-    __shared__ int s_ticket, s_first, s_abort;
+    __shared__ int s_ticket, s_q[2];
     __shared__ T s_off[G][W];
     unsigned* ready = sync + 2;
-    if (threadIdx.x == 0) {
-        s_ticket = (int)atomicAdd(&sync[0], 1u);
-        s_abort = 0;
-    }
+    if (threadIdx.x == 0) s_ticket = (int)atomicAdd(&sync[0], 1u);
     __syncthreads();
     const int p = s_ticket, j0 = p * W, w = min(W, K - j0);
     const T* Lp = Linv + (size_t)p * W * W;
     for (int i = threadIdx.x; i < W * W; i += TT) Ls[i] = Lp[i];
     const int c = (threadIdx.x % R) * V, g = threadIdx.x / R;
+    constexpr bool PRE = RPB * V <= 16;    // register budget: prefetch small tiles only
+    T last[PRE ? RPB : 1][V];
+    if (PRE && p > 0 && c < w) {
+#pragma unroll
+        for (int t = 0; t < (PRE ? RPB : 1); ++t)
+            load_vec<T, V>(A + (int64_t)((p - 1) * W + g + G * t) * K + j0 + c, last[t]);
+    }
     T part[U][V];
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int v = 0; v < V; ++v) part[u][v] = T(0);
-    int qd = 0;                 // blocks [0, qd) applied
-    long long t0 = 0;
+    int qd = 0, it = 0;         // blocks [0, qd) applied
     while (qd < p) {
-        if (threadIdx.x == 0) s_first = p;
-        __syncthreads();
-        for (int q = qd + threadIdx.x; q < p; q += TT)
-            if (ld_acquire(ready + q) == 0u) atomicMin(&s_first, q);
-        __syncthreads();
-        const int qe = s_first;
-        __syncthreads();
-        if (qe == qd) {
-            if (wait_gives_up(t0, flag, &s_abort)) break;
-            continue;
-        }
-        t0 = 0;
+        const int qe = wait_prefix(ready, qd, p, flag, s_q, it++ & 1);
+        if (qe < 0) break;
         if (c < w) {
             for (int q = qd; q < qe; ++q) {
                 const int jb = q * W + g;
+                if (PRE && q == p - 1) {
 #pragma unroll
-                for (int ta = 0; ta < RPB; ta += U) {
-                    T a[U][V], xv[U];
+                    for (int ta = 0; ta < RPB; ta += U) {
+                        T xv[U];
 #pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        const int j = jb + G * (ta + u);
-                        load_vec<T, V>(A + (int64_t)j * K + j0 + c, a[u]);
-                        xv[u] = ldcg(x + j);
+                        for (int u = 0; u < U; ++u) xv[u] = ldcg(x + jb + G * (ta + u));
+#pragma unroll
+                        for (int u = 0; u < U; ++u)
+#pragma unroll
+                            for (int v = 0; v < V; ++v)
+                                part[u][v] = fma(last[PRE ? ta + u : 0][v], xv[u], part[u][v]);
                     }
+                } else {
 #pragma unroll
-                    for (int u = 0; u < U; ++u)
+                    for (int ta = 0; ta < RPB; ta += U) {
+                        T a[U][V], xv[U];
 #pragma unroll
-                        for (int v = 0; v < V; ++v) part[u][v] = fma(a[u][v], xv[u], part[u][v]);
+                        for (int u = 0; u < U; ++u) {
+                            const int j = jb + G * (ta + u);
+                            load_vec<T, V>(A + (int64_t)j * K + j0 + c, a[u]);
+                            xv[u] = ldcg(x + j);
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; ++u)
+#pragma unroll
+                            for (int v = 0; v < V; ++v) part[u][v] = fma(a[u][v], xv[u], part[u][v]);
+                    }
                 }
             }
         }
@@ -163,17 +256,15 @@ k_trsv_fwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, const dou
     }
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        T sum = T(0);
+        T pu[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) sum += part[u][v];
-        s_off[g][c + v] = sum;
+        for (int u = 0; u < U; ++u) pu[u] = part[u][v];
+        s_off[g][c + v] = tree_sum<T, U>(pu, 1);
     }
     __syncthreads();
     if (threadIdx.x < W) {
         const int rr = threadIdx.x;
-        T sum = T(0);
-#pragma unroll
-        for (int gg = 0; gg < G; ++gg) sum += s_off[gg][rr];
+        const T sum = tree_sum<T, G>(&s_off[0][rr], W);
         acc[rr] = (rr < w) ? (T)(bin ? bin[j0 + rr] : (double)ldcg(x + j0 + rr)) - sum : T(0);
     }
     __syncthreads();
@@ -184,22 +275,20 @@ k_trsv_fwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, const dou
         for (int k = g2; k <= r; k += G2) sum = fma(Ls[k * W + r], acc[k], sum);
     red[g2 * W + r] = sum;
     __syncthreads();
-    if (threadIdx.x < w) {
-        T z = T(0);
-#pragma unroll
-        for (int gg = 0; gg < G2; ++gg) z += red[gg * W + threadIdx.x];
-        x[j0 + threadIdx.x] = z;
-        __threadfence();
-    }
+    if (threadIdx.x < w) x[j0 + threadIdx.x] = tree_sum<T, G2>(red + threadIdx.x, W);
     __syncthreads();
-    if (threadIdx.x == 0) st_release(ready + p, 1u);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        st_release(ready + p, 1u);
+    }
 }
 
 // Backward sweep L^T x = z.  Block row p: x_p = Linv_p^T (z_p - sum_{q>p} L_qp^T x_q),
 // (L_qp^T x_q)[k] = sum_{i in block q} A[(pW + k) K + i] x_i.  x holds z on entry;
 // the FP64 copy of the result also goes to xout when given.  Off-diagonal part:
 // R threads share a row (V columns each, W / (R V) segments per block), thread
-// row group g owns rows k = g + G t.
+// row group g owns rows k = g + G t.  The tile of block p+1, the last to be
+// solved, is loaded before the first wait.
 template <typename T, int W, int V>
 __global__ void __launch_bounds__(TT)
 k_trsv_bwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, T* x, double* xout, unsigned* sync, int* flag,
@@ -212,36 +301,35 @@ k_trsv_bwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, T* x, dou
     T* Ls = reinterpret_cast<T*>(smraw);
     T* red = Ls + W * W;
     T* acc = red + G2 * W;
-    __shared__ int s_ticket, s_last, s_abort;
+    __shared__ int s_ticket, s_q[2];
     const int npanel = (K + W - 1) / W;
     unsigned* ready = sync + 2 + npanel;
-    if (threadIdx.x == 0) {
-        s_ticket = (int)atomicAdd(&sync[1], 1u);
-        s_abort = 0;
-    }
+    if (threadIdx.x == 0) s_ticket = (int)atomicAdd(&sync[1], 1u);
     __syncthreads();
     const int p = npanel - 1 - s_ticket, j0 = p * W, w = min(W, K - j0);
     const T* Lp = Linv + (size_t)p * W * W;
     for (int i = threadIdx.x; i < W * W; i += TT) Ls[i] = Lp[i];
     const int cl = (threadIdx.x % R) * V, g = threadIdx.x / R;
+    constexpr bool PRE = SEG * RPB * V <= 16;   // register budget: prefetch small tiles only
+    T last[PRE ? SEG : 1][PRE ? RPB : 1][V];
+    if (PRE && p + 1 < npanel) {
+#pragma unroll
+        for (int sg = 0; sg < (PRE ? SEG : 1); ++sg) {
+            const int i = (p + 1) * W + sg * R * V + cl;
+#pragma unroll
+            for (int t = 0; t < (PRE ? RPB : 1); ++t) {
+                const int k = g + G * t;
+                if (i < K && k < w) load_vec<T, V>(A + (int64_t)(j0 + k) * K + i, last[sg][t]);
+            }
+        }
+    }
     T part[RPB];
 #pragma unroll
     for (int t = 0; t < RPB; ++t) part[t] = T(0);
-    int qd = npanel;            // blocks [qd, npanel) applied
-    long long t0 = 0;
+    int qd = npanel, it = 0;    // blocks [qd, npanel) applied
     while (qd > p + 1) {
-        if (threadIdx.x == 0) s_last = p;
-        __syncthreads();
-        for (int q = p + 1 + threadIdx.x; q < qd; q += TT)
-            if (ld_acquire(ready + q) == 0u) atomicMax(&s_last, q);
-        __syncthreads();
-        const int qe = s_last + 1;   // blocks [qe, qd) are solved
-        __syncthreads();
-        if (qe == qd) {
-            if (wait_gives_up(t0, flag, &s_abort)) break;
-            continue;
-        }
-        t0 = 0;
+        const int qe = wait_suffix(ready, qd, p, flag, s_q, it++ & 1);
+        if (qe < 0) break;
         // blocks in descending order, segments ascending inside a block
         for (int q = qd - 1; q >= qe; --q) {
 #pragma unroll
@@ -255,7 +343,12 @@ k_trsv_bwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, T* x, dou
                         const int k = g + G * t;
                         if (k < w) {
                             T a[V];
-                            load_vec<T, V>(A + (int64_t)(j0 + k) * K + i, a);
+                            if (PRE && q == p + 1) {
+#pragma unroll
+                                for (int v = 0; v < V; ++v) a[v] = last[PRE ? sg : 0][PRE ? t : 0][v];
+                            } else {
+                                load_vec<T, V>(A + (int64_t)(j0 + k) * K + i, a);
+                            }
 #pragma unroll
                             for (int v = 0; v < V; ++v) part[t] = fma(a[v], xv[v], part[t]);
                         }
@@ -283,15 +376,15 @@ k_trsv_bwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, T* x, dou
     red[g2 * W + k] = s;
     __syncthreads();
     if (threadIdx.x < w) {
-        T z = T(0);
-#pragma unroll
-        for (int gg = 0; gg < G2; ++gg) z += red[gg * W + threadIdx.x];
+        const T z = tree_sum<T, G2>(red + threadIdx.x, W);
         x[j0 + threadIdx.x] = z;
         if (xout) xout[j0 + threadIdx.x] = (double)z;
-        __threadfence();
     }
     __syncthreads();
-    if (threadIdx.x == 0) st_release(ready + p, 1u);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        st_release(ready + p, 1u);
+    }
 }
 
 template <typename T, int W>

@@ -122,6 +122,8 @@ struct psdp_ctx {
     float *d_opA_hi = nullptr, *d_opA_lo = nullptr, *d_opB_hi = nullptr, *d_opB_lo = nullptr;
     double *d_prodA = nullptr, *d_prodB = nullptr;     // GEMM-built operand products [nlyap_prod][n][n]
     float *d_T32 = nullptr, *d_Om32 = nullptr, *d_Linv32 = nullptr, *d_Pt_hi = nullptr, *d_Pt_lo = nullptr;
+    float *d_Pk_hi = nullptr, *d_Pk_lo = nullptr;   // unsolved panel, K-major TF32 pairs [K][nb32]
+    float *d_Lt_hi = nullptr, *d_Lt_lo = nullptr;   // current diagonal-block inverse, row-major TF32 pairs
     float *d_z32 = nullptr, *d_part32 = nullptr;
     double *d_pcg_x = nullptr, *d_pcg_r = nullptr, *d_pcg_z = nullptr, *d_pcg_p = nullptr, *d_pcg_q = nullptr;
     double *d_pcg_state = nullptr;
@@ -237,7 +239,8 @@ bool tc_make_map(CUtensorMap* map, const void* base, bool bf16, int64_t kdim, in
 bool launch_tc_gemm(cudaStream_t st, bool bf16, int split, const CUtensorMap& A, const CUtensorMap& B,
                     const CUtensorMap* Alo, const CUtensorMap* Blo, int M, int N, int batch, int b0,
                     const int32_t* kd, int kd_uniform, float* C, int64_t ldc, int64_t c_batch, float alpha,
-                    float beta, int tri, int* flag);
+                    float beta, int tri, int* flag, float* aux_hi = nullptr, float* aux_lo = nullptr,
+                    int aux_ld = 0);
 void launch_split_tf32(cudaStream_t st, int64_t n, const float* x, float* hi, float* lo);
 bool launch_tc_gemm_persist(cudaStream_t st, int split, const CUtensorMap& A, const CUtensorMap& B,
                             const CUtensorMap* Alo, const CUtensorMap* Blo, int M, int N, int kd, float* C,
@@ -247,7 +250,9 @@ void init_attrs_tc(int smem_optin);
 // mixed precision (k_mixed.cu)
 void launch_schur_pack32(cudaStream_t st, psdp_ctx* c);
 void launch_schur_gather32(cudaStream_t st, psdp_ctx* c, int p0, int np, const float* T, float* Om);
-void launch_potrf_diag32(cudaStream_t st, float* A, int K, int j0, int nb, float* Linv, int* flag);
+void launch_potrf_diag32(cudaStream_t st, float* A, int K, int j0, int nb, float* Linv, float* LtHi, float* LtLo,
+                         int* flag);
+void launch_pack_panel32(cudaStream_t st, const float* A, int K, int j0, int nb, float* PkHi, float* PkLo);
 void launch_trsm32_pack(cudaStream_t st, float* A, int K, int j0, int nb, const float* Linv, float* PtHi,
                         float* PtLo);
 // Triangular sweeps with the dense factor (one launch per sweep, flag-synchronised
