@@ -9,8 +9,6 @@
 
 #include "psdp_internal.h"
 
-void dense_cholesky(cudaStream_t st, double* A, int K, int nb, double* Linv, int* flag);
-void launch_vec_copy(cudaStream_t st, int K, const double* a, double* out);
 void launch_cdiag(cudaStream_t st, psdp_ctx* c);
 void init_attrs_linalg(int smem_max);
 void init_attrs_sdp(int smem_max);
@@ -297,7 +295,7 @@ void enqueue_pcg(psdp_ctx* c, double* b) {
     const int* done = c->d_pcg_done;
     ProfScope p(c, "pcg_solve");
     launch_pcg_init(st, K, b, c->d_pcg_x, c->d_pcg_r, c->d_pcg_state, c->d_pcg_done);
-    launch_precond32_flag(st, c->d_Om32, K, c->nb32, c->d_Linv32, c->d_z32, c->d_pcg_r, c->d_pcg_z, c->d_trsv_sync,
+    launch_precond32(st, c->d_Om32, K, c->nb32, c->d_Linv32, c->d_z32, c->d_pcg_r, c->d_pcg_z, c->d_trsv_sync,
                           c->d_flag, done);
     launch_pcg_start(st, K, c->d_pcg_r, c->d_pcg_z, c->d_pcg_p, c->d_pcg_state, done);
     for (int it = 0; it < c->pcg_max; ++it) {
@@ -307,7 +305,7 @@ void enqueue_pcg(psdp_ctx* c, double* b) {
         launch_b(st, c, c->d_M1, c->d_pcg_q, 0.0, done);
         launch_pcg_alpha(st, K, c->d_pcg_p, c->d_pcg_q, c->d_pcg_x, c->d_pcg_r, c->d_pcg_state, c->d_pcg_done,
                          c->pcg_tol);
-        launch_precond32_flag(st, c->d_Om32, K, c->nb32, c->d_Linv32, c->d_z32, c->d_pcg_r, c->d_pcg_z,
+        launch_precond32(st, c->d_Om32, K, c->nb32, c->d_Linv32, c->d_z32, c->d_pcg_r, c->d_pcg_z,
                               c->d_trsv_sync, c->d_flag, done);
         launch_pcg_beta(st, K, c->d_pcg_r, c->d_pcg_z, c->d_pcg_p, c->d_pcg_state, done);
     }
@@ -418,12 +416,12 @@ void free_ctx(psdp_ctx* c) {
     if (c->graph32) cudaGraphDestroy(c->graph32);
     void* ptrs[] = {c->d_beta, c->d_cH, c->d_W0, c->d_Wa, c->d_A, c->d_H, c->d_cdiag, c->d_X, c->d_Z, c->d_G,
                     c->d_Y, c->d_T1, c->d_T2, c->d_W, c->d_F, c->d_dXh, c->d_dZh, c->d_dX, c->d_dZ, c->d_S,
-                    c->d_adj, c->d_adj2, c->d_y, c->d_dyh, c->d_dyb, c->d_rhs, c->d_BX, c->d_part, c->d_tstep,
+                    c->d_adj, c->d_adj2, c->d_y, c->d_dyh, c->d_dyb, c->d_BX, c->d_part, c->d_tstep,
                     c->d_scal, c->d_info, c->d_flag, c->d_pair_a, c->d_pair_b, c->d_term_off, c->d_term_cnt,
                     c->d_term_desc, c->d_term_w, c->d_uv_idx, c->d_prod_idx, c->d_U, c->d_V, c->d_Aop, c->d_Bop,
                     c->d_Tbuf, c->d_Om, c->d_Linv, c->d_grid, c->d_svec, c->d_cert, c->d_term_off_t,
                     c->d_opA_hi, c->d_opA_lo, c->d_opB_hi, c->d_opB_lo, c->d_prodA, c->d_prodB, c->d_T32,
-                    c->d_Om32, c->d_Linv32, c->d_Pt_hi, c->d_Pt_lo, c->d_z32, c->d_part32, c->d_trsv_sync, c->d_Pk_hi, c->d_Pk_lo, c->d_Lt_hi, c->d_Lt_lo, c->d_pcg_x, c->d_pcg_r,
+                    c->d_Om32, c->d_Linv32, c->d_Pt_hi, c->d_Pt_lo, c->d_z32, c->d_trsv_sync, c->d_Pk_hi, c->d_Pk_lo, c->d_Lt_hi, c->d_Lt_lo, c->d_pcg_x, c->d_pcg_r,
                     c->d_pcg_z, c->d_pcg_p, c->d_pcg_q, c->d_pcg_state, c->d_pcg_done, c->d_M1, c->d_M2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -575,7 +573,6 @@ psdp_status alloc_mixed(psdp_ctx* c) {
     TRY(dalloc(&c->d_Lt_hi, nb * nb));
     TRY(dalloc(&c->d_Lt_lo, nb * nb));
     TRY(dalloc(&c->d_z32, K));
-    TRY(dalloc(&c->d_part32, (size_t)nb * (K / 2048 + 2)));
     double** vecs[] = {&c->d_pcg_x, &c->d_pcg_r, &c->d_pcg_z, &c->d_pcg_p, &c->d_pcg_q};
     for (double** p : vecs) TRY(dalloc(p, K));
     TRY(dalloc(&c->d_pcg_state, 8));
@@ -663,12 +660,10 @@ psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psd
     if ((s = dalloc(&c->d_S, (size_t)M * Na * c->n2)) || (s = dalloc(&c->d_adj, (size_t)L0 * (Na + 1) * c->n2)) ||
         (s = dalloc(&c->d_adj2, (size_t)L0 * Na * c->n2)))
         return fail(s);
-    const int nbc = c->nb_chol;
-    const size_t rhs_len = std::max<size_t>(K, (size_t)nbc * (K / 2048 + 2));
     double** vecs[] = {&c->d_y, &c->d_dyh, &c->d_dyb, &c->d_BX};
     for (double** p : vecs)
         if ((s = dalloc(p, (size_t)K))) return fail(s);
-    if ((s = dalloc(&c->d_rhs, rhs_len)) || (s = dalloc(&c->d_part, (size_t)4 * (c->nblk + 1))) ||
+    if ((s = dalloc(&c->d_part, (size_t)4 * (c->nblk + 1))) ||
         (s = dalloc(&c->d_tstep, (size_t)2 * c->nblk)) || (s = dalloc(&c->d_scal, SC_COUNT)) ||
         (s = dalloc(&c->d_info, PSDP_INFO_LEN)) || (s = dalloc(&c->d_flag, 1)) || (s = dalloc(&c->d_cert, 4)) ||
         (s = dalloc(&c->d_svec, (size_t)2 * Nt)) || (s = dalloc(&c->d_trsv_sync, trsv_sync_words((int)K, 32))))

@@ -1,13 +1,14 @@
-// Dense K x K Cholesky of the Schur complement and the two triangular solves.
+// Dense K x K Cholesky of the Schur complement: the diagonal-block factor.
 //
 // Omega is held row-major with its upper triangle filled, which is the same
 // memory as a column-major matrix with its lower triangle filled: element
 // (i, j), i >= j, of the column-major view sits at A[j*K + i].  The factor is
 // L with Omega = L L^T, overwriting that lower triangle.  Right-looking blocked
-// algorithm with panels of nb columns: (1) factor the nb x nb diagonal block in
-// shared memory and invert it, (2) panel <- panel * L_jj^{-T} as a GEMM with the
-// inverse, (3) symmetric rank-nb update of the trailing lower triangle with the
-// FP64 TN GEMM.  The diagonal-block inverses are kept for the solves.
+// algorithm with panels of nb columns (orchestrated in api.cu): (1) factor the
+// nb x nb diagonal block in shared memory and invert it (this file), (2) panel
+// <- panel * L_jj^{-T} as a GEMM with the inverse, (3) symmetric rank-nb
+// update of the trailing lower triangle with the FP64 TN GEMM.  The
+// diagonal-block inverses are kept for the triangular sweeps (k_trsv.cu).
 #include <cmath>
 
 #include "psdp_internal.h"
@@ -151,72 +152,6 @@ k_potrf_diag32x4(double* A, int K, int j0, int w, int nb, double* Linv, int* fla
     if (tid == 0 && bad) atomicOr(flag, (int)FL_CHOL_SCHUR);
 }
 
-// b[j0 .. j0+w) <- L_jj^{-1} b[j0 .. j0+w)   (Linv column-major, leading dim nb)
-__global__ void k_trsv_fwd_diag(const double* __restrict__ Linv, int nb, int w, int j0, double* b) {
-    __shared__ double z[128];
-    for (int i = threadIdx.x; i < w; i += blockDim.x) z[i] = b[j0 + i];
-    __syncthreads();
-    for (int r = threadIdx.x; r < w; r += blockDim.x) {
-        double s = 0.0;
-        for (int k = 0; k <= r; ++k) s = fma(Linv[k * nb + r], z[k], s);
-        b[j0 + r] = s;
-    }
-}
-
-// b[i] -= sum_k A(i, j0+k) b[j0+k] for i >= j0+w
-__global__ void k_gemv_fwd(const double* __restrict__ A, int K, int j0, int w, double* b) {
-    __shared__ double z[128];
-    for (int i = threadIdx.x; i < w; i += blockDim.x) z[i] = b[j0 + i];
-    __syncthreads();
-    for (int i = j0 + w + blockIdx.x * blockDim.x + threadIdx.x; i < K; i += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int k = 0; k < w; ++k) s = fma(A[(int64_t)(j0 + k) * K + i], z[k], s);
-        b[i] -= s;
-    }
-}
-
-// partial[k*nchunk + ch] = sum over chunk ch of A(i, j0+k) b[i], i >= j0+w
-constexpr int kChunk = 2048;
-__global__ void k_gemv_bwd_partial(const double* __restrict__ A, int K, int j0, int w, const double* __restrict__ b,
-                                   double* partial, int nchunk) {
-    __shared__ double red[32];
-    const int k = blockIdx.x, ch = blockIdx.y;
-    const int i0 = j0 + w + ch * kChunk, i1 = min(K, i0 + kChunk);
-    double s = 0.0;
-    const double* col = A + (int64_t)(j0 + k) * K;
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) s = fma(col[i], b[i], s);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
-        partial[k * nchunk + ch] = t;
-    }
-}
-
-// b[j0+k] <- sum_{r>=k} Linv(r,k) (b[j0+r] - sum_ch partial[r][ch])
-__global__ void k_trsv_bwd_diag(const double* __restrict__ Linv, int nb, int w, int j0, const double* partial,
-                                int nchunk, double* b) {
-    __shared__ double z[128];
-    for (int r = threadIdx.x; r < w; r += blockDim.x) {
-        double s = b[j0 + r];
-        for (int ch = 0; ch < nchunk; ++ch) s -= partial[r * nchunk + ch];
-        z[r] = s;
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < w; k += blockDim.x) {
-        double s = 0.0;
-        for (int r = k; r < w; ++r) s = fma(Linv[k * nb + r], z[r], s);
-        b[j0 + k] = s;
-    }
-}
-
-__global__ void k_vec_copy(int K, const double* __restrict__ a, double* out) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K; i += gridDim.x * blockDim.x) out[i] = a[i];
-}
-
 }  // namespace
 
 void launch_potrf_diag(cudaStream_t st, double* A, int K, int j0, int nb, double* Linv, int* flag) {
@@ -227,55 +162,6 @@ void launch_potrf_diag(cudaStream_t st, double* A, int K, int j0, int nb, double
     }
     const size_t sm = (size_t)2 * w * (w + 1) * sizeof(double);
     k_potrf_diag<<<1, kThreads, sm, st>>>(A, K, j0, w, nb, Linv, flag);
-}
-
-// Omega = L L^T in place (column-major lower view), diagonal-block inverses to Linv.
-void dense_cholesky(cudaStream_t st, double* A, int K, int nb, double* Linv, int* flag) {
-    for (int j0 = 0, p = 0; j0 < K; j0 += nb, ++p) {
-        const int w = (K - j0 < nb) ? K - j0 : nb;
-        double* Lp = Linv + (size_t)p * nb * nb;
-        launch_potrf_diag(st, A, K, j0, nb, Lp, flag);
-        const int rest = K - j0 - w;
-        if (rest <= 0) break;
-        double* panel = A + (int64_t)j0 * K + j0 + w;
-        // panel <- panel L_jj^{-T}:  C[k][i] = sum_m Linv(k,m) P(i,m)
-        launch_gemm_tn(st, w, rest, 1, Lp, nb, nullptr, 0, panel, K, nullptr, 0, nullptr, w, panel, K, 0, 1.0, 0.0, 0);
-        // trailing lower triangle -= P P^T
-        launch_gemm_tn(st, rest, rest, 1, panel, K, nullptr, 0, panel, K, nullptr, 0, nullptr, w,
-                       A + (int64_t)(j0 + w) * K + j0 + w, K, 0, -1.0, 1.0, 1);
-    }
-}
-
-// x <- Omega^{-1} x with the factor from dense_cholesky (forward then backward).
-void dense_solve(cudaStream_t st, const double* A, int K, int nb, const double* Linv, double* partial, double* x) {
-    const int npanel = (K + nb - 1) / nb;
-    for (int p = 0; p < npanel; ++p) {
-        const int j0 = p * nb, w = (K - j0 < nb) ? K - j0 : nb;
-        k_trsv_fwd_diag<<<1, 128, 0, st>>>(Linv + (size_t)p * nb * nb, nb, w, j0, x);
-        const int rest = K - j0 - w;
-        if (rest > 0) {
-            int blocks = (rest + kThreads - 1) / kThreads;
-            if (blocks > 1024) blocks = 1024;
-            k_gemv_fwd<<<blocks, kThreads, 0, st>>>(A, K, j0, w, x);
-        }
-    }
-    for (int p = npanel - 1; p >= 0; --p) {
-        const int j0 = p * nb, w = (K - j0 < nb) ? K - j0 : nb;
-        const int rest = K - j0 - w;
-        int nchunk = 0;
-        if (rest > 0) {
-            nchunk = (rest + kChunk - 1) / kChunk;
-            dim3 g(w, nchunk);
-            k_gemv_bwd_partial<<<g, kThreads, 0, st>>>(A, K, j0, w, x, partial, nchunk);
-        }
-        k_trsv_bwd_diag<<<1, 128, 0, st>>>(Linv + (size_t)p * nb * nb, nb, w, j0, partial, nchunk, x);
-    }
-}
-
-void launch_vec_copy(cudaStream_t st, int K, const double* a, double* out) {
-    int blocks = (K + kThreads - 1) / kThreads;
-    if (blocks > 4096) blocks = 4096;
-    k_vec_copy<<<blocks, kThreads, 0, st>>>(K, a, out);
 }
 
 void init_attrs_dense(int smem_max) {

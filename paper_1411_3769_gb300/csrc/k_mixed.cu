@@ -84,101 +84,229 @@ __global__ void k_schur_pack32(int n, int tpad, const int32_t* __restrict__ term
 // ------------------------------------------------------------- FP32 Cholesky
 // Diagonal w x w block (w <= 128) of the FP32 matrix (column-major lower view),
 // factored in FP32 (it only seeds the preconditioner; FP64 PCG fixes the
-// rest); writes L back and L^{-1} (column-major, ld nb).
-__global__ void __launch_bounds__(kThreads)
-k_potrf_diag32(float* A, int K, int j0, int w, int nb, float* Linv, float* LtHi, float* LtLo, int* flag) {
-    extern __shared__ float smf[];
-    const int ld = w + 1;
-    float* L = smf;
-    float* I = smf + (size_t)w * ld;
-    __shared__ float rinv[128], ldiag[128];
-    __shared__ int bad;
-    if (threadIdx.x == 0) bad = 0;
-    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
-        const int j = idx / w, i = idx % w;
-        L[j * ld + i] = (i >= j) ? A[(int64_t)(j0 + j) * K + j0 + i] : 0.f;
-    }
-    __syncthreads();
-    for (int j = 0; j < w; ++j) {
-        float piv = L[j * ld + j];
+// rest); writes L back, L^{-1} (column-major, ld nb) and L^{-1} row-major as
+// TF32 (hi, lo) pairs.  The block is padded to Wp = 32 ceil(w/32) with an
+// identity tail and processed in 32-column sub-panels:
+//   (a) warp 0 factors the 32 x 32 diagonal sub-block in registers (a lane
+//       per row, multipliers exchanged by shuffles);
+//   (b) its inverse by forward substitution, a thread per column, the column
+//       kept in registers;
+//   (c) the rows below: S = B D^{-T} (a thread per row and four columns);
+//   (d) the trailing update A22 -= S S^T on 4 x 4 register tiles, and S back
+//       into the panel;
+// then the off-diagonal blocks of L^{-1} level by level,
+//   X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj,
+// on 4 x 4 register tiles.  Five barriers per sub-panel instead of two per column.
+constexpr int PB = 32;
+constexpr int kPotrfThreads = 256;
+
+size_t potrf32_smem(int w) {
+    const int wp = (w + PB - 1) / PB * PB;
+    return ((size_t)2 * wp * (wp + 1) + 96 * 33) * sizeof(float);
+}
+
+// Column J of the in-register factor of a 32 x 32 block (lane = row), then
+// the columns after it; compile-time recursion keeps d[] in registers.
+template <int J>
+__device__ __forceinline__ void chol_warp_step(float (&d)[PB], int lane, int c0, float* rinv, float* ldiag, int& badl) {
+    if constexpr (J < PB) {
+        float piv = __shfl_sync(0xffffffffu, d[J], J);
         if (!(piv > 0.f) || !isfinite(piv)) {
-            if (threadIdx.x == 0) bad = 1;
+            badl = 1;
             piv = 1.f;
         }
-        const float ri = 1.f / sqrtf(piv);
-        if (threadIdx.x == 0) {
-            rinv[j] = ri;
-            ldiag[j] = piv * ri;
+        const float rj = rsqrtf(piv);
+        if (lane == J) {
+            d[J] = piv * rj;
+            rinv[c0 + J] = rj;
+            ldiag[c0 + J] = piv * rj;
+        } else if (lane > J) {
+            d[J] *= rj;
         }
-        for (int i = j + 1 + threadIdx.x; i < w; i += blockDim.x) L[j * ld + i] *= ri;
-        __syncthreads();
-        // trailing lower triangle: warps take columns, lanes take rows
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        for (int c = j + 1 + wid; c < w; c += nw) {
-            const float ljc = L[j * ld + c];
-            for (int r = c + lane; r < w; r += 32) L[c * ld + r] = fmaf(-L[j * ld + r], ljc, L[c * ld + r]);
+#pragma unroll
+        for (int c = J + 1; c < PB; ++c) {
+            const float lc = __shfl_sync(0xffffffffu, d[J], c);
+            if (lane >= c) d[c] = fmaf(-d[J], lc, d[c]);
         }
-        __syncthreads();
+        chol_warp_step<J + 1>(d, lane, c0, rinv, ldiag, badl);
     }
-    // L^{-1} by 32 x 32 blocks: diagonal blocks by forward substitution (one
-    // thread per column, all blocks at once), then block row i of column j from
-    // X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj, one block diagonal per level.
-    for (int idx = threadIdx.x; idx < w * ld; idx += blockDim.x) I[idx] = 0.f;
+}
+
+__global__ void __launch_bounds__(kPotrfThreads)
+k_potrf_diag32(float* A, int K, int j0, int w, int nb, float* Linv, float* LtHi, float* LtLo, int* flag) {
+    extern __shared__ float smf[];
+    const int wp = (w + PB - 1) / PB * PB, ld = wp + 1, nsub = wp / PB;
+    float* L = smf;                        // [wp][ld] column-major: L(r, c) = L[c*ld + r]
+    float* X = L + (size_t)wp * ld;        // L^{-1}, same layout
+    float* S = X + (size_t)wp * ld;        // [96][33] scratch
+    __shared__ float rinv[128], ldiag[128];
+    __shared__ int bad;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) bad = 0;
+    for (int idx = tid; idx < wp * wp; idx += kPotrfThreads) {
+        const int c = idx / wp, r = idx - c * wp;
+        float v = 0.f;
+        if (r < w && c < w) {
+            if (r >= c) v = A[(int64_t)(j0 + c) * K + j0 + r];
+        } else if (r == c) {
+            v = 1.f;                       // identity tail
+        }
+        L[c * ld + r] = v;
+        X[c * ld + r] = 0.f;
+    }
     __syncthreads();
-    const int nbk = (w + 31) / 32;
-    if (threadIdx.x < nbk * 32) {
-        const int d = threadIdx.x >> 5, c = threadIdx.x;
-        const int hi = min(w, d * 32 + 32);
-        if (c < w) {
-            for (int r = c; r < hi; ++r) {
-                float s = (r == c) ? 1.f : 0.f;
-                for (int k = c; k < r; ++k) s = fmaf(-L[k * ld + r], I[c * ld + k], s);
-                I[c * ld + r] = s * rinv[r];
+    for (int kb = 0; kb < nsub; ++kb) {
+        const int c0 = kb * PB, rest = wp - c0 - PB;
+        // (a) factor the diagonal sub-block D
+        if (warp == 0) {
+            float d[PB];
+#pragma unroll
+            for (int c = 0; c < PB; ++c) d[c] = (c <= lane) ? L[(c0 + c) * ld + c0 + lane] : 0.f;
+            int badl = 0;
+            chol_warp_step<0>(d, lane, c0, rinv, ldiag, badl);
+#pragma unroll
+            for (int c = 0; c < PB; ++c)
+                if (c <= lane) L[(c0 + c) * ld + c0 + lane] = d[c];
+            if (lane == 0 && badl) bad = 1;
+        }
+        __syncthreads();
+        // (b) D^{-1}: thread c solves D x = e_c, x kept in registers
+        if (tid < PB) {
+            const int c = tid;
+            float xr[PB];
+#pragma unroll
+            for (int r = 0; r < PB; ++r) {
+                float sacc = (r == c) ? 1.f : 0.f;
+#pragma unroll
+                for (int k = 0; k < r; ++k)
+                    if (k >= c) sacc = fmaf(-L[(c0 + k) * ld + c0 + r], xr[k], sacc);
+                xr[r] = (r >= c) ? sacc * rinv[c0 + r] : 0.f;
             }
+#pragma unroll
+            for (int r = 0; r < PB; ++r) X[(c0 + c) * ld + c0 + r] = xr[r];
+        }
+        __syncthreads();
+        if (rest > 0) {
+            // (c) S[i][j] = sum_k B(i, k) D^{-1}(j, k), B(i, k) = L(c0+32+i, c0+k)
+            for (int idx = tid; idx < rest * 8; idx += kPotrfThreads) {
+                const int i = idx % rest, jg = idx / rest;
+                float acc4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+                for (int k = 0; k < PB; ++k) {
+                    const float bik = L[(c0 + k) * ld + c0 + PB + i];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) acc4[t] = fmaf(bik, X[(c0 + k) * ld + c0 + jg + 8 * t], acc4[t]);
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t) S[i * 33 + jg + 8 * t] = acc4[t];
+            }
+            __syncthreads();
+            // (d) A22 -= S S^T on the lower 4 x 4 tiles; S back into the panel
+            const int nt = rest / 4, ntiles = nt * (nt + 1) / 2;
+            for (int q = tid; q < ntiles; q += kPotrfThreads) {
+                // q -> (ti, tc), ti >= tc, row-major over the lower triangle of tiles
+                int ti = (int)((sqrtf(8.f * q + 1.f) - 1.f) * 0.5f);
+                while ((ti + 1) * (ti + 2) / 2 <= q) ++ti;
+                while (ti * (ti + 1) / 2 > q) --ti;
+                const int tc = q - ti * (ti + 1) / 2;
+                float acc[4][4] = {};
+#pragma unroll 4
+                for (int k = 0; k < PB; ++k) {
+                    float a[4], bb[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        a[u] = S[(4 * ti + u) * 33 + k];
+                        bb[u] = S[(4 * tc + u) * 33 + k];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], bb[v], acc[u][v]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const int i = 4 * ti + u, cc = 4 * tc + v;
+                        if (i >= cc) L[(c0 + PB + cc) * ld + c0 + PB + i] -= acc[u][v];
+                    }
+            }
+            for (int idx = tid; idx < rest * PB; idx += kPotrfThreads) {
+                const int i = idx % rest, j = idx / rest;
+                L[(c0 + j) * ld + c0 + PB + i] = S[i * 33 + j];
+            }
+            __syncthreads();
         }
     }
-    __syncthreads();
-    __shared__ float Tb[3][32][33];
-    for (int lev = 1; lev < nbk; ++lev) {
-        const int npair = nbk - lev;
-        for (int idx = threadIdx.x; idx < npair * 1024; idx += blockDim.x) {
-            const int q = idx >> 10, e = idx & 1023, rr = e >> 5, cc = e & 31;
+    // off-diagonal blocks of L^{-1}, one block diagonal per level
+    float* T = S;                          // [3][32][33]
+    for (int lev = 1; lev < nsub; ++lev) {
+        const int npair = nsub - lev;      // pairs (bi, bj) = (q + lev, q)
+        // T_q = sum_{k=bj}^{bi-1} L_{bi,k} X_{k,bj}: 64 tiles of 4 x 4 per pair
+        for (int idx = tid; idx < npair * 64; idx += kPotrfThreads) {
+            const int q = idx >> 6, tt = idx & 63, tr = tt >> 3, tcl = tt & 7;
             const int bj = q, bi = q + lev;
-            const int r = bi * 32 + rr, c = bj * 32 + cc;
-            float s = 0.f;
-            if (r < w && c < w)
-                for (int k = c; k < bi * 32; ++k) s = fmaf(L[k * ld + r], I[c * ld + k], s);
-            Tb[q][rr][cc] = s;
+            float acc[4][4] = {};
+            for (int k = bj * PB; k < bi * PB; ++k) {
+                float a[4], bb[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    a[u] = L[k * ld + bi * PB + 4 * tr + u];       // L(bi*32 + row, k)
+                    bb[u] = X[(bj * PB + 4 * tcl + u) * ld + k];   // X(k, bj*32 + col)
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], bb[v], acc[u][v]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) T[q * PB * 33 + (4 * tr + u) * 33 + 4 * tcl + v] = acc[u][v];
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < npair * 1024; idx += blockDim.x) {
-            const int q = idx >> 10, e = idx & 1023, rr = e >> 5, cc = e & 31;
-            const int bi = q + lev;
-            const int r = bi * 32 + rr, c = q * 32 + cc;
-            if (r < w && c < w) {
-                float s = 0.f;
-                for (int k = 0; k <= rr; ++k) s = fmaf(I[(bi * 32 + k) * ld + r], Tb[q][k][cc], s);
-                I[c * ld + r] = -s;
+        // X_{bi,bj} = -X_{bi,bi} T_q
+        for (int idx = tid; idx < npair * 64; idx += kPotrfThreads) {
+            const int q = idx >> 6, tt = idx & 63, tr = tt >> 3, tcl = tt & 7;
+            const int bj = q, bi = q + lev;
+            float acc[4][4] = {};
+#pragma unroll 4
+            for (int k = 0; k < PB; ++k) {
+                float a[4], bb[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    a[u] = X[(bi * PB + k) * ld + bi * PB + 4 * tr + u];   // X(bi*32 + row, bi*32 + k)
+                    bb[u] = T[q * PB * 33 + k * 33 + 4 * tcl + u];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], bb[v], acc[u][v]);
             }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    X[(bj * PB + 4 * tcl + v) * ld + bi * PB + 4 * tr + u] = -acc[u][v];
         }
         __syncthreads();
     }
-    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
-        const int j = idx / w, i = idx % w;
+    for (int idx = tid; idx < w * w; idx += kPotrfThreads) {
+        const int j = idx / w, i = idx - j * w;
         if (i >= j) A[(int64_t)(j0 + j) * K + j0 + i] = (i == j) ? ldiag[j] : L[j * ld + i];
     }
-    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
-        const int j = idx / nb, i = idx % nb;
-        Linv[idx] = (j < w && i < w) ? I[j * ld + i] : 0.f;
+    for (int idx = tid; idx < nb * nb; idx += kPotrfThreads) {
+        const int j = idx / nb, i = idx - j * nb;
+        Linv[idx] = (j < w && i < w) ? X[j * ld + i] : 0.f;
         // row-major copy split into TF32 (hi, lo): LtHi[k*nb + m] ~ Linv(k, m),
         // the K-major right operand of the tensor-core panel solve
-        const float v = (j < w && i < w) ? I[i * ld + j] : 0.f;    // Linv(j, i)
+        const float v = (j < w && i < w) ? X[i * ld + j] : 0.f;    // Linv(j, i)
         uint32_t h;
         asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
         LtHi[idx] = __uint_as_float(h);
         LtLo[idx] = v - __uint_as_float(h);
     }
-    if (threadIdx.x == 0 && bad) atomicOr(flag, (int)FL_CHOL_SCHUR);
+    if (tid == 0 && bad) atomicOr(flag, (int)FL_CHOL_SCHUR);
 }
 
 // Unsolved panel rows packed K-major as TF32 (hi, lo) pairs:
@@ -204,112 +332,6 @@ k_pack_panel32(const float* __restrict__ A, int K, int j0, int w, int nb, float*
             PkLo[(int64_t)i * nb + m] = v - __uint_as_float(h);
         }
     }
-}
-
-// Panel rows i in [j0+w, K): P'(i,k) = sum_{m<=k} P(i,m) Linv(k,m), written back
-// column-major and packed K-major as (hi, lo) into Pt*[i - j0 - w][k] (row length nb).
-constexpr int TR = 64;   // panel rows per CTA
-__global__ void __launch_bounds__(kThreads)
-k_trsm32_pack(float* A, int K, int j0, int w, int nb, const float* __restrict__ Linv, float* PtHi, float* PtLo) {
-    extern __shared__ float smf[];
-    float* Li = smf;                    // [w][w]  Li[k*w + m] = Linv(k, m)
-    float* Ps = smf + w * w;            // [w][TR+1]  Ps[m*(TR+1) + r] = P(i0 + r, m)
-    const int i0 = j0 + w + blockIdx.x * TR;
-    const int rows = min(TR, K - i0);
-    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
-        const int m = idx / w, k = idx % w;              // column-major source: Linv(k, m) at m*nb + k
-        Li[k * w + m] = Linv[m * nb + k];
-    }
-    for (int idx = threadIdx.x; idx < w * TR; idx += blockDim.x) {
-        const int m = idx / TR, r = idx % TR;
-        Ps[m * (TR + 1) + r] = (r < rows) ? A[(int64_t)(j0 + m) * K + i0 + r] : 0.f;
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < w * TR; idx += blockDim.x) {
-        const int k = idx / TR, r = idx % TR;
-        float s = 0.f;
-        for (int m = 0; m <= k; ++m) s = fmaf(Ps[m * (TR + 1) + r], Li[k * w + m], s);
-        if (r < rows) {
-            A[(int64_t)(j0 + k) * K + i0 + r] = s;
-            float h, l;
-            split_tf32(s, h, l);
-            const int64_t o = (int64_t)(i0 + r - j0 - w) * nb + k;
-            PtHi[o] = h;
-            PtLo[o] = l;
-        }
-    }
-}
-
-// ----------------------------------------------------------- FP32 solves
-__global__ void k_trsv_fwd_diag32(const float* __restrict__ Linv, int nb, int w, int j0, float* b, const int* skip) {
-    if (skip && *skip) return;
-    __shared__ float z[128];
-    for (int i = threadIdx.x; i < w; i += blockDim.x) z[i] = b[j0 + i];
-    __syncthreads();
-    for (int r = threadIdx.x; r < w; r += blockDim.x) {
-        float s = 0.f;
-        for (int k = 0; k <= r; ++k) s = fmaf(Linv[k * nb + r], z[k], s);
-        b[j0 + r] = s;
-    }
-}
-
-__global__ void k_gemv_fwd32(const float* __restrict__ A, int K, int j0, int w, float* b, const int* skip) {
-    if (skip && *skip) return;
-    __shared__ float z[128];
-    for (int i = threadIdx.x; i < w; i += blockDim.x) z[i] = b[j0 + i];
-    __syncthreads();
-    for (int i = j0 + w + blockIdx.x * blockDim.x + threadIdx.x; i < K; i += gridDim.x * blockDim.x) {
-        float s = 0.f;
-        for (int k = 0; k < w; ++k) s = fmaf(A[(int64_t)(j0 + k) * K + i], z[k], s);
-        b[i] -= s;
-    }
-}
-
-constexpr int kChunk = 2048;
-__global__ void k_gemv_bwd_partial32(const float* __restrict__ A, int K, int j0, int w, const float* __restrict__ b,
-                                     float* partial, int nchunk, const int* skip) {
-    if (skip && *skip) return;
-    __shared__ float red[32];
-    const int k = blockIdx.x, ch = blockIdx.y;
-    const int i0 = j0 + w + ch * kChunk, i1 = min(K, i0 + kChunk);
-    float s = 0.f;
-    const float* col = A + (int64_t)(j0 + k) * K;
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) s = fmaf(col[i], b[i], s);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = 0.f;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
-        partial[k * nchunk + ch] = t;
-    }
-}
-
-__global__ void k_trsv_bwd_diag32(const float* __restrict__ Linv, int nb, int w, int j0, const float* partial,
-                                  int nchunk, float* b, const int* skip) {
-    if (skip && *skip) return;
-    __shared__ float z[128];
-    for (int r = threadIdx.x; r < w; r += blockDim.x) {
-        float s = b[j0 + r];
-        for (int ch = 0; ch < nchunk; ++ch) s -= partial[r * nchunk + ch];
-        z[r] = s;
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < w; k += blockDim.x) {
-        float s = 0.f;
-        for (int r = k; r < w; ++r) s = fmaf(Linv[k * nb + r], z[r], s);
-        b[j0 + k] = s;
-    }
-}
-
-__global__ void k_cvt64to32(int K, const double* __restrict__ a, float* b, const int* skip) {
-    if (skip && *skip) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K; i += gridDim.x * blockDim.x) b[i] = (float)a[i];
-}
-__global__ void k_cvt32to64(int K, const float* __restrict__ a, double* b, const int* skip) {
-    if (skip && *skip) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K; i += gridDim.x * blockDim.x) b[i] = (double)a[i];
 }
 
 // ------------------------------------------------------------------- PCG
@@ -433,8 +455,7 @@ void launch_schur_pack32(cudaStream_t st, psdp_ctx* c) {
 void launch_potrf_diag32(cudaStream_t st, float* A, int K, int j0, int nb, float* Linv, float* LtHi, float* LtLo,
                          int* flag) {
     const int w = (K - j0 < nb) ? K - j0 : nb;
-    const size_t sm = (size_t)2 * w * (w + 1) * sizeof(float);
-    k_potrf_diag32<<<1, kThreads, sm, st>>>(A, K, j0, w, nb, Linv, LtHi, LtLo, flag);
+    k_potrf_diag32<<<1, kPotrfThreads, potrf32_smem(w), st>>>(A, K, j0, w, nb, Linv, LtHi, LtLo, flag);
 }
 
 void launch_pack_panel32(cudaStream_t st, const float* A, int K, int j0, int nb, float* PkHi, float* PkLo) {
@@ -443,46 +464,6 @@ void launch_pack_panel32(cudaStream_t st, const float* A, int K, int j0, int nb,
     if (rest <= 0) return;
     dim3 grid((rest + 31) / 32, (w + 31) / 32);
     k_pack_panel32<<<grid, 256, 0, st>>>(A, K, j0, w, nb, PkHi, PkLo);
-}
-
-void launch_trsm32_pack(cudaStream_t st, float* A, int K, int j0, int nb, const float* Linv, float* PtHi,
-                        float* PtLo) {
-    const int w = (K - j0 < nb) ? K - j0 : nb;
-    const int rest = K - j0 - w;
-    if (rest <= 0) return;
-    const size_t sm = ((size_t)w * w + (size_t)w * (TR + 1)) * sizeof(float);
-    k_trsm32_pack<<<(rest + TR - 1) / TR, kThreads, sm, st>>>(A, K, j0, w, nb, Linv, PtHi, PtLo);
-}
-
-// z <- M^{-1} r with M = L L^T the FP32 factor (r, z FP64; work in FP32 in z32)
-void launch_precond32(cudaStream_t st, const float* A, int K, int nb, const float* Linv, float* z32, float* partial,
-                      const double* r, double* z, const int* skip) {
-    int blocks = (K + kThreads - 1) / kThreads;
-    if (blocks > 4096) blocks = 4096;
-    k_cvt64to32<<<blocks, kThreads, 0, st>>>(K, r, z32, skip);
-    const int npanel = (K + nb - 1) / nb;
-    for (int p = 0; p < npanel; ++p) {
-        const int j0 = p * nb, w = (K - j0 < nb) ? K - j0 : nb;
-        k_trsv_fwd_diag32<<<1, 128, 0, st>>>(Linv + (size_t)p * nb * nb, nb, w, j0, z32, skip);
-        const int rest = K - j0 - w;
-        if (rest > 0) {
-            int b = (rest + kThreads - 1) / kThreads;
-            if (b > 1024) b = 1024;
-            k_gemv_fwd32<<<b, kThreads, 0, st>>>(A, K, j0, w, z32, skip);
-        }
-    }
-    for (int p = npanel - 1; p >= 0; --p) {
-        const int j0 = p * nb, w = (K - j0 < nb) ? K - j0 : nb;
-        const int rest = K - j0 - w;
-        int nchunk = 0;
-        if (rest > 0) {
-            nchunk = (rest + kChunk - 1) / kChunk;
-            dim3 g(w, nchunk);
-            k_gemv_bwd_partial32<<<g, kThreads, 0, st>>>(A, K, j0, w, z32, partial, nchunk, skip);
-        }
-        k_trsv_bwd_diag32<<<1, 128, 0, st>>>(Linv + (size_t)p * nb * nb, nb, w, j0, partial, nchunk, z32, skip);
-    }
-    k_cvt32to64<<<blocks, kThreads, 0, st>>>(K, z32, z, skip);
 }
 
 void launch_pcg_init(cudaStream_t st, int K, const double* b, double* x, double* r, double* s, int* done) {
@@ -505,5 +486,4 @@ void launch_pcg_finish(cudaStream_t st, int K, const double* x, double* out, dou
 
 void init_attrs_mixed(int smem_optin) {
     set_max_dynamic_smem((const void*)k_potrf_diag32, smem_optin);
-    set_max_dynamic_smem((const void*)k_trsm32_pack, smem_optin);
 }

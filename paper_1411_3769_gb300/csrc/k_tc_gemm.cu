@@ -297,13 +297,15 @@ struct TileWalk {
 
 // Persistent form of k_tc_gemm for one large update (batch 1): one CTA per SM
 // walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...  Warp 0 issues the
-// TMA loads, warp 1 the MMAs (and owns TMEM), warps 2-5 drain the accumulator.
-// Two TMEM accumulators of BN columns alternate between tiles, so the epilogue
-// of one tile (which reads and writes C in HBM) runs under the MMAs and loads of
+// TMA loads, warp 1 the MMAs (and owns TMEM), warps 2-9 drain the accumulators.
+// Two TMEM accumulators of BN columns alternate between tiles and each has its
+// own group of four epilogue warps, so the epilogues of two tiles (each reads
+// and writes its C tile in HBM) run at once and under the MMAs and loads of
 // the next.  Barriers: full/empty per stage (TMA <-> MMA), tfull/tempty per
-// accumulator (MMA <-> epilogue, tempty counts the four epilogue warps).
+// accumulator (MMA <-> epilogue, tempty counts the group's four warps).
+constexpr int kPersistThreads = 320;
 template <int SPLIT, int STAGES>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kPersistThreads, 1)
 k_tc_gemm_persist(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
                   const __grid_constant__ CUtensorMap mAlo, const __grid_constant__ CUtensorMap mBlo, int M, int N,
                   int Kd, float* C, int64_t ldc, float alpha, float beta, int tri, int* flag) {
@@ -414,10 +416,13 @@ k_tc_gemm_persist(const __grid_constant__ CUtensorMap mA, const __grid_constant_
             mbar_wait(drain, 0, flag);
         }
     } else if (warp >= 2) {
-        // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (rows m0 + 32*(w%4) + lane)
-        const int qd = warp & 3;
+        // epilogue: two groups of four warps, group g drains the tiles i = g
+        // (mod 2), i.e. accumulator g, so two tiles' C traffic is in flight at
+        // once; warp w reads TMEM lanes 32*(w%4) .. +31 (rows m0 + 32*(w%4) + lane)
+        const int qd = warp & 3, grp = (warp - 2) >> 2;
         int i = 0;
         for (TileWalk t(M, N, tri, blockIdx.x); t.valid(); t.advance(gridDim.x), ++i) {
+            if ((i & 1) != grp) continue;
             const int b = i & 1;
             const int m0 = t.mt() * BM, n0 = t.nt * BN;
             const int m = m0 + 32 * qd + lane;
@@ -544,10 +549,10 @@ bool launch_tc_gemm_persist(cudaStream_t st, int split, const CUtensorMap& A, co
     if (tiles == 0) return true;
     const int grid = (int)std::min<int64_t>(tiles, std::max(1, ctas));
     if (split == 3)
-        k_tc_gemm_persist<3, 3><<<grid, 192, smem_bytes_persist<3, 3>(), st>>>(A, B, *Alo, *Blo, M, N, kd, C, ldc,
+        k_tc_gemm_persist<3, 3><<<grid, kPersistThreads, smem_bytes_persist<3, 3>(), st>>>(A, B, *Alo, *Blo, M, N, kd, C, ldc,
                                                                               alpha, beta, tri, flag);
     else
-        k_tc_gemm_persist<1, 4><<<grid, 192, smem_bytes_persist<1, 4>(), st>>>(A, B, A, B, M, N, kd, C, ldc, alpha,
+        k_tc_gemm_persist<1, 4><<<grid, kPersistThreads, smem_bytes_persist<1, 4>(), st>>>(A, B, A, B, M, N, kd, C, ldc, alpha,
                                                                               beta, tri, flag);
     return true;
 }

@@ -202,6 +202,8 @@ k_trsv_fwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, const dou
     const int p = s_ticket, j0 = p * W, w = min(W, K - j0);
     const T* Lp = Linv + (size_t)p * W * W;
     for (int i = threadIdx.x; i < W * W; i += TT) Ls[i] = Lp[i];
+    // this block's right-hand side, read before any wait
+    const T bown = (threadIdx.x < w) ? (T)(bin ? bin[j0 + threadIdx.x] : (double)ldcg(x + j0 + threadIdx.x)) : T(0);
     const int c = (threadIdx.x % R) * V, g = threadIdx.x / R;
     constexpr bool PRE = RPB * V <= 16;    // register budget: prefetch small tiles only
     T last[PRE ? RPB : 1][V];
@@ -265,7 +267,7 @@ k_trsv_fwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, const dou
     if (threadIdx.x < W) {
         const int rr = threadIdx.x;
         const T sum = tree_sum<T, G>(&s_off[0][rr], W);
-        acc[rr] = (rr < w) ? (T)(bin ? bin[j0 + rr] : (double)ldcg(x + j0 + rr)) - sum : T(0);
+        acc[rr] = (rr < w) ? bown - sum : T(0);
     }
     __syncthreads();
     // z_p[r] = sum_{k <= r} Linv_p(r, k) acc[k], k = g2 (mod G2)
@@ -277,10 +279,7 @@ k_trsv_fwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, const dou
     __syncthreads();
     if (threadIdx.x < w) x[j0 + threadIdx.x] = tree_sum<T, G2>(red + threadIdx.x, W);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        st_release(ready + p, 1u);
-    }
+    if (threadIdx.x == 0) st_release(ready + p, 1u);   // cumulative over the block's stores ordered by bar.sync
 }
 
 // Backward sweep L^T x = z.  Block row p: x_p = Linv_p^T (z_p - sum_{q>p} L_qp^T x_q),
@@ -309,6 +308,7 @@ k_trsv_bwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, T* x, dou
     const int p = npanel - 1 - s_ticket, j0 = p * W, w = min(W, K - j0);
     const T* Lp = Linv + (size_t)p * W * W;
     for (int i = threadIdx.x; i < W * W; i += TT) Ls[i] = Lp[i];
+    if (threadIdx.x < W) acc[threadIdx.x] = (threadIdx.x < w) ? ldcg(x + j0 + threadIdx.x) : T(0);   // z_p
     const int cl = (threadIdx.x % R) * V, g = threadIdx.x / R;
     constexpr bool PRE = SEG * RPB * V <= 16;   // register budget: prefetch small tiles only
     T last[PRE ? SEG : 1][PRE ? RPB : 1][V];
@@ -326,6 +326,7 @@ k_trsv_bwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, T* x, dou
     T part[RPB];
 #pragma unroll
     for (int t = 0; t < RPB; ++t) part[t] = T(0);
+    __syncthreads();            // z_p in acc before any thread may read it
     int qd = npanel, it = 0;    // blocks [qd, npanel) applied
     while (qd > p + 1) {
         const int qe = wait_suffix(ready, qd, p, flag, s_q, it++ & 1);
@@ -364,7 +365,7 @@ k_trsv_bwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, T* x, dou
 #pragma unroll
         for (int o = R / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         const int k = g + G * t;
-        if ((threadIdx.x % R) == 0) acc[k] = (k < w) ? ldcg(x + j0 + k) - v : T(0);
+        if ((threadIdx.x % R) == 0) acc[k] = (k < w) ? acc[k] - v : T(0);
     }
     __syncthreads();
     // x_p[k] = sum_{r >= k} Linv_p(r, k) acc[r], r = g2 (mod G2)
@@ -381,10 +382,7 @@ k_trsv_bwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, T* x, dou
         if (xout) xout[j0 + threadIdx.x] = (double)z;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        st_release(ready + p, 1u);
-    }
+    if (threadIdx.x == 0) st_release(ready + p, 1u);   // cumulative over the block's stores ordered by bar.sync
 }
 
 template <typename T, int W>
@@ -437,7 +435,7 @@ bool launch_solve_fp64(cudaStream_t st, const double* A, int K, int nb, const do
 
 // z <- M^{-1} r with M = L L^T the FP32 factor (panel width 64 or 128); the
 // sweeps run in FP32 in z32, r and z are FP64.  Nothing runs when *skip != 0.
-bool launch_precond32_flag(cudaStream_t st, const float* A, int K, int nb, const float* Linv, float* z32,
+bool launch_precond32(cudaStream_t st, const float* A, int K, int nb, const float* Linv, float* z32,
                            const double* r, double* z, unsigned* sync, int* flag, const int* skip) {
     if (nb == 128)
         sweeps<float, 128>(st, A, K, Linv, r, z32, z, sync, flag, skip);

@@ -80,7 +80,7 @@ struct psdp_ctx {
     double *d_S = nullptr;      // [M][Na][n][n]   B^T scratch
     double *d_adj = nullptr;    // [L0][Na+1][n][n] adjoint scratch
     double *d_adj2 = nullptr;   // [L0][Na][n][n]
-    double *d_y = nullptr, *d_dyh = nullptr, *d_dyb = nullptr, *d_rhs = nullptr, *d_BX = nullptr;
+    double *d_y = nullptr, *d_dyh = nullptr, *d_dyb = nullptr, *d_BX = nullptr;
     double *d_part = nullptr;   // per-block partial sums [2*nblk][4]
     double *d_tstep = nullptr;  // per-block max steps [2*nblk]
     double *d_scal = nullptr;   // [SC_COUNT]
@@ -124,7 +124,7 @@ struct psdp_ctx {
     float *d_T32 = nullptr, *d_Om32 = nullptr, *d_Linv32 = nullptr, *d_Pt_hi = nullptr, *d_Pt_lo = nullptr;
     float *d_Pk_hi = nullptr, *d_Pk_lo = nullptr;   // unsolved panel, K-major TF32 pairs [K][nb32]
     float *d_Lt_hi = nullptr, *d_Lt_lo = nullptr;   // current diagonal-block inverse, row-major TF32 pairs
-    float *d_z32 = nullptr, *d_part32 = nullptr;
+    float *d_z32 = nullptr;
     double *d_pcg_x = nullptr, *d_pcg_r = nullptr, *d_pcg_z = nullptr, *d_pcg_p = nullptr, *d_pcg_q = nullptr;
     double *d_pcg_state = nullptr;
     int *d_pcg_done = nullptr;
@@ -210,9 +210,6 @@ void launch_schur_gather(cudaStream_t st, psdp_ctx* c, int p0, int np);
 
 // dense Cholesky (Omega stored row-major with the upper triangle, i.e. column-major lower)
 void launch_potrf_diag(cudaStream_t st, double* A, int K, int j0, int nb, double* Linv, int* flag);
-void dense_cholesky(cudaStream_t st, double* A, int K, int nb, double* Linv, int* flag);
-void dense_solve(cudaStream_t st, const double* A, int K, int nb, const double* Linv, double* partial, double* x);
-void launch_vec_copy(cudaStream_t st, int K, const double* a, double* out);
 void launch_cdiag(cudaStream_t st, psdp_ctx* c);
 
 // raise the dynamic shared-memory limit of the shared-memory-heavy kernels once,
@@ -253,18 +250,15 @@ void launch_schur_gather32(cudaStream_t st, psdp_ctx* c, int p0, int np, const f
 void launch_potrf_diag32(cudaStream_t st, float* A, int K, int j0, int nb, float* Linv, float* LtHi, float* LtLo,
                          int* flag);
 void launch_pack_panel32(cudaStream_t st, const float* A, int K, int j0, int nb, float* PkHi, float* PkLo);
-void launch_trsm32_pack(cudaStream_t st, float* A, int K, int j0, int nb, const float* Linv, float* PtHi,
-                        float* PtLo);
+
 // Triangular sweeps with the dense factor (one launch per sweep, flag-synchronised
 // block rows).  sync needs trsv_sync_words(K, nb) words; false for an
 // unsupported panel width (FP64: 32; FP32: 64, 128).
 size_t trsv_sync_words(int K, int nb);
 bool launch_solve_fp64(cudaStream_t st, const double* A, int K, int nb, const double* Linv, double* x,
                        unsigned* sync, int* flag);
-bool launch_precond32_flag(cudaStream_t st, const float* A, int K, int nb, const float* Linv, float* z32,
+bool launch_precond32(cudaStream_t st, const float* A, int K, int nb, const float* Linv, float* z32,
                            const double* r, double* z, unsigned* sync, int* flag, const int* skip);
-void launch_precond32(cudaStream_t st, const float* A, int K, int nb, const float* Linv, float* z32, float* partial,
-                      const double* r, double* z, const int* skip);
 void launch_pcg_init(cudaStream_t st, int K, const double* b, double* x, double* r, double* s, int* done);
 void launch_pcg_start(cudaStream_t st, int K, const double* r, const double* z, double* p, double* s, const int* done);
 void launch_pcg_alpha(cudaStream_t st, int K, const double* p, const double* q, double* x, double* r, double* s,

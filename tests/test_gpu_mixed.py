@@ -70,6 +70,9 @@ def test_mixed_step_matches_oracle(bd, name, seed, k):
         ipm.newton_step(prob, st, ipm.Options())
         s, info = bd.psdp_step(h)
         assert s == 0 and info[13] == 0.0          # no fallback to FP64
+        # a sound FP32 factor preconditions both systems to the 1e-12 target in a
+        # few iterations each (8 is the cap per solve)
+        assert info[12] <= 10
         X, Z, y = bd.psdp_get_iterate(h)
         assert np.abs(y - st.y).max() <= 1e-8 * (1 + np.abs(st.y).max())
         assert np.abs(X - st.X).max() <= 1e-8 * (1 + np.abs(st.X).max())
