@@ -120,8 +120,13 @@ def newton_step(prob: Problem, st: State, opt: Options) -> dict:
     dXb = sym(mu * Y - YdZdX - np.einsum("gab,gbc,gcd->gad", Y, dZb, X))
     dX, dZ, dy = dXh + dXb, dZh + dZb, dyh + dyb
     # step lengths and update (Eqs. X, y, Z)
-    tp = min(1.0, opt.tau * max_step(X, dX))
-    td = min(1.0, opt.tau * max_step(Z, dZ))
+    try:
+        tp = min(1.0, opt.tau * max_step(X, dX))
+        td = min(1.0, opt.tau * max_step(Z, dZ))
+    except np.linalg.LinAlgError:
+        # a block no longer numerically positive definite (the iterate is
+        # diverging on an infeasible problem): stop as the library does
+        return dict(status=CHOL_BLOCK)
     st.X = X + tp * dX
     st.Z = Z + td * dZ
     st.y = y + td * dy

@@ -170,6 +170,36 @@ def homogenize(terms: dict, l: int) -> dict:
     return out
 
 
+def substitute_linear(terms: dict, M) -> dict:
+    """A(M alpha) for A(beta) = sum_gamma A_gamma beta^gamma (Sec. V, Examples 1
+    and 2 pose the uncertainty set as the image of the simplex under a map g
+    and certify A'(alpha) = A(g(alpha)) on the simplex).
+
+    ``terms`` maps exponent tuples to coefficients; M is l x l, beta_i =
+    sum_j M_ij alpha_j, so a homogeneous A of degree d stays homogeneous of
+    degree d.  Each beta^gamma is expanded factor by factor (brute-force
+    polynomial multiplication).
+    """
+    M = np.asarray(M, dtype=np.float64)
+    l = M.shape[0]
+    out: dict = {}
+    for expo, coef in terms.items():
+        poly = {tuple([0] * l): 1.0}
+        for i in range(l):
+            for _ in range(expo[i]):
+                nxt: dict = {}
+                for e, v in poly.items():
+                    for j in range(l):
+                        if M[i, j] == 0.0:
+                            continue
+                        e2 = tuple(e[k] + (1 if k == j else 0) for k in range(l))
+                        nxt[e2] = nxt.get(e2, 0.0) + v * M[i, j]
+                poly = nxt
+        for e, v in poly.items():
+            out[e] = out.get(e, 0) + v * np.asarray(coef, dtype=np.float64)
+    return out
+
+
 def sizes(n: int, l: int, d_p: int, d1: int, d2: int | None = None, d_a: int = 1) -> dict:
     """Eqs. (L0), (L), (M), (K): the SDP's dimensions."""
     if d2 is None:

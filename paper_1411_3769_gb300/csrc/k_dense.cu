@@ -70,24 +70,26 @@ k_potrf_diag(double* A, int K, int j0, int w, int nb, double* Linv, int* flag) {
     if (threadIdx.x == 0 && bad) atomicOr(flag, (int)FL_CHOL_SCHUR);
 }
 
-// Diagonal block of at most 32 columns, four warps.  GB300's FP64 pipe is
-// narrow, so the critical path is counted in dependent FP64 operations:
-// column j needs one rsqrt (1/L_jj; L_jj = piv * rsqrt(piv)) shared by the
-// column scale, then a rank-1 update spread over 128 threads.  L^{-1} is
-// built by 2 x 2 block recursion: the 16 x 16 diagonal inverses by forward
-// substitution in two warps at once, then -C^{-1} (B A^{-1}) as two small GEMMs.
+// Diagonal block of at most 32 columns, four warps, factor and inverse in one
+// sweep.  GB300's FP64 pipe is narrow, so the critical path is counted in
+// dependent FP64 operations: column j needs one rsqrt (L_jj = piv * rsqrt(piv))
+// shared by the column scale and by row j of L^{-1}, then one rank-1 step
+// that updates the trailing lower triangle of L and, beside it, the running
+// sums of L^{-1}:  S(i, c) = -sum_{k<j} L(i, k) X(k, c),  X(j, c) = S(j, c) / L_jj.
+// Row i of the combined update touches positions q <= i: S(i, q) for q <= j,
+// L(i, q) for q > j (warps take rows, lanes take q).  The block is padded to
+// 32 with an identity tail.
 __global__ void __launch_bounds__(128)
 k_potrf_diag32x4(double* A, int K, int j0, int w, int nb, double* Linv, int* flag) {
     constexpr int LD = 33;
-    __shared__ double L[32 * LD];   // column-major: L[c*LD + r]
-    __shared__ double X[32 * LD];   // L^{-1}, column-major
-    __shared__ double T[16 * 17];
-    __shared__ double rinv[32], ldiag[32];
+    __shared__ double L[32 * LD];   // column-major: L(r, c) = L[c*LD + r]
+    __shared__ double X[32 * LD];   // S, then L^{-1}, column-major
+    __shared__ double ldiag[32];
     __shared__ int bad;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) bad = 0;
     for (int idx = tid; idx < 32 * 32; idx += 128) {
-        const int c = idx / 32, r = idx % 32;
+        const int c = idx >> 5, r = idx & 31;
         double v = (r == c) ? 1.0 : 0.0;
         if (r < w && c < w && r >= c) v = A[(int64_t)(j0 + c) * K + j0 + r];
         L[c * LD + r] = v;
@@ -101,48 +103,25 @@ k_potrf_diag32x4(double* A, int K, int j0, int w, int nb, double* Linv, int* fla
             piv = 1.0;
         }
         const double ri = rsqrt(piv);
-        if (tid == 0) {
-            rinv[j] = ri;
-            ldiag[j] = piv * ri;    // L_jj; the stored diagonal is read by no later step
-        }
-        if (tid > j && tid < 32) L[j * LD + tid] *= ri;
-        __syncthreads();
-        // trailing lower triangle: the four warps take columns, lanes take rows
-        for (int c = j + 1 + (tid >> 5); c < 32; c += 4) {
-            const double ljc = L[j * LD + c];
-            const int r = tid & 31;
-            if (r >= c) L[c * LD + r] = fma(-L[j * LD + r], ljc, L[c * LD + r]);
+        if (wid == 0) {
+            if (lane > j) L[j * LD + lane] *= ri;                  // column j of L
+        } else if (wid == 1) {
+            if (lane < j) X[lane * LD + j] *= ri;                  // row j of L^{-1}
+            else if (lane == j) X[j * LD + j] = ri;
+        } else if (tid == 64) {
+            ldiag[j] = piv * ri;
         }
         __syncthreads();
-    }
-    // diagonal 16 x 16 inverses: warp 0 -> rows/cols 0..15, warp 1 -> 16..31 (lane = column)
-    if (tid < 64 && (tid & 31) < 16) {
-        const int o = (tid >> 5) * 16, c = o + (tid & 31);
-        for (int r = c; r < o + 16; ++r) {
-            double s = (r == c) ? 1.0 : 0.0;
-            for (int k = c; k < r; ++k) s = fma(-L[k * LD + r], X[c * LD + k], s);
-            X[c * LD + r] = s * rinv[r];
+        for (int i = j + 1 + wid; i < 32; i += 4) {
+            const double lij = L[j * LD + i];
+            const int q = lane;
+            if (q <= j) X[q * LD + i] = fma(-lij, X[q * LD + j], X[q * LD + i]);
+            else if (q <= i) L[q * LD + i] = fma(-lij, L[j * LD + q], L[q * LD + i]);
         }
+        __syncthreads();
     }
-    __syncthreads();
-    // T = B A^{-1}   (B = L[16..31][0..15], A^{-1} = X[0..15][0..15])
-    for (int idx = tid; idx < 256; idx += 128) {
-        const int r = idx / 16, c = idx % 16;
-        double s = 0.0;
-        for (int k = c; k < 16; ++k) s = fma(L[k * LD + 16 + r], X[c * LD + k], s);
-        T[r * 17 + c] = s;
-    }
-    __syncthreads();
-    // X[16..31][0..15] = -C^{-1} T
-    for (int idx = tid; idx < 256; idx += 128) {
-        const int r = idx / 16, c = idx % 16;
-        double s = 0.0;
-        for (int k = 0; k <= r; ++k) s = fma(X[(16 + k) * LD + 16 + r], T[k * 17 + c], s);
-        X[c * LD + 16 + r] = -s;
-    }
-    __syncthreads();
     for (int idx = tid; idx < 32 * 32; idx += 128) {
-        const int c = idx / 32, r = idx % 32;
+        const int c = idx >> 5, r = idx & 31;
         if (r < w && c < w && r >= c) A[(int64_t)(j0 + c) * K + j0 + r] = (r == c) ? ldiag[c] : L[c * LD + r];
     }
     for (int idx = tid; idx < nb * nb; idx += 128) {

@@ -1,0 +1,53 @@
+"""Example 2 of Sec. V on the GPU: the bisection driver over the library
+against the oracle's bisection on the same scales (same verdicts, so the same
+bound), and the batched multisection against the same bound."""
+
+import numpy as np
+import pytest
+
+from tests.test_oracle_example2 import L_OPT, certified, load_example2, oracle_bisect
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bd():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1411_3769_gb300 import build
+    build.build()
+    from paper_1411_3769_gb300 import binding
+    binding._lib()
+    return binding
+
+
+def test_substitution_matches_oracle(bd):
+    from oracle import polya
+    from paper_1411_3769_gb300 import robust
+    from tests.test_oracle_example2 import coeffs_on_simplex, g_matrix
+    for L in (-0.1, 0.0, 0.3):
+        ours = robust.substitute(load_example2(), robust.simplex_scale_map(L, 3))
+        assert np.allclose(ours, coeffs_on_simplex(L), rtol=1e-13, atol=1e-14)
+    assert np.array_equal(robust.simplex_scale_map(0.25, 3), g_matrix(0.25))
+    assert robust.monomials(3, 3) == polya.monomials(3, 3)
+
+
+@pytest.mark.parametrize("d_p,d1", [(1, 1), (2, 2)])
+def test_bisection_matches_oracle(bd, d_p, d1):
+    from paper_1411_3769_gb300 import robust
+    ours, trace = robust.bisect(load_example2(), -0.2, 1.0, d_p, d1, iters=10)
+    assert ours == oracle_bisect(d_p, d1, iters=10)
+    assert ours > L_OPT
+    # each verdict on the way agrees with the oracle's at the same scale
+    for s, v in trace[:4]:
+        assert v == int(certified(s, d_p, d1)[0])
+
+
+def test_batched_multisection_brackets_the_bisection_bound(bd):
+    from paper_1411_3769_gb300 import robust
+    b_bis, _ = robust.bisect(load_example2(), -0.2, 1.0, 2, 3, iters=12)
+    b_mul, trace = robust.multisection(load_example2(), -0.2, 1.0, 2, 3, points=7, rounds=4)
+    assert len(trace) == 28
+    assert abs(b_mul - b_bis) <= 1.2 / 8 ** 4 + 1.2 / 2 ** 12
+    assert b_mul > L_OPT
