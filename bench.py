@@ -219,14 +219,14 @@ def oracle_steps(A, w, nsteps):
     return times
 
 
-def measure_mixed(bd, synth, name, device, nsteps):
+def measure_mixed(bd, synth, name, device, nsteps, crit_sms=0):
     """Mixed-precision Newton steps/s (from the cold start, CUDA events around
     each step on the library's stream) and the full time-to-certificate."""
     import torch
     w = synth.WORKLOADS[name]
     A = synth.system(w["n"], w["l"], w["s"], 0)
     stream = torch.cuda.Stream()
-    opts = bd.psdp_default_opts(stream=stream.cuda_stream, device=device, precision=1)
+    opts = bd.psdp_default_opts(stream=stream.cuda_stream, device=device, precision=1, crit_sms=crit_sms)
     h = bd.psdp_setup(w["n"], w["l"], w["d_p"], w["d1"], A, opts)
     try:
         X0, Z0, y0 = bd.psdp_get_iterate(h)
@@ -261,7 +261,7 @@ def measure_mixed(bd, synth, name, device, nsteps):
     finally:
         bd.psdp_destroy(h)
     t0 = time.perf_counter()
-    with bd.Solver(A, w["d_p"], w["d1"], device=device, precision=1) as s:
+    with bd.Solver(A, w["d_p"], w["d1"], device=device, precision=1, crit_sms=crit_sms) as s:
         status, iters, info = s.solve()
         verdict, _, _ = s.certify()
         bd.psdp_get_P(s.h)

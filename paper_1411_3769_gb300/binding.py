@@ -36,7 +36,8 @@ EXPORTS = ("psdp_default_opts", "psdp_setup", "psdp_sizes", "psdp_step", "psdp_s
 class Opts(C.Structure):
     _fields_ = [("delta", C.c_double), ("delta_L", C.c_double), ("eps", C.c_double), ("sigma", C.c_double),
                 ("tau", C.c_double), ("max_iter", C.c_int), ("d2", C.c_int), ("d_a", C.c_int),
-                ("precision", C.c_int), ("use_graph", C.c_int), ("stream", C.c_void_p), ("device", C.c_int)]
+                ("precision", C.c_int), ("use_graph", C.c_int), ("stream", C.c_void_p), ("device", C.c_int),
+                ("crit_sms", C.c_int)]
 
 
 class PsdpError(RuntimeError):

@@ -213,7 +213,8 @@ void enqueue_schur_mixed(psdp_ctx* c) {
 }
 
 // SMs the persistent trailing update leaves free for the panel factor, the
-// panel solve and the next-rows update of the look-ahead.
+// panel solve and the next-rows update of the look-ahead (psdp_opts.crit_sms
+// overrides it).
 constexpr int kCritSms = 16;
 
 // FP32 Cholesky of Omega32: diagonal blocks factored and inverted in FP32 shared
@@ -248,7 +249,9 @@ void enqueue_cholesky_mixed(psdp_ctx* c) {
             // panel solve P L_jj^{-T} on the tensor cores (3xTF32): written back
             // to Omega's panel rows and, as TF32 pairs, packed for the update
             ProfScope q(c, "chol32_trsm", cs);
-            launch_pack_panel32(cs, A, K, j0, nb, c->d_Pk_hi, c->d_Pk_lo);
+            // panel 0 is packed from Omega; every later panel was packed by the
+            // epilogue of the previous next-rows update, which produced it
+            if (p == 0) launch_pack_panel32(cs, A, K, j0, nb, c->d_Pk_hi, c->d_Pk_lo);
             launch_tc_gemm(cs, false, 3, pkh, lth, &pkl, &ltl, rest, w, 1, 0, nullptr, w, A + (int64_t)j0 * K + j0 + w,
                            K, 0, 1.f, 0.f, 0, c->d_flag, phi, plo, nb);
         }
@@ -272,15 +275,18 @@ void enqueue_cholesky_mixed(psdp_ctx* c) {
         stream_dep(st, cs, c->ev_fork);                     // crit: after bulk(p-1)
         {
             // rows [0, w2) of the trailing upper triangle (C[n][m], n < w2, m >= n)
+            // rows [0, w2) of the trailing matrix are panel p+1: the epilogue also
+            // packs them (columns from w2 on) K-major as TF32 pairs for its solve
             ProfScope q(c, "chol32_syrk_next", cs);
             launch_tc_gemm(cs, false, 3, hi, hi2, &lo, &lo2, rest, w2, 1, 0, nullptr, w, T, K, 0, -1.f, 1.f, 1,
-                           c->d_flag);
+                           c->d_flag, c->d_Pk_hi, c->d_Pk_lo, nb, w2);
         }
         if (rest > w2) {
             // persistent CTAs leave a few SMs to the critical-path kernels
             ProfScope q(c, "chol32_syrk_tc", st);
+            const int crit = c->opt.crit_sms > 0 ? c->opt.crit_sms : kCritSms;
             launch_tc_gemm_persist(st, 3, hib, hib, &lob, &lob, rest - w2, rest - w2, w, T + (int64_t)w2 * K + w2, K,
-                                   -1.f, 1.f, 1, std::max(1, c->num_sms - kCritSms), c->d_flag);
+                                   -1.f, 1.f, 1, std::max(1, c->num_sms - crit), c->d_flag);
         }
     }
     stream_dep(cs, st, c->ev_join);
@@ -598,7 +604,7 @@ psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psd
         return PSDP_EINVAL;
     if (!(opt.tau > 0 && opt.tau < 1) || !(opt.sigma >= 0 && opt.sigma < 1) || !(opt.eps > 0) || opt.max_iter < 1 ||
         !std::isfinite(opt.delta) || !std::isfinite(opt.delta_L) ||
-        (opt.precision != PSDP_FP64 && opt.precision != PSDP_MIXED))
+        (opt.precision != PSDP_FP64 && opt.precision != PSDP_MIXED) || opt.crit_sms < 0)
         return PSDP_EINVAL;
     const int64_t Na = hcard(l, d_a), L0 = hcard(l, d_p), L = hcard(l, d_p + d1), M = hcard(l, d_p + d_a + d2);
     const int64_t Nt = (int64_t)n * (n + 1) / 2, K = L0 * Nt;
@@ -822,6 +828,7 @@ void psdp_default_opts(psdp_opts* o) {
     o->use_graph = 1;
     o->stream = nullptr;
     o->device = 0;
+    o->crit_sms = 0;
 }
 
 psdp_status psdp_setup(int n, int l, int d_p, int d1, const double* A, const psdp_opts* o, psdp_ctx** out) {

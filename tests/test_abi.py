@@ -37,7 +37,7 @@ def test_default_opts_and_strerror(lib):
     from paper_1411_3769_gb300 import binding as b
     o = b.psdp_default_opts()
     assert o.delta == 1.0 and o.eps == 1e-7 and abs(o.sigma - 1 / 3) < 1e-15 and o.tau == 0.95
-    assert o.d2 == -1 and o.d_a == 1 and o.max_iter == 100
+    assert o.d2 == -1 and o.d_a == 1 and o.max_iter == 100 and o.crit_sms == 0
     assert b.psdp_strerror(0) == "ok"
     assert "positive definite" in b.psdp_strerror(5)
 
@@ -63,6 +63,9 @@ def test_setup_rejects_nonfinite_and_bad_options(lib):
     assert e.value.name == "EINVAL"
     with pytest.raises(b.PsdpError) as e:
         b.psdp_setup(3, 2, 1, 1, np.zeros((2, 3, 3)), b.psdp_default_opts(tau=1.5))
+    assert e.value.name == "EINVAL"
+    with pytest.raises(b.PsdpError) as e:
+        b.psdp_setup(3, 2, 1, 1, np.zeros((2, 3, 3)), b.psdp_default_opts(precision=1, crit_sms=-1))
     assert e.value.name == "EINVAL"
 
 
