@@ -35,6 +35,10 @@ METRIC = "Newton steps/s (plain FP64 path; time-to-certificate in e2e)"
 UNIT = "steps/s"
 NOMINAL_BF16_TFLOPS = 2250.0
 NOMINAL_FP64_TFLOPS = 1.25
+# DRAM read + write bytes per bulk trailing-update launch (mean over the 64
+# launches of one mid-workload step), from one ncu capture of the current
+# k_gemm_tn revision; to be refreshed whenever that kernel changes
+CHOL_BULK_DRAM_BYTES = 6.48e6
 
 
 def parse():
@@ -519,7 +523,8 @@ def run_ours(args):
     dom = max(("schur_gemm", "chol_syrk_gemm"), key=lambda k: kern.get(k, {}).get("share_of_step", 0))
     ach = kern.get(dom, {}).get("tflops")
     roof = {"kernel": "k_gemm_tn (" + dom + ")", "bound": "fp64", "achieved": ach,
-            "peak": fp64_peak, "unit": "TFLOP/s", "frac": (ach / fp64_peak) if ach else None, "traffic": None,
+            "peak": fp64_peak, "unit": "TFLOP/s", "frac": (ach / fp64_peak) if ach else None,
+            "traffic": CHOL_BULK_DRAM_BYTES if dom == "chol_syrk_gemm" else None,
             "peak_source": f"{pk_kind} bf16 {pk['bf16_tflops']} TFLOP/s x nominal FP64/BF16 ratio 1.25/2250"}
     try:
         roof["fp64_probe_tflops"] = bd.psdp_fp64_peak(local)
