@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--mixed-steps", type=int, default=5)
     ap.add_argument("--fp64-large", type=int, default=1, help="time one plain FP64 step of the large workload")
     ap.add_argument("--mixed-workloads", default="mid,large")
-    ap.add_argument("--extra-items", default="syrk,batch,warm")
+    ap.add_argument("--extra-items", default="ex2,syrk,batch,warm")
     ap.add_argument("--syrk-m", type=int, default=15000)
     ap.add_argument("--extra", action="store_true", help="measure the batched and warm-start rows instead")
     ap.add_argument("--batch-count", type=int, default=512)
@@ -369,6 +369,36 @@ def measure_syrk_probe(bd, M, K=128, ctas=152):
             "useful_tflops": flops / (ms * 1e-3) / 1e12}
 
 
+def load_example2():
+    """The six 3x3 coefficients printed in Sec. V, Example 2 (exponent -> matrix)."""
+    mats, cur = {}, None
+    with open(os.path.join(ROOT, "tests", "golden", "example2_A.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line.startswith("A"):
+                cur = tuple(int(x) for x in line.split()[1:])
+                mats[cur] = []
+            else:
+                mats[cur].append([float(x) for x in line.split()])
+    return {k: np.array(v) for k, v in mats.items()}
+
+
+def measure_example2(degrees=((1, 1), (2, 2), (2, 3), (3, 3), (3, 4))):
+    """Upper bounds on L_opt = -0.111 (Sec. V, Example 2) by batched multisection
+    (7 scales per round, 4 rounds, scale range [-0.2, 1]), wall time per bound."""
+    from paper_1411_3769_gb300 import robust
+    terms = load_example2()
+    out = []
+    for d_p, d1 in degrees:
+        t0 = time.perf_counter()
+        bound, trace = robust.multisection(terms, -0.2, 1.0, d_p, d1, points=7, rounds=4)
+        out.append({"d_p": d_p, "d1=d2": d1, "bound": bound, "solves": len(trace),
+                    "seconds": time.perf_counter() - t0})
+    return {"L_opt_printed": -0.111, "bounds": out}
+
+
 def run_extra(args):
     """Batched, learned-warm-start and kernel-probe rows (minutes of GPU time;
     not the default line)."""
@@ -380,6 +410,8 @@ def run_extra(args):
     from paper_1411_3769_gb300 import synth
     items = [x for x in args.extra_items.split(",") if x]
     out = {}
+    if "ex2" in items:
+        out["example2"] = measure_example2()
     if "syrk" in items:
         out["syrk_probe"] = [measure_syrk_probe(bd, args.syrk_m, ctas=c) for c in (152, 136)]
     if "batch" in items:

@@ -245,6 +245,13 @@ psdp_status psdp_tc_gemm_check(int M, int N, int K, int dtype, int split, const 
  * persistent CTAs (>= 1; fewer CTAs walk more tiles each).  ms (may be NULL)
  * receives the kernel's duration from CUDA events around the launch.  Allocates
  * its own scratch.  Errors: EINVAL on bad sizes, ETIMEOUT if a bounded wait expired. */
+/* Self-test of the bounded device waits (no counterpart in the paper): runs a
+ * triangular sweep in which one block is never solved, so every waiting CTA
+ * gives up after its 2 s limit.  Returns PSDP_ETIMEOUT when the wait gave up as
+ * designed (the context stays usable), PSDP_OK if it did not; waited_ms (may be
+ * NULL) receives the kernel's duration. */
+psdp_status psdp_trsv_timeout_check(float* waited_ms);
+
 psdp_status psdp_tc_gemm_persist_check(int M, int N, int K, int split, int tri, int ctas, const float* A,
                                        const float* B, float* C, float* ms);
 

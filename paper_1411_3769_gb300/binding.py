@@ -28,7 +28,7 @@ EXPORTS = ("psdp_default_opts", "psdp_setup", "psdp_sizes", "psdp_step", "psdp_s
            "psdp_grid_check", "psdp_get_P", "psdp_get_y", "psdp_get_tables", "psdp_load_iterate",
            "psdp_get_iterate", "psdp_get_schur", "psdp_apply_BT", "psdp_apply_B", "psdp_profile_enable",
            "psdp_profile_reset", "psdp_profile_get", "psdp_work", "psdp_stream", "psdp_fp64_peak",
-           "psdp_destroy", "psdp_strerror", "psdp_tc_gemm_check", "psdp_tc_gemm_persist_check", "psdp_get_schur_mixed",
+           "psdp_destroy", "psdp_strerror", "psdp_tc_gemm_check", "psdp_tc_gemm_persist_check", "psdp_trsv_timeout_check", "psdp_get_schur_mixed",
            "psdp_tc_gemm_noalloc", "psdp_solve_batch", "psdp_autotune", "psdp_set_start", "psdp_mlp_create",
            "psdp_mlp_destroy", "psdp_mlp_params", "psdp_mlp_grads", "psdp_mlp_train", "psdp_mlp_predict")
 
@@ -86,6 +86,7 @@ def _lib():
             "psdp_tc_gemm_check": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp]),
             "psdp_tc_gemm_persist_check": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp,
                                                      vp, vp]),
+            "psdp_trsv_timeout_check": (C.c_int, [vp]),
             "psdp_get_schur_mixed": (C.c_int, [vp, vp]),
             "psdp_tc_gemm_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]),
             "psdp_solve_batch": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
@@ -301,6 +302,13 @@ def psdp_tc_gemm_persist_check(A: np.ndarray, B: np.ndarray, C0: np.ndarray, spl
     _check(_lib().psdp_tc_gemm_persist_check(M, N, K, split, tri, ctas, A.ctypes.data, B.ctypes.data,
                                              C_.ctypes.data, ms.ctypes.data), "psdp_tc_gemm_persist_check")
     return (C_.T, float(ms[0])) if timing else C_.T
+
+
+def psdp_trsv_timeout_check() -> tuple[str, float]:
+    """Status name and the kernel's duration in ms of the bounded-wait self-test."""
+    ms = np.zeros(1, dtype=np.float32)
+    s = _lib().psdp_trsv_timeout_check(ms.ctypes.data)
+    return STATUS.get(s, str(s)), float(ms[0])
 
 
 def psdp_tc_gemm_noalloc(M: int, N: int, K: int, split: int, A_ptr: int, B_ptr: int, C_ptr: int,

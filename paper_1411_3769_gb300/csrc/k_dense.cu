@@ -72,19 +72,21 @@ k_potrf_diag(double* A, int K, int j0, int w, int nb, double* Linv, int* flag) {
 
 // Diagonal block of at most 32 columns, four warps, factor and inverse in one
 // sweep.  GB300's FP64 pipe is narrow, so the critical path is counted in
-// dependent FP64 operations: column j needs one rsqrt (L_jj = piv * rsqrt(piv))
-// shared by the column scale and by row j of L^{-1}, then one rank-1 step
-// that updates the trailing lower triangle of L and, beside it, the running
-// sums of L^{-1}:  S(i, c) = -sum_{k<j} L(i, k) X(k, c),  X(j, c) = S(j, c) / L_jj.
-// Row i of the combined update touches positions q <= i: S(i, q) for q <= j,
-// L(i, q) for q > j (warps take rows, lanes take q).  The block is padded to
-// 32 with an identity tail.
+// dependent FP64 operations.  Column j needs 1/L_jj = rsqrt(piv_j) for the
+// column scale and for row j of L^{-1}; then one rank-1 step updates the
+// trailing lower triangle of L and, beside it, the running sums of L^{-1}:
+// S(i, c) = -sum_{k<j} L(i, k) X(k, c), X(j, c) = S(j, c) / L_jj.  Row i of the
+// combined update touches positions q <= i: S(i, q) for q <= j, L(i, q) for
+// q > j (a lane per q).  Warp 0 updates only row j+1 and computes the next
+// pivot's rsqrt at once, while warps 1-3 update the other rows, so the rsqrt
+// overlaps the rank-1 step.  The block is padded to 32 with an identity tail.
 __global__ void __launch_bounds__(128)
 k_potrf_diag32x4(double* A, int K, int j0, int w, int nb, double* Linv, int* flag) {
     constexpr int LD = 33;
     __shared__ double L[32 * LD];   // column-major: L(r, c) = L[c*LD + r]
     __shared__ double X[32 * LD];   // S, then L^{-1}, column-major
     __shared__ double ldiag[32];
+    __shared__ double s_piv, s_ri;
     __shared__ int bad;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) bad = 0;
@@ -96,13 +98,19 @@ k_potrf_diag32x4(double* A, int K, int j0, int w, int nb, double* Linv, int* fla
         X[c * LD + r] = 0.0;
     }
     __syncthreads();
-    for (int j = 0; j < 32; ++j) {
-        double piv = L[j * LD + j];
+    if (tid == 0) {
+        double piv = L[0];
         if (!(piv > 0.0) || !isfinite(piv)) {
-            if (tid == 0) bad = 1;
+            bad = 1;
             piv = 1.0;
         }
-        const double ri = rsqrt(piv);
+        s_piv = piv;
+        s_ri = rsqrt(piv);
+    }
+    __syncthreads();
+    const int q = lane;
+    for (int j = 0; j < 32; ++j) {
+        const double ri = s_ri, piv = s_piv;
         if (wid == 0) {
             if (lane > j) L[j * LD + lane] *= ri;                  // column j of L
         } else if (wid == 1) {
@@ -112,11 +120,29 @@ k_potrf_diag32x4(double* A, int K, int j0, int w, int nb, double* Linv, int* fla
             ldiag[j] = piv * ri;
         }
         __syncthreads();
-        for (int i = j + 1 + wid; i < 32; i += 4) {
-            const double lij = L[j * LD + i];
-            const int q = lane;
-            if (q <= j) X[q * LD + i] = fma(-lij, X[q * LD + j], X[q * LD + i]);
-            else if (q <= i) L[q * LD + i] = fma(-lij, L[j * LD + q], L[q * LD + i]);
+        const bool sx = q <= j;
+        double* U = sx ? X : L;                                    // U(i, q) = U[q*LD + i]
+        const double vq = sx ? X[q * LD + j] : L[j * LD + q];      // X(j, q) or L(q, j)
+        if (wid == 0) {
+            const int i = j + 1;
+            if (i < 32 && (sx || q <= i)) {
+                const double u = fma(-L[j * LD + i], vq, U[q * LD + i]);
+                U[q * LD + i] = u;
+                if (q == i) {                                      // next pivot, its rsqrt now
+                    double p = u;
+                    if (!(p > 0.0) || !isfinite(p)) {
+                        bad = 1;
+                        p = 1.0;
+                    }
+                    s_piv = p;
+                    s_ri = rsqrt(p);
+                }
+            }
+        } else {
+#pragma unroll 4
+            for (int i = j + 1 + wid; i < 32; i += 3) {
+                if (sx || q <= i) U[q * LD + i] = fma(-L[j * LD + i], vq, U[q * LD + i]);
+            }
         }
         __syncthreads();
     }

@@ -445,3 +445,53 @@ bool launch_precond32(cudaStream_t st, const float* A, int K, int nb, const floa
         return false;
     return true;
 }
+
+// Self-test of the bounded wait (no counterpart in the paper): a forward sweep
+// whose block 0 is never solved.  Tickets start at 1, so every CTA waits for a
+// ready flag that nothing sets; each gives up after 2 s, raises FL_TIMEOUT and
+// finishes.  All indices stay inside the buffers (K = 256, eight blocks of 32,
+// seven CTAs for blocks 1..7).
+extern "C" psdp_status psdp_trsv_timeout_check(float* waited_ms) {
+    constexpr int K = 256, W = 32, np = K / W;
+    double *A = nullptr, *Li = nullptr, *x = nullptr;
+    unsigned* sync = nullptr;
+    int* flag = nullptr;
+    psdp_status s = PSDP_OK;
+    if (cudaMalloc((void**)&A, (size_t)K * K * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&Li, (size_t)np * W * W * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&x, (size_t)K * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&sync, (size_t)(2 + 2 * np) * sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc((void**)&flag, sizeof(int)) != cudaSuccess)
+        s = PSDP_ENOMEM;
+    if (s == PSDP_OK) {
+        cudaMemset(A, 0, (size_t)K * K * sizeof(double));
+        cudaMemset(Li, 0, (size_t)np * W * W * sizeof(double));
+        cudaMemset(x, 0, (size_t)K * sizeof(double));
+        cudaMemset(sync, 0, (size_t)(2 + 2 * np) * sizeof(unsigned));
+        cudaMemset(flag, 0, sizeof(int));
+        const unsigned first = 1;
+        cudaMemcpy(sync, &first, sizeof(unsigned), cudaMemcpyHostToDevice);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0);
+        k_trsv_fwd<double, W, 2><<<np - 1, TT, trsv_smem<double>(W)>>>(A, K, Li, nullptr, x, sync, flag, nullptr);
+        cudaEventRecord(e1);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) s = PSDP_ECUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (waited_ms) *waited_ms = ms;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        int h = 0;
+        cudaMemcpy(&h, flag, sizeof(int), cudaMemcpyDeviceToHost);
+        if (s == PSDP_OK) s = (h & FL_TIMEOUT) ? PSDP_ETIMEOUT : PSDP_OK;
+    }
+    cudaFree(A);
+    cudaFree(Li);
+    cudaFree(x);
+    cudaFree(sync);
+    cudaFree(flag);
+    cudaGetLastError();
+    return s;
+}
