@@ -37,8 +37,9 @@ NOMINAL_BF16_TFLOPS = 2250.0
 NOMINAL_FP64_TFLOPS = 1.25
 # DRAM read + write bytes per bulk trailing-update launch (mean over the 64
 # launches of one mid-workload step), from one ncu capture of the current
-# k_gemm_tn revision; to be refreshed whenever that kernel changes
-CHOL_BULK_DRAM_BYTES = 6.48e6
+# k_gemm_tn revision and tile choice; None until that capture is taken again
+# after a change
+CHOL_BULK_DRAM_BYTES = None
 
 
 def parse():
@@ -53,7 +54,8 @@ def parse():
     ap.add_argument("--mixed-steps", type=int, default=5)
     ap.add_argument("--fp64-large", type=int, default=1, help="time one plain FP64 step of the large workload")
     ap.add_argument("--mixed-workloads", default="mid,large")
-    ap.add_argument("--extra-items", default="ex2,syrk,batch,warm")
+    ap.add_argument("--extra-items", default="err,ex2,syrk,batch,warm")
+    ap.add_argument("--err-large", type=int, default=1, help="also solve the large workload in plain FP64")
     ap.add_argument("--syrk-m", type=int, default=15000)
     ap.add_argument("--extra", action="store_true", help="measure the batched and warm-start rows instead")
     ap.add_argument("--batch-count", type=int, default=512)
@@ -399,6 +401,40 @@ def measure_example2(degrees=((1, 1), (2, 2), (2, 3), (3, 3), (3, 4))):
     return {"L_opt_printed": -0.111, "bounds": out}
 
 
+def measure_mixed_error(bd, synth, name, device, with_oracle):
+    """The mixed-precision solution against the plain FP64 GPU solution (and the
+    FP64 oracle where it finishes): optimal value a^T y, P_h, verdicts."""
+    w = synth.WORKLOADS[name]
+    A = synth.system(w["n"], w["l"], w["s"], 0)
+    res = {}
+    for prec in (0, 1):
+        t0 = time.perf_counter()
+        with bd.Solver(A, w["d_p"], w["d1"], device=device, precision=prec) as s:
+            status, iters, info = s.solve()
+            verdict = s.certify()[0]
+            P = bd.psdp_get_P(s.h)
+        res[prec] = dict(status=status, iters=iters, psi=info["psi"], relgap=info["relgap"], verdict=verdict, P=P,
+                         seconds=time.perf_counter() - t0)
+    out = {"workload": name, "fp64": {k: v for k, v in res[0].items() if k != "P"},
+           "mixed": {k: v for k, v in res[1].items() if k != "P"},
+           "psi_rel_err_vs_fp64_gpu": abs(res[1]["psi"] - res[0]["psi"]) / abs(res[0]["psi"]),
+           "P_max_rel_diff_vs_fp64_gpu": float(np.abs(res[1]["P"] - res[0]["P"]).max() / np.abs(res[0]["P"]).max())}
+    if with_oracle:
+        from oracle import certify, ipm, sdp
+        t0 = time.perf_counter()
+        prob = sdp.Problem(A, w["d_p"], w["d1"])
+        st, state = ipm.solve(prob, ipm.Options())
+        psi_o = float(prob.a @ state.y)
+        Po = prob.P_from_y(state.y)
+        out["oracle"] = {"status": st, "iters": state.it, "psi": psi_o,
+                         "verdict": certify.certify(prob, state.y)["verdict"], "seconds": time.perf_counter() - t0}
+        out["psi_rel_err_vs_oracle"] = {"mixed": abs(res[1]["psi"] - psi_o) / abs(psi_o),
+                                        "fp64": abs(res[0]["psi"] - psi_o) / abs(psi_o)}
+        out["P_max_rel_diff_vs_oracle"] = {"mixed": float(np.abs(res[1]["P"] - Po).max() / np.abs(Po).max()),
+                                           "fp64": float(np.abs(res[0]["P"] - Po).max() / np.abs(Po).max())}
+    return out
+
+
 def run_extra(args):
     """Batched, learned-warm-start and kernel-probe rows (minutes of GPU time;
     not the default line)."""
@@ -410,6 +446,10 @@ def run_extra(args):
     from paper_1411_3769_gb300 import synth
     items = [x for x in args.extra_items.split(",") if x]
     out = {}
+    if "err" in items:
+        out["mixed_error"] = [measure_mixed_error(bd, synth, "mid", 0, True)]
+        if args.err_large:
+            out["mixed_error"].append(measure_mixed_error(bd, synth, "large", 0, False))
     if "ex2" in items:
         out["example2"] = measure_example2()
     if "syrk" in items:
