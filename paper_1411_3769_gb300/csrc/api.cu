@@ -357,7 +357,8 @@ void enqueue_step(psdp_ctx* c, bool mixed) {
     } else {
         enqueue_cholesky(c);
         ProfScope p(c, "dense_solve");
-        launch_solve_fp64(st, c->d_Om, c->K, c->nb_chol, c->d_Linv, c->d_dyh, c->d_trsv_sync, c->d_flag);
+        launch_pair_inverse(st, c->d_Om, c->K, c->d_Linv, c->d_Linv64);
+        launch_solve_fp64(st, c->d_Om, c->K, 64, c->d_Linv64, c->d_dyh, c->d_trsv_sync, c->d_flag);
     }
     // predictor directions
     launch_bt(st, c, c->d_dyh, c->d_T2);
@@ -374,7 +375,7 @@ void enqueue_step(psdp_ctx* c, bool mixed) {
         enqueue_pcg(c, c->d_dyb);
     } else {
         ProfScope p(c, "dense_solve");
-        launch_solve_fp64(st, c->d_Om, c->K, c->nb_chol, c->d_Linv, c->d_dyb, c->d_trsv_sync, c->d_flag);
+        launch_solve_fp64(st, c->d_Om, c->K, 64, c->d_Linv64, c->d_dyb, c->d_trsv_sync, c->d_flag);
     }
     // corrector directions and totals
     launch_bt(st, c, c->d_dyb, c->d_T2);
@@ -425,7 +426,7 @@ void free_ctx(psdp_ctx* c) {
                     c->d_adj, c->d_adj2, c->d_y, c->d_dyh, c->d_dyb, c->d_BX, c->d_part, c->d_tstep,
                     c->d_scal, c->d_info, c->d_flag, c->d_pair_a, c->d_pair_b, c->d_term_off, c->d_term_cnt,
                     c->d_term_desc, c->d_term_w, c->d_uv_idx, c->d_prod_idx, c->d_U, c->d_V, c->d_Aop, c->d_Bop,
-                    c->d_Tbuf, c->d_Om, c->d_Linv, c->d_grid, c->d_svec, c->d_cert, c->d_term_off_t,
+                    c->d_Tbuf, c->d_Om, c->d_Linv, c->d_Linv64, c->d_grid, c->d_svec, c->d_cert, c->d_term_off_t,
                     c->d_opA_hi, c->d_opA_lo, c->d_opB_hi, c->d_opB_lo, c->d_prodA, c->d_prodB, c->d_T32,
                     c->d_Om32, c->d_Linv32, c->d_Pt_hi, c->d_Pt_lo, c->d_z32, c->d_trsv_sync, c->d_Pk_hi, c->d_Pk_lo, c->d_Lt_hi, c->d_Lt_lo, c->d_pcg_x, c->d_pcg_r,
                     c->d_pcg_z, c->d_pcg_p, c->d_pcg_q, c->d_pcg_state, c->d_pcg_done, c->d_M1, c->d_M2};
@@ -550,6 +551,7 @@ psdp_status alloc_fp64(psdp_ctx* c) {
     const int npanel = (c->K + nbc - 1) / nbc;
     TRY(dalloc(&c->d_Om, (size_t)c->K * c->K));
     TRY(dalloc(&c->d_Linv, (size_t)npanel * nbc * nbc));
+    TRY(dalloc(&c->d_Linv64, (size_t)((c->K + 63) / 64) * 64 * 64));
     c->have_fp64 = true;
     return PSDP_OK;
 }

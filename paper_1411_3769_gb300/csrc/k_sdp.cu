@@ -173,32 +173,42 @@ __global__ void k_symneg(int nb, int n, double* N, const int* skip) {
 // ------------------------------------------------------------------ B(W)
 // targets t = h*(Na+1) + lp: lp == Na -> Q_h = sum_{gamma in P} beta sym(W_gamma);
 // else R_{h,lp} = sum_{gamma in Lyap} c[h][gamma][lp] sym(W_{L+gamma}).
-__global__ void k_adj_combine(int n, int L0, int L, int M, int Na, const int32_t* __restrict__ beta,
-                              const int32_t* __restrict__ cH, const double* __restrict__ W, double* out,
-                              const int* skip) {
+constexpr int kAdjE = 64, kAdjG = 4;   // outputs per CTA pass, interleaved partial sums over blocks
+__global__ void __launch_bounds__(kAdjE * kAdjG)
+k_adj_combine(int n, int L0, int L, int M, int Na, const int32_t* __restrict__ beta,
+              const int32_t* __restrict__ cH, const double* __restrict__ W, double* out, const int* skip) {
     if (skip && *skip) return;
+    __shared__ double red[kAdjG][kAdjE];
     const int n2 = n * n;
     const int t = blockIdx.y;
     const int h = t / (Na + 1), lp = t % (Na + 1);
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n2; e += gridDim.x * blockDim.x) {
-        const int i = e / n, j = e % n;
-        const int et = j * n + i;
+    const int tx = threadIdx.x % kAdjE, ty = threadIdx.x / kAdjE;
+    for (int e0 = blockIdx.x * kAdjE; e0 < n2; e0 += gridDim.x * kAdjE) {
+        const int e = e0 + tx;
         double s = 0.0;
-        if (lp == Na) {
-            for (int g = 0; g < L; ++g) {
-                const int b = beta[h * L + g];
-                if (b) s = fma((double)b, 0.5 * (W[(int64_t)g * n2 + e] + W[(int64_t)g * n2 + et]), s);
-            }
-        } else {
-            for (int g = 0; g < M; ++g) {
-                const int c = cH[((int64_t)h * M + g) * Na + lp];
-                if (c) {
-                    const int64_t o = (int64_t)(L + g) * n2;
-                    s = fma((double)c, 0.5 * (W[o + e] + W[o + et]), s);
+        if (e < n2) {
+            const int i = e / n, j = e % n;
+            const int et = j * n + i;
+            // thread row ty sums the blocks g = ty (mod kAdjG) in order
+            if (lp == Na) {
+                for (int g = ty; g < L; g += kAdjG) {
+                    const int b = beta[h * L + g];
+                    if (b) s = fma((double)b, 0.5 * (W[(int64_t)g * n2 + e] + W[(int64_t)g * n2 + et]), s);
+                }
+            } else {
+                for (int g = ty; g < M; g += kAdjG) {
+                    const int c = cH[((int64_t)h * M + g) * Na + lp];
+                    if (c) {
+                        const int64_t o = (int64_t)(L + g) * n2;
+                        s = fma((double)c, 0.5 * (W[o + e] + W[o + et]), s);
+                    }
                 }
             }
         }
-        out[(int64_t)t * n2 + e] = s;
+        red[ty][tx] = s;
+        __syncthreads();
+        if (ty == 0 && e < n2) out[(int64_t)t * n2 + e] = (red[0][tx] + red[1][tx]) + (red[2][tx] + red[3][tx]);
+        __syncthreads();
     }
 }
 
@@ -359,15 +369,25 @@ __global__ void k_partials(int nb, int n, int K, const double* __restrict__ X, c
 
 __global__ void k_finalize(int nb, int n, int K, const double* __restrict__ part, const double* __restrict__ cdiag,
                            double sigma, int iter, double* scal, double* info, int* flag) {
-    if (threadIdx.x != 0) return;
+    // lane t sums blocks g = t (mod 32) in order, then a fixed xor tree: the
+    // same bit pattern on every replay, 32 short chains instead of one long one
     double zx = 0, tx = 0, gg = 0, phi = 0, c2 = 0;
-    for (int g = 0; g < nb; ++g) {
+    for (int g = threadIdx.x; g < nb; g += 32) {
         zx += part[4 * g + 0];
         tx += part[4 * g + 1];
         gg += part[4 * g + 2];
         phi += part[4 * g + 3];
         c2 += cdiag[g] * cdiag[g] * n;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        zx += __shfl_xor_sync(0xffffffffu, zx, o);
+        tx += __shfl_xor_sync(0xffffffffu, tx, o);
+        gg += __shfl_xor_sync(0xffffffffu, gg, o);
+        phi += __shfl_xor_sync(0xffffffffu, phi, o);
+        c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+    }
+    if (threadIdx.x != 0) return;
     const double psi = part[4 * nb + 0];
     const double pres = sqrt(part[4 * nb + 1]) / (1.0 + sqrt((double)K));
     const double dres = sqrt(gg) / (1.0 + sqrt(c2));
@@ -595,8 +615,8 @@ void launch_bt(cudaStream_t st, psdp_ctx* c, const double* v, double* out, const
 
 void launch_b(cudaStream_t st, psdp_ctx* c, const double* W, double* out, double acoef, const int* skip) {
     const int n = c->n, n2 = c->n2;
-    dim3 g1((n2 + kThreads - 1) / kThreads, c->L0 * (c->Na + 1));
-    k_adj_combine<<<g1, kThreads, 0, st>>>(n, c->L0, c->L, c->M, c->Na, c->d_beta, c->d_cH, W, c->d_adj, skip);
+    dim3 g1((n2 + kAdjE - 1) / kAdjE, c->L0 * (c->Na + 1));
+    k_adj_combine<<<g1, kAdjE * kAdjG, 0, st>>>(n, c->L0, c->L, c->M, c->Na, c->d_beta, c->d_cH, W, c->d_adj, skip);
     for (int li = 0; li < c->Na; ++li)
         launch_bgemm(st, n, c->L0, c->d_A + (int64_t)li * n2, nullptr, 0, 0, c->d_adj + (int64_t)li * n2, nullptr,
                      c->Na + 1, 0, c->d_adj2 + (int64_t)li * n2, nullptr, c->Na, 0, 1.0, 0.0, skip);

@@ -415,21 +415,83 @@ void sweeps(cudaStream_t st, const T* A, int K, const T* Linv, const double* bin
     }
 }
 
+// 64 x 64 diagonal-block inverses from pairs of 32 x 32 ones, so the FP64
+// sweeps take half as many dependent steps:
+//   [X_a 0; -X_b L_ba X_a  X_b]  with L_ba(i, k) = L(j0b + i, j0a + k) = A[(j0a + k) K + j0b + i].
+// One CTA per pair; T = L_ba X_a, then the lower-left block -X_b T.
+__global__ void __launch_bounds__(256)
+k_pair_inverse(const double* __restrict__ A, int K, const double* __restrict__ Linv32, double* Linv64) {
+    __shared__ double Xa[32][33], Xb[32][33], Lba[32][33], T[32][33];
+    const int t = blockIdx.x, tid = threadIdx.x;
+    const int np32 = (K + 31) / 32;
+    const int a = 2 * t, b = 2 * t + 1;
+    const int j0a = 32 * a, j0b = 32 * b;
+    const int wb = (b < np32) ? min(32, K - j0b) : 0;
+    const double* Xa_g = Linv32 + (size_t)a * 1024;
+    const double* Xb_g = Linv32 + (size_t)b * 1024;
+    for (int idx = tid; idx < 1024; idx += 256) {
+        const int c = idx >> 5, r = idx & 31;              // column-major element (r, c)
+        Xa[r][c] = Xa_g[idx];
+        Xb[r][c] = (wb > 0) ? Xb_g[idx] : 0.0;
+        Lba[r][c] = (r < wb) ? A[(int64_t)(j0a + c) * K + j0b + r] : 0.0;
+    }
+    __syncthreads();
+    // thread (r, c4): four outputs of a row, k in order
+    const int r = tid >> 3, c4 = (tid & 7) * 4;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k = 0; k < 32; ++k) {
+        const double l = Lba[r][k];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = fma(l, Xa[k][c4 + u], acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) T[r][c4 + u] = acc[u];
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] = 0.0;
+    for (int k = 0; k < 32; ++k) {
+        const double xb = Xb[r][k];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = fma(xb, T[k][c4 + u], acc[u]);
+    }
+    double* X = Linv64 + (size_t)t * 4096;                 // X(r, c) at c*64 + r
+    for (int idx = tid; idx < 1024; idx += 256) {
+        const int c = idx >> 5, rr = idx & 31;
+        X[c * 64 + rr] = Xa[rr][c];                         // upper-left
+        X[(32 + c) * 64 + rr] = 0.0;                        // upper-right
+        X[(32 + c) * 64 + 32 + rr] = Xb[rr][c];             // lower-right
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) X[(c4 + u) * 64 + 32 + r] = -acc[u];   // lower-left
+}
+
 }  // namespace
 
 size_t trsv_sync_words(int K, int nb) { return (size_t)2 + 2 * (size_t)((K + nb - 1) / nb); }
 
 void init_attrs_trsv(int smem_max) {
     set_attrs<double, 32>(smem_max);
+    set_attrs<double, 64>(smem_max);
     set_attrs<float, 64>(smem_max);
     set_attrs<float, 128>(smem_max);
 }
 
-// x <- Omega^{-1} x with the FP64 factor (panel width 32).
+// 64 x 64 diagonal-block inverses (Linv64: [ceil(K/64)][64][64]) from the
+// 32 x 32 ones of the FP64 factor.
+void launch_pair_inverse(cudaStream_t st, const double* A, int K, const double* Linv32, double* Linv64) {
+    k_pair_inverse<<<(K + 63) / 64, 256, 0, st>>>(A, K, Linv32, Linv64);
+}
+
+// x <- Omega^{-1} x with the FP64 factor; Linv holds nb x nb diagonal-block
+// inverses (nb = 32, or 64 from launch_pair_inverse).
 bool launch_solve_fp64(cudaStream_t st, const double* A, int K, int nb, const double* Linv, double* x,
                        unsigned* sync, int* flag) {
-    if (nb != 32) return false;
-    sweeps<double, 32>(st, A, K, Linv, nullptr, x, nullptr, sync, flag, nullptr);
+    if (nb == 32)
+        sweeps<double, 32>(st, A, K, Linv, nullptr, x, nullptr, sync, flag, nullptr);
+    else if (nb == 64)
+        sweeps<double, 64>(st, A, K, Linv, nullptr, x, nullptr, sync, flag, nullptr);
+    else
+        return false;
     return true;
 }
 

@@ -103,6 +103,7 @@ struct psdp_ctx {
     int pairs_per_chunk = 1;
     double *d_Om = nullptr;           // [K][K] row-major, upper triangle authoritative
     double *d_Linv = nullptr;         // diagonal-block inverses of the dense factor [npanel][nb][nb]
+    double *d_Linv64 = nullptr;       // the same paired into 64 x 64 blocks for the sweeps [ceil(K/64)][64][64]
     unsigned *d_trsv_sync = nullptr;  // tickets and ready flags of the triangular sweeps
     int nb_chol = 32;
     double flops_schur = 0, flops_chol = 0, flops_schur_dense = 0;
@@ -257,6 +258,7 @@ void launch_pack_panel32(cudaStream_t st, const float* A, int K, int j0, int nb,
 size_t trsv_sync_words(int K, int nb);
 bool launch_solve_fp64(cudaStream_t st, const double* A, int K, int nb, const double* Linv, double* x,
                        unsigned* sync, int* flag);
+void launch_pair_inverse(cudaStream_t st, const double* A, int K, const double* Linv32, double* Linv64);
 bool launch_precond32(cudaStream_t st, const float* A, int K, int nb, const float* Linv, float* z32,
                            const double* r, double* z, unsigned* sync, int* flag, const int* skip);
 void launch_pcg_init(cudaStream_t st, int K, const double* b, double* x, double* r, double* s, int* done);
