@@ -39,7 +39,7 @@ NOMINAL_FP64_TFLOPS = 1.25
 # launches of one mid-workload step), from one ncu capture of the current
 # k_gemm_tn revision and tile choice; None until that capture is taken again
 # after a change
-CHOL_BULK_DRAM_BYTES = None
+CHOL_BULK_DRAM_BYTES = 6.24e6
 
 
 def parse():

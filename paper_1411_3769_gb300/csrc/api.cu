@@ -216,77 +216,124 @@ void enqueue_schur_mixed(psdp_ctx* c) {
 // panel solve and the next-rows update of the look-ahead (psdp_opts.crit_sms
 // overrides it).
 constexpr int kCritSms = 16;
+// inner panels per outer panel of the FP32 Cholesky
+constexpr int kOuterPanels = 4;
 
-// FP32 Cholesky of Omega32: diagonal blocks factored and inverted in FP32 shared
-// memory, panel TRSM on CUDA cores, trailing update as a persistent 3xTF32
-// tensor-core SYRK (the next panel's rows by the one-tile-per-CTA form), with the same
-// depth-one look-ahead as the FP64 factorisation.  The packed panel (hi, lo) is
-// double-buffered by panel parity: trsm(p+1) writes one buffer while the bulk
-// update p still reads the other (update p-1, the last reader of the buffer
-// trsm(p+1) overwrites, finished before the next-rows update p).
+// FP32 Cholesky of Omega32 in outer panels of nbo = 4 nb32 columns, each
+// factored as nb32-column inner panels:
+//   inner panel (critical stream): diagonal factor and inverse (FP32 shared
+//     memory), panel solve on the tensor cores (3xTF32; the epilogue writes
+//     Omega's panel rows and the TF32 pairs into the outer panel's wide packed
+//     buffer), then the update of the outer panel's remaining columns below
+//     them (whose epilogue packs the next inner panel);
+//   outer trailing update with the whole outer panel, depth nbo: the next outer
+//     panel's rows on the critical stream (packing its first inner panel), the
+//     rest on the main stream by the persistent tcgen05 kernel.
+// Depth-one look-ahead at the outer level: outer panel P+1 is factored while the
+// bulk update of P runs.  The deep outer updates move each trailing element
+// through HBM once per nbo columns instead of once per nb32, and give the tensor
+// cores nbo-deep tiles.  The wide packed buffer is double-buffered by outer
+// parity: P+1's panel solves write one copy while bulk(P) reads the other
+// (bulk(P-1), the last reader of the copy P+1 overwrites, finished before
+// P's next-rows update on the critical stream).
 void enqueue_cholesky_mixed(psdp_ctx* c) {
     cudaStream_t st = c->stream, cs = c->crit;
-    const int K = c->K, nb = c->nb32;
+    const int K = c->K, nb = c->nb32, OB = kOuterPanels * c->nb32;
     float* A = c->d_Om32;
+    const int crit = c->opt.crit_sms > 0 ? c->opt.crit_sms : kCritSms;
+    auto fail = [&]() {
+        // cannot happen for the sizes setup accepts; report a failed factor
+        // rather than leave a silently wrong one (low byte of the flag)
+        cudaMemsetAsync(c->d_flag, FL_CHOL_SCHUR, 1, cs);
+    };
     stream_dep(st, cs, c->ev_fork);
-    for (int j0 = 0, p = 0; j0 < K; j0 += nb, ++p) {
-        const int w = std::min(nb, K - j0);
-        float* Lp = c->d_Linv32 + (size_t)p * nb * nb;
-        {
-            ProfScope q(c, "chol32_potrf_diag", cs);
-            launch_potrf_diag32(cs, A, K, j0, nb, Lp, c->d_Lt_hi, c->d_Lt_lo, c->d_flag);
-        }
-        const int rest = K - j0 - w;
-        if (rest <= 0) break;
-        float* phi = c->d_Pt_hi + (size_t)(p & 1) * K * nb;
-        float* plo = c->d_Pt_lo + (size_t)(p & 1) * K * nb;
-        CUtensorMap pkh, pkl, lth, ltl;
-        bool ok = tc_make_map(&pkh, c->d_Pk_hi, false, w, rest, 1, nb, 0, 128) &&
+    bool done = false;
+    for (int J0 = 0, P = 0; J0 < K && !done; J0 += OB, ++P) {
+        const int wo = std::min(OB, K - J0);
+        // wide packed panel: row r <-> factor row J0 + nb + r, column = index within the outer panel
+        float* wh = c->d_Pt_hi + (size_t)(P & 1) * K * OB;
+        float* wl = c->d_Pt_lo + (size_t)(P & 1) * K * OB;
+        for (int j0 = J0; j0 < J0 + wo; j0 += nb) {
+            const int w = std::min(nb, K - j0);
+            float* Lp = c->d_Linv32 + (size_t)(j0 / nb) * nb * nb;
+            {
+                ProfScope q(c, "chol32_potrf_diag", cs);
+                launch_potrf_diag32(cs, A, K, j0, nb, Lp, c->d_Lt_hi, c->d_Lt_lo, c->d_flag);
+            }
+            const int rest = K - j0 - w;
+            if (rest <= 0) {
+                done = true;
+                break;
+            }
+            const int ri = j0 - J0;                              // this panel's offset in the outer panel
+            float* ah = wh + (size_t)ri * OB + ri;
+            float* al = wl + (size_t)ri * OB + ri;
+            CUtensorMap pkh, pkl, lth, ltl;
+            if (!(tc_make_map(&pkh, c->d_Pk_hi, false, w, rest, 1, nb, 0, 128) &&
                   tc_make_map(&pkl, c->d_Pk_lo, false, w, rest, 1, nb, 0, 128) &&
                   tc_make_map(&lth, c->d_Lt_hi, false, w, w, 1, nb, 0, 128) &&
-                  tc_make_map(&ltl, c->d_Lt_lo, false, w, w, 1, nb, 0, 128);
-        if (ok) {
-            // panel solve P L_jj^{-T} on the tensor cores (3xTF32): written back
-            // to Omega's panel rows and, as TF32 pairs, packed for the update
-            ProfScope q(c, "chol32_trsm", cs);
-            // panel 0 is packed from Omega; every later panel was packed by the
-            // epilogue of the previous next-rows update, which produced it
-            if (p == 0) launch_pack_panel32(cs, A, K, j0, nb, c->d_Pk_hi, c->d_Pk_lo);
-            launch_tc_gemm(cs, false, 3, pkh, lth, &pkl, &ltl, rest, w, 1, 0, nullptr, w, A + (int64_t)j0 * K + j0 + w,
-                           K, 0, 1.f, 0.f, 0, c->d_flag, phi, plo, nb);
+                  tc_make_map(&ltl, c->d_Lt_lo, false, w, w, 1, nb, 0, 128))) {
+                fail();
+                done = true;
+                break;
+            }
+            {
+                // panel solve P L_jj^{-T}; panel 0 is packed from Omega, every later
+                // panel by the epilogue of the update that finished its rows
+                ProfScope q(c, "chol32_trsm", cs);
+                if (j0 == 0) launch_pack_panel32(cs, A, K, j0, nb, c->d_Pk_hi, c->d_Pk_lo);
+                launch_tc_gemm(cs, false, 3, pkh, lth, &pkl, &ltl, rest, w, 1, 0, nullptr, w,
+                               A + (int64_t)j0 * K + j0 + w, K, 0, 1.f, 0.f, 0, c->d_flag, ah, al, OB, 0, w);
+            }
+            const int nrem = J0 + wo - (j0 + w);                 // outer-panel columns right of this panel
+            if (nrem > 0) {
+                CUtensorMap ph, pl, ph2, pl2;
+                if (!(tc_make_map(&ph, ah, false, w, rest, 1, OB, 0, 128) &&
+                      tc_make_map(&pl, al, false, w, rest, 1, OB, 0, 128) &&
+                      tc_make_map(&ph2, ah, false, w, nrem, 1, OB, 0, 128) &&
+                      tc_make_map(&pl2, al, false, w, nrem, 1, OB, 0, 128))) {
+                    fail();
+                    done = true;
+                    break;
+                }
+                ProfScope q(c, "chol32_inner_update", cs);
+                launch_tc_gemm(cs, false, 3, ph, ph2, &pl, &pl2, rest, nrem, 1, 0, nullptr, w,
+                               A + (int64_t)(j0 + w) * K + j0 + w, K, 0, -1.f, 1.f, 1, c->d_flag, c->d_Pk_hi,
+                               c->d_Pk_lo, nb, nb, nb);
+            }
         }
-        const int w2 = std::min(nb, rest);
-        float* T = A + (int64_t)(j0 + w) * K + j0 + w;
-        CUtensorMap hi, lo, hi2, lo2, hib, lob;
-        ok = ok && tc_make_map(&hi, phi, false, w, rest, 1, nb, 0, 128) &&
-                  tc_make_map(&lo, plo, false, w, rest, 1, nb, 0, 128) &&
-                  tc_make_map(&hi2, phi, false, w, w2, 1, nb, 0, 128) &&
-                  tc_make_map(&lo2, plo, false, w, w2, 1, nb, 0, 128);
-        if (rest > w2)
-            ok = ok && tc_make_map(&hib, phi + (size_t)w2 * nb, false, w, rest - w2, 1, nb, 0, 128) &&
-                 tc_make_map(&lob, plo + (size_t)w2 * nb, false, w, rest - w2, 1, nb, 0, 128);
+        if (done) break;
+        const int rest = K - (J0 + wo);
+        if (rest <= 0) break;
+        const int wo2 = std::min(OB, rest);                      // next outer panel
+        float* oh = wh + (size_t)(wo - nb) * OB;                 // rows from factor row J0 + wo
+        float* ol = wl + (size_t)(wo - nb) * OB;
+        CUtensorMap qh, ql, qh2, ql2, qhb, qlb;
+        bool ok = tc_make_map(&qh, oh, false, wo, rest, 1, OB, 0, 128) &&
+                  tc_make_map(&ql, ol, false, wo, rest, 1, OB, 0, 128) &&
+                  tc_make_map(&qh2, oh, false, wo, wo2, 1, OB, 0, 128) &&
+                  tc_make_map(&ql2, ol, false, wo, wo2, 1, OB, 0, 128);
+        if (rest > wo2)
+            ok = ok && tc_make_map(&qhb, oh + (size_t)wo2 * OB, false, wo, rest - wo2, 1, OB, 0, 128) &&
+                 tc_make_map(&qlb, ol + (size_t)wo2 * OB, false, wo, rest - wo2, 1, OB, 0, 128);
         if (!ok) {
-            // cannot happen for the sizes setup accepts; report a failed factor
-            // rather than leave a silently wrong one (low byte of the flag)
-            cudaMemsetAsync(c->d_flag, FL_CHOL_SCHUR, 1, cs);
+            fail();
             break;
         }
-        stream_dep(cs, st, c->ev_join);                     // main: after trsm(p)
-        stream_dep(st, cs, c->ev_fork);                     // crit: after bulk(p-1)
+        float* T = A + (int64_t)(J0 + wo) * K + J0 + wo;
+        stream_dep(cs, st, c->ev_join);                     // main: after outer panel P
+        stream_dep(st, cs, c->ev_fork);                     // crit: after bulk(P-1)
         {
-            // rows [0, w2) of the trailing upper triangle (C[n][m], n < w2, m >= n)
-            // rows [0, w2) of the trailing matrix are panel p+1: the epilogue also
-            // packs them (columns from w2 on) K-major as TF32 pairs for its solve
+            // the next outer panel's rows; the epilogue packs its first inner panel
             ProfScope q(c, "chol32_syrk_next", cs);
-            launch_tc_gemm(cs, false, 3, hi, hi2, &lo, &lo2, rest, w2, 1, 0, nullptr, w, T, K, 0, -1.f, 1.f, 1,
-                           c->d_flag, c->d_Pk_hi, c->d_Pk_lo, nb, w2);
+            launch_tc_gemm(cs, false, 3, qh, qh2, &ql, &ql2, rest, wo2, 1, 0, nullptr, wo, T, K, 0, -1.f, 1.f, 1,
+                           c->d_flag, c->d_Pk_hi, c->d_Pk_lo, nb, nb, nb);
         }
-        if (rest > w2) {
+        if (rest > wo2) {
             // persistent CTAs leave a few SMs to the critical-path kernels
             ProfScope q(c, "chol32_syrk_tc", st);
-            const int crit = c->opt.crit_sms > 0 ? c->opt.crit_sms : kCritSms;
-            launch_tc_gemm_persist(st, 3, hib, hib, &lob, &lob, rest - w2, rest - w2, w, T + (int64_t)w2 * K + w2, K,
-                                   -1.f, 1.f, 1, std::max(1, c->num_sms - crit), c->d_flag);
+            launch_tc_gemm_persist(st, 3, qhb, qhb, &qlb, &qlb, rest - wo2, rest - wo2, wo, T + (int64_t)wo2 * K + wo2,
+                                   K, -1.f, 1.f, 1, std::max(1, c->num_sms - crit), c->d_flag);
         }
     }
     stream_dep(cs, st, c->ev_join);
@@ -574,8 +621,8 @@ psdp_status alloc_mixed(psdp_ctx* c) {
     const int nb = std::max(c->nb32, 128), npanel = (c->K + 63) / 64;
     TRY(dalloc(&c->d_Om32, K * K));
     TRY(dalloc(&c->d_Linv32, (size_t)npanel * 64 * 64 + (size_t)((c->K + 127) / 128) * 128 * 128));
-    TRY(dalloc(&c->d_Pt_hi, 2 * K * nb));   // double-buffered by panel parity
-    TRY(dalloc(&c->d_Pt_lo, 2 * K * nb));
+    TRY(dalloc(&c->d_Pt_hi, 2 * K * kOuterPanels * nb));   // wide packed panel, double-buffered by outer parity
+    TRY(dalloc(&c->d_Pt_lo, 2 * K * kOuterPanels * nb));
     TRY(dalloc(&c->d_Pk_hi, K * nb));
     TRY(dalloc(&c->d_Pk_lo, K * nb));
     TRY(dalloc(&c->d_Lt_hi, nb * nb));

@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(128, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
           const __grid_constant__ CUtensorMap mAlo, const __grid_constant__ CUtensorMap mBlo, int M, int N, int b0,
           const int32_t* __restrict__ kd, int kd_uniform, float* C, int64_t ldc, int64_t c_batch, float alpha,
-          float beta, int tri, int* flag, float* aux_hi, float* aux_lo, int aux_ld, int aux_m0) {
+          float beta, int tri, int* flag, float* aux_hi, float* aux_lo, int aux_ld, int aux_m0, int aux_n1) {
     constexpr int STAGE_BYTES = (SPLIT == 3) ? 2 * (TILE_A + TILE_B) : (TILE_A + TILE_B);
     constexpr int BK = BF16 ? 64 : 32;            // elements per 128-byte row
     constexpr int KSTEP_BYTES = 32;               // bytes of K consumed by one MMA (K = 8 tf32 / 16 bf16)
@@ -246,13 +246,13 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtens
                     if (n < N) Cb[(int64_t)n * ldc + m] = v[j];
                 }
                 if (aux_hi && m >= aux_m0) {
-                    // the same values as (hi, lo) TF32 pairs, row-major [m - aux_m0][n]
-                    // (the K-major operand layout of a following product)
+                    // the same values as (hi, lo) TF32 pairs, row-major [m - aux_m0][n] for
+                    // n < aux_n1 (the K-major operand layout of a following product)
                     float* ph = aux_hi + (int64_t)(m - aux_m0) * aux_ld + n0 + c0;
                     float* pl = aux_lo + (int64_t)(m - aux_m0) * aux_ld + n0 + c0;
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        if (n0 + c0 + j < N) {
+                        if (n0 + c0 + j < N && n0 + c0 + j < aux_n1) {
                             uint32_t h;
                             asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v[j]));
                             ph[j] = __uint_as_float(h);
@@ -517,21 +517,23 @@ bool tc_make_map(CUtensorMap* map, const void* base, bool bf16, int64_t kdim, in
 bool launch_tc_gemm(cudaStream_t st, bool bf16, int split, const CUtensorMap& A, const CUtensorMap& B,
                     const CUtensorMap* Alo, const CUtensorMap* Blo, int M, int N, int batch, int b0,
                     const int32_t* kd, int kd_uniform, float* C, int64_t ldc, int64_t c_batch, float alpha,
-                    float beta, int tri, int* flag, float* aux_hi, float* aux_lo, int aux_ld, int aux_m0) {
+                    float beta, int tri, int* flag, float* aux_hi, float* aux_lo, int aux_ld, int aux_m0,
+                    int aux_n1) {
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
+    if (aux_n1 <= 0) aux_n1 = N;
     if (grid.x == 0 || grid.y == 0 || batch <= 0) return true;
     if (bf16) {
         k_tc_gemm<true, 1, 4><<<grid, 128, smem_bytes<true, 1, 4>(), st>>>(A, B, A, B, M, N, b0, kd, kd_uniform, C,
                                                                          ldc, c_batch, alpha, beta, tri, flag,
-                                                                         aux_hi, aux_lo, aux_ld, aux_m0);
+                                                                         aux_hi, aux_lo, aux_ld, aux_m0, aux_n1);
     } else if (split == 3) {
         k_tc_gemm<false, 3, 3><<<grid, 128, smem_bytes<false, 3, 3>(), st>>>(A, B, *Alo, *Blo, M, N, b0, kd,
                                                                            kd_uniform, C, ldc, c_batch, alpha, beta,
-                                                                           tri, flag, aux_hi, aux_lo, aux_ld, aux_m0);
+                                                                           tri, flag, aux_hi, aux_lo, aux_ld, aux_m0, aux_n1);
     } else {
         k_tc_gemm<false, 1, 4><<<grid, 128, smem_bytes<false, 1, 4>(), st>>>(A, B, A, B, M, N, b0, kd, kd_uniform, C,
                                                                            ldc, c_batch, alpha, beta, tri, flag,
-                                                                           aux_hi, aux_lo, aux_ld, aux_m0);
+                                                                           aux_hi, aux_lo, aux_ld, aux_m0, aux_n1);
     }
     return true;
 }

@@ -238,7 +238,7 @@ bool launch_tc_gemm(cudaStream_t st, bool bf16, int split, const CUtensorMap& A,
                     const CUtensorMap* Alo, const CUtensorMap* Blo, int M, int N, int batch, int b0,
                     const int32_t* kd, int kd_uniform, float* C, int64_t ldc, int64_t c_batch, float alpha,
                     float beta, int tri, int* flag, float* aux_hi = nullptr, float* aux_lo = nullptr,
-                    int aux_ld = 0, int aux_m0 = 0);
+                    int aux_ld = 0, int aux_m0 = 0, int aux_n1 = 0);
 void launch_split_tf32(cudaStream_t st, int64_t n, const float* x, float* hi, float* lo);
 bool launch_tc_gemm_persist(cudaStream_t st, int split, const CUtensorMap& A, const CUtensorMap& B,
                             const CUtensorMap* Alo, const CUtensorMap* Blo, int M, int N, int kd, float* C,

@@ -31,24 +31,33 @@ def draw(count: int, n: int, l: int, s_range, base_seed: int):
     return out
 
 
+CHUNK = 256   # instances per batched solve (bounds the device memory of the contexts)
+
+
 def solve_family(systems, d_p: int, d1: int, precision: int = 1, eps: float = 1e-7):
-    """Solve every system (one batched launch per iteration); returns features,
-    targets, statuses, iteration counts and verdicts."""
-    handles = [bd.psdp_setup(A.shape[-1], A.shape[0], d_p, d1, A, bd.psdp_default_opts(precision=precision, eps=eps))
-               for A, _ in systems]
-    try:
-        status, iters = bd.psdp_solve_batch(handles)
-        feats, targs, verdicts = [], [], []
-        for h, (A, _) in zip(handles, systems):
-            X, Z, y = bd.psdp_get_iterate(h)
-            n = A.shape[-1]
-            xs = np.log(np.maximum(np.einsum("gii->g", X) / n, 1e-30))
-            feats.append(A.reshape(-1))
-            targs.append(np.concatenate([y, xs]))
-            verdicts.append(bd.psdp_certify(h)[0])
-    finally:
-        for h in handles:
-            bd.psdp_destroy(h)
+    """Solve every system (one batched launch per iteration, CHUNK instances at
+    a time); returns features, targets, statuses, iteration counts and verdicts."""
+    feats, targs, verdicts, status, iters = [], [], [], [], []
+    for c0 in range(0, len(systems), CHUNK):
+        part = systems[c0:c0 + CHUNK]
+        handles = []
+        try:
+            for A, _ in part:
+                handles.append(bd.psdp_setup(A.shape[-1], A.shape[0], d_p, d1, A,
+                                             bd.psdp_default_opts(precision=precision, eps=eps)))
+            st, it = bd.psdp_solve_batch(handles)
+            status += list(st)
+            iters += list(it)
+            for h, (A, _) in zip(handles, part):
+                X, Z, y = bd.psdp_get_iterate(h)
+                n = A.shape[-1]
+                xs = np.log(np.maximum(np.einsum("gii->g", X) / n, 1e-30))
+                feats.append(A.reshape(-1))
+                targs.append(np.concatenate([y, xs]))
+                verdicts.append(bd.psdp_certify(h)[0])
+        finally:
+            for h in handles:
+                bd.psdp_destroy(h)
     return (np.array(feats, np.float32), np.array(targs, np.float32), status, np.array(iters),
             np.array(verdicts))
 
@@ -78,24 +87,55 @@ def solve_warm(m, A, d_p: int, d1: int, K: int, nblk: int, precision: int = 1, e
     return status, iters, verdict, fallback
 
 
+def _batch_solve(part, d_p, d1, precision, eps, starts=None):
+    """Solve a chunk in one batch, optionally from predicted starts; returns
+    statuses, iterations and verdicts."""
+    handles = []
+    try:
+        for k, (A, _) in enumerate(part):
+            h = bd.psdp_setup(A.shape[-1], A.shape[0], d_p, d1, A, bd.psdp_default_opts(precision=precision, eps=eps))
+            handles.append(h)
+            if starts is not None:
+                K = bd.psdp_sizes(h)["K"]
+                pred = starts[k]
+                bd.psdp_set_start(h, pred[:K], np.exp(np.clip(pred[K:], -30, 30)), THETA)
+        st, it = bd.psdp_solve_batch(handles)
+        return list(st), list(it), [bd.psdp_certify(h)[0] for h in handles]
+    finally:
+        for h in handles:
+            bd.psdp_destroy(h)
+
+
 def evaluate(m, systems, d_p: int, d1: int, precision: int = 1, eps: float = 1e-7):
-    """Cold vs warm solves of held-out systems: iterations, verdicts, wall time."""
+    """Cold vs warm solves of held-out systems (each side batched, CHUNK at a
+    time): iterations, verdicts, fallbacks, wall time.  A warm solve that ends
+    in neither OK nor EUNBOUNDED is repeated from the cold start (fallback), and
+    its iterations count on the warm side."""
     cold_it, warm_it, agree, fallbacks, t_cold, t_warm = [], [], [], 0, 0.0, 0.0
-    for A, _ in systems:
+    for c0 in range(0, len(systems), CHUNK):
+        part = systems[c0:c0 + CHUNK]
         t0 = time.perf_counter()
-        with bd.Solver(A, d_p, d1, precision=precision, eps=eps) as s:
-            st_c, it_c, _ = s.solve()
-            v_c = s.certify()[0]
-            K, nblk = s.sizes["K"], s.sizes["nblk"]
+        st_c, it_c, v_c = _batch_solve(part, d_p, d1, precision, eps)
         t1 = time.perf_counter()
-        st_w, it_w, v_w, fb = solve_warm(m, A, d_p, d1, K, nblk, precision, eps)
+        feats = np.stack([A.reshape(-1) for A, _ in part]).astype(np.float32)
+        first = bd.psdp_setup(part[0][0].shape[-1], part[0][0].shape[0], d_p, d1, part[0][0])
+        sz = bd.psdp_sizes(first)
+        bd.psdp_destroy(first)
+        preds = bd.psdp_mlp_predict(m, feats, sz["K"] + sz["nblk"]).astype(np.float64)
+        st_w, it_w, v_w = _batch_solve(part, d_p, d1, precision, eps, starts=preds)
+        for k, (A, _) in enumerate(part):
+            if st_w[k] not in ("OK", "EUNBOUNDED"):
+                fallbacks += 1
+                with bd.Solver(A, d_p, d1, precision=precision, eps=eps) as s:
+                    _, it2, _ = s.solve()
+                    v_w[k] = s.certify()[0]
+                    it_w[k] += it2
         t2 = time.perf_counter()
         t_cold += t1 - t0
         t_warm += t2 - t1
-        cold_it.append(it_c)
-        warm_it.append(it_w)
-        agree.append(v_c == v_w)
-        fallbacks += int(fb)
+        cold_it += it_c
+        warm_it += it_w
+        agree += [a == b for a, b in zip(v_c, v_w)]
     return dict(cold_iters=float(np.mean(cold_it)), warm_iters=float(np.mean(warm_it)),
                 iterations_saved=float(np.mean(cold_it) - np.mean(warm_it)), verdicts_agree=bool(all(agree)),
                 fallbacks=fallbacks, cold_s=t_cold, warm_s=t_warm, count=len(systems))
