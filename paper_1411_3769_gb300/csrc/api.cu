@@ -226,9 +226,10 @@ constexpr int kOuterPanels = 4;
 //     Omega's panel rows and the TF32 pairs into the outer panel's wide packed
 //     buffer), then the update of the outer panel's remaining columns below
 //     them (whose epilogue packs the next inner panel);
-//   outer trailing update with the whole outer panel, depth nbo: the next outer
-//     panel's rows on the critical stream (packing its first inner panel), the
-//     rest on the main stream by the persistent tcgen05 kernel.
+//   outer trailing update with the whole outer panel, depth nbo, by the
+//     persistent tcgen05 kernel: the next outer panel's rows on the critical
+//     stream's SMs (then its first inner panel is packed), the rest on the main
+//     stream's.
 // Depth-one look-ahead at the outer level: outer panel P+1 is factored while the
 // bulk update of P runs.  The deep outer updates move each trailing element
 // through HBM once per nbo columns instead of once per nb32, and give the tensor
@@ -278,8 +279,9 @@ void enqueue_cholesky_mixed(psdp_ctx* c) {
                 break;
             }
             {
-                // panel solve P L_jj^{-T}; panel 0 is packed from Omega, every later
-                // panel by the epilogue of the update that finished its rows
+                // panel solve P L_jj^{-T}; an outer panel's first inner panel is packed
+                // from Omega, every later one by the epilogue of the inner update
+                // that finished its rows
                 ProfScope q(c, "chol32_trsm", cs);
                 if (j0 == 0) launch_pack_panel32(cs, A, K, j0, nb, c->d_Pk_hi, c->d_Pk_lo);
                 launch_tc_gemm(cs, false, 3, pkh, lth, &pkl, &ltl, rest, w, 1, 0, nullptr, w,
@@ -324,10 +326,11 @@ void enqueue_cholesky_mixed(psdp_ctx* c) {
         stream_dep(cs, st, c->ev_join);                     // main: after outer panel P
         stream_dep(st, cs, c->ev_fork);                     // crit: after bulk(P-1)
         {
-            // the next outer panel's rows; the epilogue packs its first inner panel
+            // the next outer panel's rows (persistent on the critical SMs), then
+            // the pack of its first inner panel
             ProfScope q(c, "chol32_syrk_next", cs);
-            launch_tc_gemm(cs, false, 3, qh, qh2, &ql, &ql2, rest, wo2, 1, 0, nullptr, wo, T, K, 0, -1.f, 1.f, 1,
-                           c->d_flag, c->d_Pk_hi, c->d_Pk_lo, nb, nb, nb);
+            launch_tc_gemm_persist(cs, 3, qh, qh2, &ql, &ql2, rest, wo2, wo, T, K, -1.f, 1.f, 1, crit, c->d_flag);
+            launch_pack_panel32(cs, A, K, J0 + wo, nb, c->d_Pk_hi, c->d_Pk_lo);
         }
         if (rest > wo2) {
             // persistent CTAs leave a few SMs to the critical-path kernels
