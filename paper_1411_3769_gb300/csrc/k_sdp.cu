@@ -488,6 +488,9 @@ k_schur_gather(int n, int Nt, int K, int p0, const int32_t* __restrict__ pa, con
     const F* Tp = T + (int64_t)pl * n2 * n2;
     F* F1 = sm;                   // F_rs
     F* F2 = sm + n2;              // F_sr (only if r != s)
+    // unrolled so each thread has several loads in flight (the staging is
+    // latency-bound: two CTAs per SM at n = 100)
+#pragma unroll 4
     for (int e = threadIdx.x; e < n2; e += blockDim.x) {
         const int j = e / n, u = e % n;
         F1[e] = Tp[((int64_t)r * n + j) * n2 + s * n + u];

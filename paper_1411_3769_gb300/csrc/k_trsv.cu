@@ -187,7 +187,10 @@ __global__ void __launch_bounds__(TT)
 k_trsv_fwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, const double* __restrict__ bin, T* x,
            unsigned* sync, int* flag, const int* skip) {
     if (skip && *skip) return;
-    constexpr int R = W / V, G = TT / R, RPB = W / G, U = RPB < 8 ? RPB : 8;
+    // U independent running sums per column: FP32 keeps 8 for loads in flight;
+    // FP64 keeps 2, because folding them costs FP64 adds on GB300's narrow pipe
+    constexpr int UMAX = (sizeof(T) == 8) ? 2 : 8;
+    constexpr int R = W / V, G = TT / R, RPB = W / G, U = RPB < UMAX ? RPB : UMAX;
     constexpr int G2 = TT / W;
     static_assert(TT % R == 0 && W % G == 0 && RPB % U == 0, "thread layout");
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -293,7 +296,9 @@ __global__ void __launch_bounds__(TT)
 k_trsv_bwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, T* x, double* xout, unsigned* sync, int* flag,
            const int* skip) {
     if (skip && *skip) return;
-    constexpr int R = (W / V < 32) ? W / V : 32, G = TT / R, RPB = W / G, SEG = W / (R * V);
+    // eight lanes share a row (fewer cross-lane adds: three shuffle levels), each
+    // lane covering SEG segments of V columns per block
+    constexpr int R = (W / V < 8) ? W / V : 8, G = TT / R, RPB = W / G, SEG = W / (R * V);
     constexpr int G2 = TT / W;
     static_assert(32 % R == 0 && W % G == 0 && W % (R * V) == 0, "thread layout");
     extern __shared__ __align__(16) unsigned char smraw[];
