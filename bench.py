@@ -549,9 +549,8 @@ def run_ours(args):
     prof = bd.psdp_profile_get(h)
     bd.psdp_profile_enable(h, False)
     if dist:
-        t = torch.tensor([tot_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+        from paper_1411_3769_gb300 import replicas
+        tot_ms = replicas.max_over_ranks(tot_ms, dist, device="cuda")    # the slowest replica
         dist.barrier()
 
     # ---- end to end through the C ABI with host buffers: setup + solve + certify + P
