@@ -90,7 +90,8 @@ k_potrf_diag32x4(double* A, int K, int j0, int w, int nb, double* Linv, int* fla
     __shared__ int bad;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) bad = 0;
-    for (int idx = tid; idx < 32 * 32; idx += 128) {
+#pragma unroll
+    for (int idx = tid; idx < 32 * 32; idx += 128) {             // all eight loads in flight
         const int c = idx >> 5, r = idx & 31;
         double v = (r == c) ? 1.0 : 0.0;
         if (r < w && c < w && r >= c) v = A[(int64_t)(j0 + c) * K + j0 + r];

@@ -143,7 +143,8 @@ k_potrf_diag32(float* A, int K, int j0, int w, int nb, float* Linv, float* LtHi,
     __shared__ int bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) bad = 0;
-    for (int idx = tid; idx < wp * wp; idx += kPotrfThreads) {
+#pragma unroll 8
+    for (int idx = tid; idx < wp * wp; idx += kPotrfThreads) {   // unrolled: loads in flight
         const int c = idx / wp, r = idx - c * wp;
         float v = 0.f;
         if (r < w && c < w) {
@@ -317,6 +318,7 @@ k_pack_panel32(const float* __restrict__ A, int K, int j0, int w, int nb, float*
     const int rest = K - j0 - w;
     const int i0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 8 rows of 32
+#pragma unroll
     for (int r = ty; r < 32; r += 8) {
         const int m = m0 + r, i = i0 + tx;
         t[r][tx] = (m < w && i < rest) ? A[(int64_t)(j0 + m) * K + j0 + w + i] : 0.f;

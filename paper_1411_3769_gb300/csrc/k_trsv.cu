@@ -204,6 +204,7 @@ k_trsv_fwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, const dou
     __syncthreads();
     const int p = s_ticket, j0 = p * W, w = min(W, K - j0);
     const T* Lp = Linv + (size_t)p * W * W;
+#pragma unroll 8
     for (int i = threadIdx.x; i < W * W; i += TT) Ls[i] = Lp[i];
     // this block's right-hand side, read before any wait
     const T bown = (threadIdx.x < w) ? (T)(bin ? bin[j0 + threadIdx.x] : (double)ldcg(x + j0 + threadIdx.x)) : T(0);
@@ -312,6 +313,7 @@ k_trsv_bwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, T* x, dou
     __syncthreads();
     const int p = npanel - 1 - s_ticket, j0 = p * W, w = min(W, K - j0);
     const T* Lp = Linv + (size_t)p * W * W;
+#pragma unroll 8
     for (int i = threadIdx.x; i < W * W; i += TT) Ls[i] = Lp[i];
     if (threadIdx.x < W) acc[threadIdx.x] = (threadIdx.x < w) ? ldcg(x + j0 + threadIdx.x) : T(0);   // z_p
     const int cl = (threadIdx.x % R) * V, g = threadIdx.x / R;
@@ -434,6 +436,7 @@ k_pair_inverse(const double* __restrict__ A, int K, const double* __restrict__ L
     const int wb = (b < np32) ? min(32, K - j0b) : 0;
     const double* Xa_g = Linv32 + (size_t)a * 1024;
     const double* Xb_g = Linv32 + (size_t)b * 1024;
+#pragma unroll
     for (int idx = tid; idx < 1024; idx += 256) {
         const int c = idx >> 5, r = idx & 31;              // column-major element (r, c)
         Xa[r][c] = Xa_g[idx];
