@@ -348,6 +348,19 @@ def measure_warm(bd, n_train, n_test, device):
     t2 = time.perf_counter()
     try:
         res = ws.evaluate(m, test_sys, d_p, d1)
+        # held-out prediction error (standardised by the training targets) of the
+        # network and of the training-target mean
+        mean = T[ok].mean(axis=0)
+        sd = np.maximum(T[ok].std(axis=0), 1e-6)
+        Fte, Tte, st_te, _, _ = ws.solve_family(test_sys, d_p, d1)
+        okt = np.array([s == "OK" for s in st_te])
+        P = bd.psdp_mlp_predict(m, Fte[okt], T.shape[1])
+        res["heldout_std_mse"] = {"network": float((((P - Tte[okt]) / sd) ** 2).mean()),
+                                  "mean_predictor": float((((mean - Tte[okt]) / sd) ** 2).mean())}
+        # ablation: the same warm-start machinery fed the training-target mean
+        abl = ws.evaluate(None, test_sys, d_p, d1, predict=lambda f, k: np.tile(mean, (f.shape[0], 1)))
+        res["mean_predictor"] = {"warm_iters": abl["warm_iters"], "iterations_saved": abl["iterations_saved"],
+                                 "verdicts_agree": abl["verdicts_agree"], "fallbacks": abl["fallbacks"]}
     finally:
         bd.psdp_mlp_destroy(m)
     res.update(train_instances=int(ok.sum()), train_generate_s=t1 - t0, train_s=t2 - t1, final_train_loss=loss,

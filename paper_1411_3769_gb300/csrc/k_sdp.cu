@@ -4,6 +4,8 @@
 #include <cfloat>
 #include <cmath>
 
+#include <type_traits>
+
 #include "psdp_internal.h"
 
 namespace {
@@ -488,13 +490,28 @@ k_schur_gather(int n, int Nt, int K, int p0, const int32_t* __restrict__ pa, con
     const F* Tp = T + (int64_t)pl * n2 * n2;
     F* F1 = sm;                   // F_rs
     F* F2 = sm + n2;              // F_sr (only if r != s)
-    // unrolled so each thread has several loads in flight (the staging is
-    // latency-bound: two CTAs per SM at n = 100)
+    // 16-byte loads, unrolled, so each thread has several loads in flight (the
+    // staging is latency-bound: two CTAs per SM at n = 100)
+    constexpr int V = 16 / sizeof(F);
+    if (n % V == 0) {
+        using VT = typename std::conditional<sizeof(F) == 4, float4, double2>::type;
+        const int nv = n / V;
 #pragma unroll 4
-    for (int e = threadIdx.x; e < n2; e += blockDim.x) {
-        const int j = e / n, u = e % n;
-        F1[e] = Tp[((int64_t)r * n + j) * n2 + s * n + u];
-        if (r != s) F2[e] = Tp[((int64_t)s * n + j) * n2 + r * n + u];
+        for (int e = threadIdx.x; e < n * nv; e += blockDim.x) {
+            const int j = e / nv, u = (e - j * nv) * V;
+            *reinterpret_cast<VT*>(F1 + j * n + u) =
+                *reinterpret_cast<const VT*>(Tp + ((int64_t)r * n + j) * n2 + s * n + u);
+            if (r != s)
+                *reinterpret_cast<VT*>(F2 + j * n + u) =
+                    *reinterpret_cast<const VT*>(Tp + ((int64_t)s * n + j) * n2 + r * n + u);
+        }
+    } else {
+#pragma unroll 4
+        for (int e = threadIdx.x; e < n2; e += blockDim.x) {
+            const int j = e / n, u = e % n;
+            F1[e] = Tp[((int64_t)r * n + j) * n2 + s * n + u];
+            if (r != s) F2[e] = Tp[((int64_t)s * n + j) * n2 + r * n + u];
+        }
     }
     __syncthreads();
     F* row = Om + (int64_t)(a * Nt + p) * K + (int64_t)b * Nt;

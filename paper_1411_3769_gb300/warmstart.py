@@ -106,11 +106,13 @@ def _batch_solve(part, d_p, d1, precision, eps, starts=None):
             bd.psdp_destroy(h)
 
 
-def evaluate(m, systems, d_p: int, d1: int, precision: int = 1, eps: float = 1e-7):
+def evaluate(m, systems, d_p: int, d1: int, precision: int = 1, eps: float = 1e-7, predict=None):
     """Cold vs warm solves of held-out systems (each side batched, CHUNK at a
     time): iterations, verdicts, fallbacks, wall time.  A warm solve that ends
     in neither OK nor EUNBOUNDED is repeated from the cold start (fallback), and
-    its iterations count on the warm side."""
+    its iterations count on the warm side.  predict(features, n_out) replaces
+    the network's prediction when given (e.g. the training-set mean, the
+    ablation without learning)."""
     cold_it, warm_it, agree, fallbacks, t_cold, t_warm = [], [], [], 0, 0.0, 0.0
     for c0 in range(0, len(systems), CHUNK):
         part = systems[c0:c0 + CHUNK]
@@ -121,7 +123,8 @@ def evaluate(m, systems, d_p: int, d1: int, precision: int = 1, eps: float = 1e-
         first = bd.psdp_setup(part[0][0].shape[-1], part[0][0].shape[0], d_p, d1, part[0][0])
         sz = bd.psdp_sizes(first)
         bd.psdp_destroy(first)
-        preds = bd.psdp_mlp_predict(m, feats, sz["K"] + sz["nblk"]).astype(np.float64)
+        n_out = sz["K"] + sz["nblk"]
+        preds = (predict(feats, n_out) if predict is not None else bd.psdp_mlp_predict(m, feats, n_out)).astype(np.float64)
         st_w, it_w, v_w = _batch_solve(part, d_p, d1, precision, eps, starts=preds)
         for k, (A, _) in enumerate(part):
             if st_w[k] not in ("OK", "EUNBOUNDED"):
