@@ -225,7 +225,8 @@ constexpr int kOuterPanels = 4;
 //     memory), panel solve on the tensor cores (3xTF32; the epilogue writes
 //     Omega's panel rows and the TF32 pairs into the outer panel's wide packed
 //     buffer), then the update of the outer panel's remaining columns below
-//     them (whose epilogue packs the next inner panel);
+//     them (whose epilogue packs the next inner panel); both by the persistent
+//     kernel on the critical stream's SMs;
 //   outer trailing update with the whole outer panel, depth nbo, by the
 //     persistent tcgen05 kernel: the next outer panel's rows on the critical
 //     stream's SMs (then its first inner panel is packed), the rest on the main
@@ -284,8 +285,13 @@ void enqueue_cholesky_mixed(psdp_ctx* c) {
                 // that finished its rows
                 ProfScope q(c, "chol32_trsm", cs);
                 if (j0 == 0) launch_pack_panel32(cs, A, K, j0, nb, c->d_Pk_hi, c->d_Pk_lo);
-                launch_tc_gemm(cs, false, 3, pkh, lth, &pkl, &ltl, rest, w, 1, 0, nullptr, w,
-                               A + (int64_t)j0 * K + j0 + w, K, 0, 1.f, 0.f, 0, c->d_flag, ah, al, OB, 0, w);
+                TcAux aux;
+                aux.hi = ah;
+                aux.lo = al;
+                aux.ld = OB;
+                aux.n1 = w;
+                launch_tc_gemm_persist(cs, 3, pkh, lth, &pkl, &ltl, rest, w, w, A + (int64_t)j0 * K + j0 + w, K, 1.f,
+                                       0.f, 0, crit, c->d_flag, aux);
             }
             const int nrem = J0 + wo - (j0 + w);                 // outer-panel columns right of this panel
             if (nrem > 0) {
@@ -299,9 +305,14 @@ void enqueue_cholesky_mixed(psdp_ctx* c) {
                     break;
                 }
                 ProfScope q(c, "chol32_inner_update", cs);
-                launch_tc_gemm(cs, false, 3, ph, ph2, &pl, &pl2, rest, nrem, 1, 0, nullptr, w,
-                               A + (int64_t)(j0 + w) * K + j0 + w, K, 0, -1.f, 1.f, 1, c->d_flag, c->d_Pk_hi,
-                               c->d_Pk_lo, nb, nb, nb);
+                TcAux aux;                                   // packs the next inner panel
+                aux.hi = c->d_Pk_hi;
+                aux.lo = c->d_Pk_lo;
+                aux.ld = nb;
+                aux.m0 = nb;
+                aux.n1 = nb;
+                launch_tc_gemm_persist(cs, 3, ph, ph2, &pl, &pl2, rest, nrem, w, A + (int64_t)(j0 + w) * K + j0 + w, K,
+                                       -1.f, 1.f, 1, crit, c->d_flag, aux);
             }
         }
         if (done) break;

@@ -143,17 +143,41 @@ k_potrf_diag32(float* A, int K, int j0, int w, int nb, float* Linv, float* LtHi,
     __shared__ int bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) bad = 0;
-#pragma unroll 8
-    for (int idx = tid; idx < wp * wp; idx += kPotrfThreads) {   // unrolled: loads in flight
-        const int c = idx / wp, r = idx - c * wp;
-        float v = 0.f;
-        if (r < w && c < w) {
-            if (r >= c) v = A[(int64_t)(j0 + c) * K + j0 + r];
-        } else if (r == c) {
-            v = 1.f;                       // identity tail
+    if ((K & 3) == 0) {
+        // 16-byte loads of four rows of a column, unrolled: loads in flight
+        const int wp4 = wp / 4;
+#pragma unroll 4
+        for (int idx = tid; idx < wp * wp4; idx += kPotrfThreads) {
+            const int c = idx / wp4, r0 = (idx - c * wp4) * 4;
+            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (c < w && r0 < w) q = *reinterpret_cast<const float4*>(A + (int64_t)(j0 + c) * K + j0 + r0);
+            const float qv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int r = r0 + u;
+                float v = 0.f;
+                if (r < w && c < w) {
+                    if (r >= c) v = qv[u];
+                } else if (r == c) {
+                    v = 1.f;               // identity tail
+                }
+                L[c * ld + r] = v;
+                X[c * ld + r] = 0.f;
+            }
         }
-        L[c * ld + r] = v;
-        X[c * ld + r] = 0.f;
+    } else {
+#pragma unroll 8
+        for (int idx = tid; idx < wp * wp; idx += kPotrfThreads) {   // unrolled: loads in flight
+            const int c = idx / wp, r = idx - c * wp;
+            float v = 0.f;
+            if (r < w && c < w) {
+                if (r >= c) v = A[(int64_t)(j0 + c) * K + j0 + r];
+            } else if (r == c) {
+                v = 1.f;                   // identity tail
+            }
+            L[c * ld + r] = v;
+            X[c * ld + r] = 0.f;
+        }
     }
     __syncthreads();
     for (int kb = 0; kb < nsub; ++kb) {
