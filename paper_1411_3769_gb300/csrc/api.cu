@@ -159,6 +159,8 @@ void enqueue_cholesky(psdp_ctx* c) {
         }
         const int w2 = std::min(nb, rest);
         double* T = A + (int64_t)(j0 + w) * K + j0 + w;     // trailing matrix, leading dimension K
+        // the next-rows update and bulk(p) start together (measured faster than
+        // holding bulk(p) until the next-rows update has finished)
         stream_dep(cs, st, c->ev_join);                     // main: after trsm(p)
         stream_dep(st, cs, c->ev_fork);                     // crit: after bulk(p-1)
         {
@@ -225,8 +227,7 @@ constexpr int kOuterPanels = 4;
 //     memory), panel solve on the tensor cores (3xTF32; the epilogue writes
 //     Omega's panel rows and the TF32 pairs into the outer panel's wide packed
 //     buffer), then the update of the outer panel's remaining columns below
-//     them (whose epilogue packs the next inner panel); both by the persistent
-//     kernel on the critical stream's SMs;
+//     them (whose epilogue packs the next inner panel);
 //   outer trailing update with the whole outer panel, depth nbo, by the
 //     persistent tcgen05 kernel: the next outer panel's rows on the critical
 //     stream's SMs (then its first inner panel is packed), the rest on the main
@@ -285,13 +286,8 @@ void enqueue_cholesky_mixed(psdp_ctx* c) {
                 // that finished its rows
                 ProfScope q(c, "chol32_trsm", cs);
                 if (j0 == 0) launch_pack_panel32(cs, A, K, j0, nb, c->d_Pk_hi, c->d_Pk_lo);
-                TcAux aux;
-                aux.hi = ah;
-                aux.lo = al;
-                aux.ld = OB;
-                aux.n1 = w;
-                launch_tc_gemm_persist(cs, 3, pkh, lth, &pkl, &ltl, rest, w, w, A + (int64_t)j0 * K + j0 + w, K, 1.f,
-                                       0.f, 0, crit, c->d_flag, aux);
+                launch_tc_gemm(cs, false, 3, pkh, lth, &pkl, &ltl, rest, w, 1, 0, nullptr, w,
+                               A + (int64_t)j0 * K + j0 + w, K, 0, 1.f, 0.f, 0, c->d_flag, ah, al, OB, 0, w);
             }
             const int nrem = J0 + wo - (j0 + w);                 // outer-panel columns right of this panel
             if (nrem > 0) {
@@ -305,14 +301,9 @@ void enqueue_cholesky_mixed(psdp_ctx* c) {
                     break;
                 }
                 ProfScope q(c, "chol32_inner_update", cs);
-                TcAux aux;                                   // packs the next inner panel
-                aux.hi = c->d_Pk_hi;
-                aux.lo = c->d_Pk_lo;
-                aux.ld = nb;
-                aux.m0 = nb;
-                aux.n1 = nb;
-                launch_tc_gemm_persist(cs, 3, ph, ph2, &pl, &pl2, rest, nrem, w, A + (int64_t)(j0 + w) * K + j0 + w, K,
-                                       -1.f, 1.f, 1, crit, c->d_flag, aux);
+                launch_tc_gemm(cs, false, 3, ph, ph2, &pl, &pl2, rest, nrem, 1, 0, nullptr, w,
+                               A + (int64_t)(j0 + w) * K + j0 + w, K, 0, -1.f, 1.f, 1, c->d_flag, c->d_Pk_hi,
+                               c->d_Pk_lo, nb, nb, nb);   // packs the next inner panel
             }
         }
         if (done) break;
@@ -484,7 +475,7 @@ void free_ctx(psdp_ctx* c) {
     if (c->graph32) cudaGraphDestroy(c->graph32);
     void* ptrs[] = {c->d_beta, c->d_cH, c->d_W0, c->d_Wa, c->d_A, c->d_H, c->d_cdiag, c->d_X, c->d_Z, c->d_G,
                     c->d_Y, c->d_T1, c->d_T2, c->d_W, c->d_F, c->d_dXh, c->d_dZh, c->d_dX, c->d_dZ, c->d_S,
-                    c->d_adj, c->d_adj2, c->d_y, c->d_dyh, c->d_dyb, c->d_BX, c->d_part, c->d_tstep,
+                    c->d_adj, c->d_adj2, c->d_adj_idx, c->d_y, c->d_dyh, c->d_dyb, c->d_BX, c->d_part, c->d_tstep,
                     c->d_scal, c->d_info, c->d_flag, c->d_pair_a, c->d_pair_b, c->d_term_off, c->d_term_cnt,
                     c->d_term_desc, c->d_term_w, c->d_uv_idx, c->d_prod_idx, c->d_U, c->d_V, c->d_Aop, c->d_Bop,
                     c->d_Tbuf, c->d_Om, c->d_Linv, c->d_Linv64, c->d_grid, c->d_svec, c->d_cert, c->d_term_off_t,
@@ -727,8 +718,20 @@ psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psd
     for (double** p : blocks)
         if ((s = dalloc(p, nbn2))) return fail(s);
     if ((s = dalloc(&c->d_S, (size_t)M * Na * c->n2)) || (s = dalloc(&c->d_adj, (size_t)L0 * (Na + 1) * c->n2)) ||
-        (s = dalloc(&c->d_adj2, (size_t)L0 * Na * c->n2)))
+        (s = dalloc(&c->d_adj2, (size_t)L0 * Na * c->n2)) || (s = dalloc(&c->d_adj_idx, (size_t)3 * L0 * Na)))
         return fail(s);
+    {
+        // product e = g Na + lambda of the adjoint: A_lambda x adj[g][lambda] -> adj2[g][lambda]
+        std::vector<int32_t> ix((size_t)3 * L0 * Na);
+        for (int g = 0; g < L0; ++g)
+            for (int li = 0; li < Na; ++li) {
+                const size_t e = (size_t)g * Na + li;
+                ix[e] = li;
+                ix[(size_t)L0 * Na + e] = g * (Na + 1) + li;
+                ix[(size_t)2 * L0 * Na + e] = (int32_t)e;
+            }
+        cudaMemcpy(c->d_adj_idx, ix.data(), ix.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    }
     double** vecs[] = {&c->d_y, &c->d_dyh, &c->d_dyb, &c->d_BX};
     for (double** p : vecs)
         if ((s = dalloc(p, (size_t)K))) return fail(s);

@@ -46,7 +46,8 @@ constexpr int BG = 32;
 __global__ void __launch_bounds__(kThreads)
 k_bgemm(int n, int count, const double* __restrict__ A, const int32_t* __restrict__ ia, int sa, int ta,
         const double* __restrict__ B, const int32_t* __restrict__ ib, int sb, int tb,
-        double* C, const int32_t* __restrict__ ic, int sc, int tc, double alpha, double beta, const int* skip) {
+        double* C, const int32_t* __restrict__ ic, int sc, int tc, double alpha, double beta, const int* skip,
+        int nsum, int qa, int qb) {
     if (skip && *skip) return;
     __shared__ double As[BG][BG + 1];
     __shared__ double Bs[BG][BG + 1];
@@ -59,31 +60,35 @@ k_bgemm(int n, int count, const double* __restrict__ A, const int32_t* __restric
         const double* Be = B + (size_t)(ib ? ib[e] : e * sb) * n2;
         double* Ce = C + (size_t)(ic ? ic[e] : e * sc) * n2;
         double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
-        for (int k0 = 0; k0 < n; k0 += BG) {
-            for (int idx = threadIdx.x; idx < BG * BG; idx += kThreads) {
-                const int a = idx / BG, b = idx % BG;
-                int i, k;
-                if (!ta) { i = i0 + a; k = k0 + b; } else { k = k0 + a; i = i0 + b; }
-                double v = 0.0;
-                if (i < n && k < n) v = ta ? Ae[(size_t)k * n + i] : Ae[(size_t)i * n + k];
-                As[k - k0][i - i0] = v;
-                int j;
-                if (!tb) { k = k0 + a; j = j0 + b; } else { j = j0 + a; k = k0 + b; }
-                double w = 0.0;
-                if (j < n && k < n) w = tb ? Be[(size_t)j * n + k] : Be[(size_t)k * n + j];
-                Bs[k - k0][j - j0] = w;
-            }
-            __syncthreads();
+        for (int q = 0; q < nsum; ++q) {
+            const double* Aq = Ae + (size_t)q * qa * n2;
+            const double* Bq = Be + (size_t)q * qb * n2;
+            for (int k0 = 0; k0 < n; k0 += BG) {
+                for (int idx = threadIdx.x; idx < BG * BG; idx += kThreads) {
+                    const int a = idx / BG, b = idx % BG;
+                    int i, k;
+                    if (!ta) { i = i0 + a; k = k0 + b; } else { k = k0 + a; i = i0 + b; }
+                    double v = 0.0;
+                    if (i < n && k < n) v = ta ? Aq[(size_t)k * n + i] : Aq[(size_t)i * n + k];
+                    As[k - k0][i - i0] = v;
+                    int j;
+                    if (!tb) { k = k0 + a; j = j0 + b; } else { j = j0 + a; k = k0 + b; }
+                    double w = 0.0;
+                    if (j < n && k < n) w = tb ? Bq[(size_t)j * n + k] : Bq[(size_t)k * n + j];
+                    Bs[k - k0][j - j0] = w;
+                }
+                __syncthreads();
 #pragma unroll 8
-            for (int kk = 0; kk < BG; ++kk) {
-                const double a0 = As[kk][ty], a1 = As[kk][ty + 16];
-                const double b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
-                acc[0][0] = fma(a0, b0, acc[0][0]);
-                acc[0][1] = fma(a0, b1, acc[0][1]);
-                acc[1][0] = fma(a1, b0, acc[1][0]);
-                acc[1][1] = fma(a1, b1, acc[1][1]);
+                for (int kk = 0; kk < BG; ++kk) {
+                    const double a0 = As[kk][ty], a1 = As[kk][ty + 16];
+                    const double b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+                    acc[0][0] = fma(a0, b0, acc[0][0]);
+                    acc[0][1] = fma(a0, b1, acc[0][1]);
+                    acc[1][0] = fma(a1, b0, acc[1][0]);
+                    acc[1][1] = fma(a1, b1, acc[1][1]);
+                }
+                __syncthreads();
             }
-            __syncthreads();
         }
 #pragma unroll
         for (int r = 0; r < 2; ++r)
@@ -107,7 +112,7 @@ __global__ void __launch_bounds__(1024)
 k_bgemm_small(int n, int count, const double* __restrict__ A, const int32_t* __restrict__ ia, int sa, int ta,
               const double* __restrict__ B, const int32_t* __restrict__ ib, int sb, int tb,
               double* C, const int32_t* __restrict__ ic, int sc, int tc, double alpha, double beta,
-              const int* skip) {
+              const int* skip, int nsum, int qa, int qb) {
     if (skip && *skip) return;
     __shared__ double As[32][33];   // As[i][k] = op(A)(i, k)
     __shared__ double Bs[32][33];   // Bs[k][j] = op(B)(k, j)
@@ -117,16 +122,22 @@ k_bgemm_small(int n, int count, const double* __restrict__ A, const int32_t* __r
         const double* Ae = A + (size_t)(ia ? ia[e] : e * sa) * n2;
         const double* Be = B + (size_t)(ib ? ib[e] : e * sb) * n2;
         double* Ce = C + (size_t)(ic ? ic[e] : e * sc) * n2;
-        for (int idx = t; idx < n2; idx += blockDim.x) {
-            const int r = idx / n, q = idx - (idx / n) * n;   // element (r, q) of the stored matrix
-            const double a = Ae[idx], b = Be[idx];
-            if (ta) As[q][r] = a; else As[r][q] = a;
-            if (tb) Bs[q][r] = b; else Bs[r][q] = b;
+        double acc = 0.0;
+        for (int s = 0; s < nsum; ++s) {
+            const double* Aq = Ae + (size_t)s * qa * n2;
+            const double* Bq = Be + (size_t)s * qb * n2;
+            for (int idx = t; idx < n2; idx += blockDim.x) {
+                const int r = idx / n, q = idx - (idx / n) * n;   // element (r, q) of the stored matrix
+                const double a = Aq[idx], b = Bq[idx];
+                if (ta) As[q][r] = a; else As[r][q] = a;
+                if (tb) Bs[q][r] = b; else Bs[r][q] = b;
+            }
+            __syncthreads();
+            if (t < n2)
+                for (int k = 0; k < n; ++k) acc = fma(As[i][k], Bs[k][j], acc);
+            __syncthreads();
         }
-        __syncthreads();
         if (t < n2) {
-            double acc = 0.0;
-            for (int k = 0; k < n; ++k) acc = fma(As[i][k], Bs[k][j], acc);
             const size_t o = tc ? (size_t)j * n + i : (size_t)i * n + j;
             double val = alpha * acc;
             if (beta != 0.0) val += beta * Ce[o];
@@ -508,17 +519,18 @@ size_t smem_two_mats(int n) { return (size_t)2 * n * (n + 1) * sizeof(double); }
 // ===================================================================== launchers
 void launch_bgemm(cudaStream_t st, int n, int count, const double* A, const int32_t* ia, int sa, int ta,
                   const double* B, const int32_t* ib, int sb, int tb, double* C, const int32_t* ic, int sc,
-                  int tc, double alpha, double beta, const int* skip) {
+                  int tc, double alpha, double beta, const int* skip, int nsum, int qa, int qb) {
     if (count <= 0) return;
     if (n <= 32) {
         const int threads = (n * n + 31) / 32 * 32;
         k_bgemm_small<<<count < 65535 ? count : 65535, threads, 0, st>>>(n, count, A, ia, sa, ta, B, ib, sb, tb, C, ic,
-                                                                         sc, tc, alpha, beta, skip);
+                                                                         sc, tc, alpha, beta, skip, nsum, qa, qb);
         return;
     }
     const int tiles = (n + BG - 1) / BG;
     dim3 grid(tiles * tiles, count < 65535 ? count : 65535);
-    k_bgemm<<<grid, kThreads, 0, st>>>(n, count, A, ia, sa, ta, B, ib, sb, tb, C, ic, sc, tc, alpha, beta, skip);
+    k_bgemm<<<grid, kThreads, 0, st>>>(n, count, A, ia, sa, ta, B, ib, sb, tb, C, ic, sc, tc, alpha, beta, skip, nsum,
+                                       qa, qb);
 }
 
 void launch_gemm_tn(cudaStream_t st, int m, int ncol, int batch, const double* A, int lda, const int32_t* a_off,

@@ -626,9 +626,8 @@ void launch_bt(cudaStream_t st, psdp_ctx* c, const double* v, double* out, const
                                           skip);
     // N_gamma = sum_lambda S_{gamma,lambda} A_lambda  (written into the Lyapunov output blocks)
     double* outL = out + (int64_t)c->L * n2;
-    for (int li = 0; li < c->Na; ++li)
-        launch_bgemm(st, n, c->M, c->d_S + (int64_t)li * n2, nullptr, c->Na, 0, c->d_A + (int64_t)li * n2, nullptr, 0,
-                     0, outL, nullptr, 1, 0, 1.0, li ? 1.0 : 0.0, skip);
+    launch_bgemm(st, n, c->M, c->d_S, nullptr, c->Na, 0, c->d_A, nullptr, 0, 0, outL, nullptr, 1, 0, 1.0, 0.0, skip,
+                 c->Na, 1, 1);
     dim3 g2((n2 + kThreads - 1) / kThreads, c->M);
     k_symneg<<<g2, kThreads, 0, st>>>(c->M, n, outL, skip);
 }
@@ -637,9 +636,9 @@ void launch_b(cudaStream_t st, psdp_ctx* c, const double* W, double* out, double
     const int n = c->n, n2 = c->n2;
     dim3 g1((n2 + kAdjE - 1) / kAdjE, c->L0 * (c->Na + 1));
     k_adj_combine<<<g1, kAdjE * kAdjG, 0, st>>>(n, c->L0, c->L, c->M, c->Na, c->d_beta, c->d_cH, W, c->d_adj, skip);
-    for (int li = 0; li < c->Na; ++li)
-        launch_bgemm(st, n, c->L0, c->d_A + (int64_t)li * n2, nullptr, 0, 0, c->d_adj + (int64_t)li * n2, nullptr,
-                     c->Na + 1, 0, c->d_adj2 + (int64_t)li * n2, nullptr, c->Na, 0, 1.0, 0.0, skip);
+    const int32_t* ix = c->d_adj_idx;
+    const int np = c->L0 * c->Na;
+    launch_bgemm(st, n, np, c->d_A, ix, 0, 0, c->d_adj, ix + np, 0, 0, c->d_adj2, ix + 2 * np, 0, 0, 1.0, 0.0, skip);
     k_adj_finish<<<grid_for((int64_t)c->L0 * c->Nt), kThreads, 0, st>>>(n, c->Nt, c->L0, c->Na, c->d_adj, c->d_adj2,
                                                                         c->d_svec, acoef, out, skip);
 }

@@ -80,6 +80,7 @@ struct psdp_ctx {
     double *d_S = nullptr;      // [M][Na][n][n]   B^T scratch
     double *d_adj = nullptr;    // [L0][Na+1][n][n] adjoint scratch
     double *d_adj2 = nullptr;   // [L0][Na][n][n]
+    int32_t *d_adj_idx = nullptr;   // operand indices of the adjoint's products [3][L0*Na]
     double *d_y = nullptr, *d_dyh = nullptr, *d_dyb = nullptr, *d_BX = nullptr;
     double *d_part = nullptr;   // per-block partial sums [2*nblk][4]
     double *d_tstep = nullptr;  // per-block max steps [2*nblk]
@@ -162,13 +163,14 @@ void launch_tables(cudaStream_t st, int l, int d_p, int d1, int d2, int d_a, int
 // H[h][g] = sum_lambda cH[h][g][lambda] A[lambda]
 void launch_hmat(cudaStream_t st, int L0, int M, int Na, int n, const int32_t* cH, const double* A, double* H);
 
-// batched n x n GEMM: C_e = alpha op(A_e) op(B_e) + beta C_e (or its transpose if tc);
-// matrix index of operand X for element e is (ix ? ix[e] : e * sx).
+// batched n x n GEMM: C_e = alpha sum_{q < nsum} op(A_{e,q}) op(B_{e,q}) + beta C_e
+// (or its transpose if tc); matrix index of operand X for element e and term q
+// is (ix ? ix[e] : e * sx) + q * qx.
 void launch_bgemm(cudaStream_t st, int n, int count,
                   const double* A, const int32_t* ia, int sa, int ta,
                   const double* B, const int32_t* ib, int sb, int tb,
                   double* C, const int32_t* ic, int sc, int tc, double alpha, double beta,
-                  const int* skip = nullptr);
+                  const int* skip = nullptr, int nsum = 1, int qa = 0, int qb = 0);
 
 // batched TN GEMM: C_b[r][c] = alpha * sum_{k<kd_b} A_b[k*lda + r] * B_b[k*ldb + c] + beta * C_b[r*ldc + c]
 // for r < m, c < ncol; per-batch offsets (elements) and contraction lengths from device arrays
