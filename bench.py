@@ -37,9 +37,10 @@ NOMINAL_BF16_TFLOPS = 2250.0
 NOMINAL_FP64_TFLOPS = 1.25
 # DRAM read + write bytes per bulk trailing-update launch (mean over the 64
 # launches of one mid-workload step), from one ncu capture of the current
-# k_gemm_tn revision and tile choice; None until that capture is taken again
-# after a change
-CHOL_BULK_DRAM_BYTES = 6.24e6
+# k_syrk_tri_persist revision; None until that capture is taken again after a
+# change
+CHOL_BULK_DRAM_BYTES = 6.14e6
+KERNEL_OF = {"schur_gemm": "k_gemm_tn", "chol_syrk_gemm": "k_syrk_tri_persist"}
 
 
 def parse():
@@ -606,7 +607,7 @@ def run_ours(args):
     kern["_profiled_ms_per_step"] = prof_ms / args.steps
     dom = max(("schur_gemm", "chol_syrk_gemm"), key=lambda k: kern.get(k, {}).get("share_of_step", 0))
     ach = kern.get(dom, {}).get("tflops")
-    roof = {"kernel": "k_gemm_tn (" + dom + ")", "bound": "fp64", "achieved": ach,
+    roof = {"kernel": KERNEL_OF[dom] + " (" + dom + ")", "bound": "fp64", "achieved": ach,
             "peak": fp64_peak, "unit": "TFLOP/s", "frac": (ach / fp64_peak) if ach else None,
             "traffic": CHOL_BULK_DRAM_BYTES if dom == "chol_syrk_gemm" else None,
             "peak_source": f"{pk_kind} bf16 {pk['bf16_tflops']} TFLOP/s x nominal FP64/BF16 ratio 1.25/2250"}

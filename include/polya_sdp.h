@@ -69,8 +69,9 @@ typedef struct {
     int    use_graph;   /* capture one Newton step in a CUDA graph and replay it; default 1 */
     void*  stream;      /* cudaStream_t to run on; NULL: the context creates its own */
     int    device;      /* CUDA device ordinal; default 0 */
-    int    crit_sms;    /* mixed form: SMs the persistent trailing update leaves to the
-                           Cholesky critical path (panel factor and solve); 0 = 16 */
+    int    crit_sms;    /* SMs the persistent Cholesky trailing update leaves to the
+                           critical path (panel factor, panel solve, next-rows
+                           update); 0 = the default (8 in FP64, 16 in the mixed form) */
 } psdp_opts;
 
 /* Number of doubles psdp_step / psdp_solve write to their info array. */

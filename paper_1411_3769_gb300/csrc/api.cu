@@ -136,10 +136,22 @@ void stream_dep(cudaStream_t from, cudaStream_t to, cudaEvent_t e) {
 //   crit: potrf(p), trsm(p) | wait bulk(p-1) | next-rows update(p)
 //   main: wait trsm(p) | bulk update(p) of the rows below the next panel
 // Both updates read only panel p; they write disjoint rows.
+// SMs the persistent FP64 trailing update leaves to the look-ahead chain
+// (psdp_opts.crit_sms overrides it); measured on the mid-size workload:
+// 6.97 ms per step with 8 or 12, 7.02 with 16, 7.18 with 24.
+constexpr int kCritSms64 = 8;
+// trailing updates of more than this many waves of 32 x 32 tiles per SM take
+// the one-shot kernel (large workload: 97 % FP64 pipe on 152 SMs against 92 %
+// for the persistent one on 144)
+constexpr int kOneShotWaves = 64;
+
 void enqueue_cholesky(psdp_ctx* c) {
     cudaStream_t st = c->stream, cs = c->crit;
     const int K = c->K, nb = c->nb_chol;
     double* A = c->d_Om;
+    const int npanel = (K + nb - 1) / nb;
+    const int crit = c->opt.crit_sms > 0 ? c->opt.crit_sms : kCritSms64;
+    cudaMemsetAsync(c->d_chol_ctr, 0, (size_t)npanel * sizeof(int), st);
     stream_dep(st, cs, c->ev_fork);
     for (int j0 = 0, p = 0; j0 < K; j0 += nb, ++p) {
         const int w = std::min(nb, K - j0);
@@ -170,10 +182,22 @@ void enqueue_cholesky(psdp_ctx* c) {
                            1.0, 1);
         }
         if (rest > w2) {
-            // rows [w2, rest) of the trailing upper triangle -= P[:, w2:]^T P[:, w2:]
+            // rows [w2, rest) of the trailing upper triangle -= P[:, w2:]^T P[:, w2:].
+            // Persistent on all but the SMs left to the look-ahead chain while the
+            // chain can be the longer path; a trailing matrix of many waves of
+            // tiles (the large workloads' early panels) takes the one-shot tiled
+            // kernel on every SM, where the chain hides under the update anyway.
             ProfScope q(c, "chol_syrk_gemm", st);
-            launch_gemm_tn(st, rest - w2, rest - w2, 1, panel + w2, K, nullptr, 0, panel + w2, K, nullptr, 0,
-                           nullptr, w, T + (int64_t)w2 * K + w2, K, 0, -1.0, 1.0, 1);
+            const int m = rest - w2, nt = (m + 31) / 32;
+            const int64_t ntiles = (int64_t)nt * (nt + 1) / 2;
+            double* C = T + (int64_t)w2 * K + w2;
+            if (ntiles > (int64_t)kOneShotWaves * c->num_sms) {
+                launch_gemm_tn(st, m, m, 1, panel + w2, K, nullptr, 0, panel + w2, K, nullptr, 0, nullptr, w, C, K, 0,
+                               -1.0, 1.0, 1);
+            } else {
+                const int grid = (int)std::min<int64_t>(std::max(1, c->num_sms - crit), (ntiles + 1) / 2);
+                launch_syrk_tri_persist(st, m, w, panel + w2, K, C, K, c->d_chol_ctr + p, grid);
+            }
         }
     }
     stream_dep(cs, st, c->ev_join);
@@ -478,7 +502,7 @@ void free_ctx(psdp_ctx* c) {
                     c->d_adj, c->d_adj2, c->d_adj_idx, c->d_y, c->d_dyh, c->d_dyb, c->d_BX, c->d_part, c->d_tstep,
                     c->d_scal, c->d_info, c->d_flag, c->d_pair_a, c->d_pair_b, c->d_term_off, c->d_term_cnt,
                     c->d_term_desc, c->d_term_w, c->d_uv_idx, c->d_prod_idx, c->d_U, c->d_V, c->d_Aop, c->d_Bop,
-                    c->d_Tbuf, c->d_Om, c->d_Linv, c->d_Linv64, c->d_grid, c->d_svec, c->d_cert, c->d_term_off_t,
+                    c->d_Tbuf, c->d_Om, c->d_Linv, c->d_Linv64, c->d_chol_ctr, c->d_grid, c->d_svec, c->d_cert, c->d_term_off_t,
                     c->d_opA_hi, c->d_opA_lo, c->d_opB_hi, c->d_opB_lo, c->d_prodA, c->d_prodB, c->d_T32,
                     c->d_Om32, c->d_Linv32, c->d_Pt_hi, c->d_Pt_lo, c->d_z32, c->d_trsv_sync, c->d_Pk_hi, c->d_Pk_lo, c->d_Lt_hi, c->d_Lt_lo, c->d_pcg_x, c->d_pcg_r,
                     c->d_pcg_z, c->d_pcg_p, c->d_pcg_q, c->d_pcg_state, c->d_pcg_done, c->d_M1, c->d_M2};
@@ -604,6 +628,7 @@ psdp_status alloc_fp64(psdp_ctx* c) {
     TRY(dalloc(&c->d_Om, (size_t)c->K * c->K));
     TRY(dalloc(&c->d_Linv, (size_t)npanel * nbc * nbc));
     TRY(dalloc(&c->d_Linv64, (size_t)((c->K + 63) / 64) * 64 * 64));
+    TRY(dalloc(&c->d_chol_ctr, (size_t)npanel));
     c->have_fp64 = true;
     return PSDP_OK;
 }

@@ -71,22 +71,24 @@ k_potrf_diag(double* A, int K, int j0, int w, int nb, double* Linv, int* flag) {
 }
 
 // Diagonal block of at most 32 columns, four warps, factor and inverse in one
-// sweep.  GB300's FP64 pipe is narrow, so the critical path is counted in
-// dependent FP64 operations.  Column j needs 1/L_jj = rsqrt(piv_j) for the
-// column scale and for row j of L^{-1}; then one rank-1 step updates the
-// trailing lower triangle of L and, beside it, the running sums of L^{-1}:
-// S(i, c) = -sum_{k<j} L(i, k) X(k, c), X(j, c) = S(j, c) / L_jj.  Row i of the
-// combined update touches positions q <= i: S(i, q) for q <= j, L(i, q) for
-// q > j (a lane per q).  Warp 0 updates only row j+1 and computes the next
-// pivot's rsqrt at once, while warps 1-3 update the other rows, so the rsqrt
-// overlaps the rank-1 step.  The block is padded to 32 with an identity tail.
+// sweep with one CTA barrier per column.  On GB300 a dependent FP64 operation
+// costs ~65 cycles and rsqrt ~375, and one warp issues DFMAs slowly, so the
+// sweep is built around the chain pivot_j -> rsqrt -> pivot_{j+1}.  The
+// columns stay unscaled during the sweep (A(i, j) instead of
+// L(i, j) = A(i, j) r_j, r_j = 1/L_jj) and every rank-1 step uses r_j^2:
+//   A(i, q) -= A(i, j) (A(q, j) r_j^2)          (trailing lower triangle, q > j)
+//   S(i, q) -= A(i, j) (S(j, q) r_j^2)          (running sums of L^{-1}, q <= j)
+// with S the identity at the start, so that L^{-1}(i, q) = S(i, q) r_i and
+// L(i, j) = A(i, j) r_j are formed once at the end.  Warp 0 updates only row
+// j+1, whose diagonal entry is the next pivot, and its lane j+1 takes the
+// rsqrt at once while warps 1-3 update the other rows two at a time (lane =
+// column q).  The block is padded to 32 with an identity tail.
 __global__ void __launch_bounds__(128)
 k_potrf_diag32x4(double* A, int K, int j0, int w, int nb, double* Linv, int* flag) {
     constexpr int LD = 33;
-    __shared__ double L[32 * LD];   // column-major: L(r, c) = L[c*LD + r]
-    __shared__ double X[32 * LD];   // S, then L^{-1}, column-major
-    __shared__ double ldiag[32];
-    __shared__ double s_piv, s_ri;
+    __shared__ double L[32 * LD];   // A, column-major: A(r, c) = L[c*LD + r]
+    __shared__ double X[32 * LD];   // S, column-major
+    __shared__ double piv[32], rinv[32], rinv2[32];
     __shared__ int bad;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) bad = 0;
@@ -96,64 +98,61 @@ k_potrf_diag32x4(double* A, int K, int j0, int w, int nb, double* Linv, int* fla
         double v = (r == c) ? 1.0 : 0.0;
         if (r < w && c < w && r >= c) v = A[(int64_t)(j0 + c) * K + j0 + r];
         L[c * LD + r] = v;
-        X[c * LD + r] = 0.0;
+        X[c * LD + r] = (r == c) ? 1.0 : 0.0;
     }
-    __syncthreads();
-    if (tid == 0) {
-        double piv = L[0];
-        if (!(piv > 0.0) || !isfinite(piv)) {
+    // a pivot that is not positive and finite is flagged and replaced by 1
+    auto take_pivot = [&](int j, double p) {
+        const long long bits = __double_as_longlong(p);
+        if (!(bits > 0 && bits < 0x7ff0000000000000LL)) {
             bad = 1;
-            piv = 1.0;
+            p = 1.0;
         }
-        s_piv = piv;
-        s_ri = rsqrt(piv);
-    }
+        const double r = rsqrt(p);
+        piv[j] = p;
+        rinv[j] = r;
+        rinv2[j] = r * r;
+    };
+    __syncthreads();
+    if (tid == 0) take_pivot(0, L[0]);
     __syncthreads();
     const int q = lane;
     for (int j = 0; j < 32; ++j) {
-        const double ri = s_ri, piv = s_piv;
-        if (wid == 0) {
-            if (lane > j) L[j * LD + lane] *= ri;                  // column j of L
-        } else if (wid == 1) {
-            if (lane < j) X[lane * LD + j] *= ri;                  // row j of L^{-1}
-            else if (lane == j) X[j * LD + j] = ri;
-        } else if (tid == 64) {
-            ldiag[j] = piv * ri;
-        }
-        __syncthreads();
-        const bool sx = q <= j;
-        double* U = sx ? X : L;                                    // U(i, q) = U[q*LD + i]
-        const double vq = sx ? X[q * LD + j] : L[j * LD + q];      // X(j, q) or L(q, j)
+        const double r2 = rinv2[j];
+        const double vq = (q <= j ? X[q * LD + j] : L[j * LD + q]) * r2;   // S(j, q) or A(q, j), times r_j^2
+        double* U = q <= j ? X : L;                                        // U(i, q) = U[q*LD + i]
         if (wid == 0) {
             const int i = j + 1;
-            if (i < 32 && (sx || q <= i)) {
+            if (i < 32 && q <= i) {
                 const double u = fma(-L[j * LD + i], vq, U[q * LD + i]);
                 U[q * LD + i] = u;
-                if (q == i) {                                      // next pivot, its rsqrt now
-                    double p = u;
-                    if (!(p > 0.0) || !isfinite(p)) {
-                        bad = 1;
-                        p = 1.0;
-                    }
-                    s_piv = p;
-                    s_ri = rsqrt(p);
-                }
+                if (q == i) take_pivot(i, u);                               // next pivot, its rsqrt now
             }
         } else {
-#pragma unroll 4
-            for (int i = j + 1 + wid; i < 32; i += 3) {
-                if (sx || q <= i) U[q * LD + i] = fma(-L[j * LD + i], vq, U[q * LD + i]);
+            // rows j+1+wid, j+4+wid, ... two per round: both loads, both DFMAs,
+            // both stores, so the second row's DFMA does not wait for the first
+            for (int i = j + 1 + wid; i < 32; i += 6) {
+                const int ib = i + 3;
+                const double la = L[j * LD + i], ua = q <= i ? U[q * LD + i] : 0.0;
+                double lb = 0.0, ub = 0.0;
+                if (ib < 32) {
+                    lb = L[j * LD + ib];
+                    ub = q <= ib ? U[q * LD + ib] : 0.0;
+                }
+                const double ra = fma(-la, vq, ua), rb = fma(-lb, vq, ub);
+                if (q <= i) U[q * LD + i] = ra;
+                if (ib < 32 && q <= ib) U[q * LD + ib] = rb;
             }
         }
         __syncthreads();
     }
     for (int idx = tid; idx < 32 * 32; idx += 128) {
         const int c = idx >> 5, r = idx & 31;
-        if (r < w && c < w && r >= c) A[(int64_t)(j0 + c) * K + j0 + r] = (r == c) ? ldiag[c] : L[c * LD + r];
+        if (r < w && c < w && r >= c)
+            A[(int64_t)(j0 + c) * K + j0 + r] = (r == c ? piv[c] : L[c * LD + r]) * rinv[c];
     }
     for (int idx = tid; idx < nb * nb; idx += 128) {
         const int c = idx / nb, r = idx % nb;
-        Linv[idx] = (r < w && c < w) ? X[c * LD + r] : 0.0;
+        Linv[idx] = (r < w && c < w) ? X[c * LD + r] * rinv[r] : 0.0;
     }
     if (tid == 0 && bad) atomicOr(flag, (int)FL_CHOL_SCHUR);
 }

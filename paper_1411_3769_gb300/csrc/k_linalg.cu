@@ -243,6 +243,103 @@ k_gemm_tn(int m, int ncol, const double* __restrict__ A, int lda, const int32_t*
         }
 }
 
+// ------------------------------------------- persistent Cholesky trailing update
+// C[r][c] -= sum_k P[k*lda + r] P[k*lda + c] on the c >= r tiles of an m x m
+// trailing matrix (depth kdep), 32 x 32 tiles claimed from a global counter.
+// A CTA is two independent 256-thread groups (own tile, own named barrier), so
+// one group's loads overlap the other's DFMAs, and it reserves nearly all of
+// its SM's shared memory: no critical-path kernel (panel factor, panel solve,
+// next-rows update) is placed beside it, so those run at full FP64 rate on the
+// SMs the grid leaves free.
+constexpr int kPT = 32;
+constexpr int kPersistThreads = 512;
+constexpr size_t kPersistSmem = 216 * 1024;
+bool g_persist_ok = false;
+
+__device__ __forceinline__ void group_bar(int id) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(256) : "memory");
+}
+
+__global__ void __launch_bounds__(kPersistThreads, 1)
+k_syrk_tri_persist(int m, int kdep, const double* __restrict__ P, int lda, double* C, int ldc, int* ctr) {
+    constexpr int T = kPT, MI = T / 16, QA = TK * T / 256;
+    extern __shared__ double dsm[];
+    __shared__ int s_tile[2];
+    const int g = threadIdx.x >> 8, t = threadIdx.x & 255;
+    double* As = dsm + (size_t)g * 4 * TK * T;   // [2][TK][T]
+    double* Bs = As + 2 * TK * T;                // [2][TK][T]
+    const int tx = t & 15, ty = t >> 4;
+    const int nT = (m + T - 1) / T, ntiles = nT * (nT + 1) / 2;
+    for (;;) {
+        if (t == 0) s_tile[g] = atomicAdd(ctr, 1);
+        group_bar(1 + g);
+        const int tile = s_tile[g];
+        if (tile >= ntiles) break;
+        int tr = 0, rem = tile;
+        while (rem >= nT - tr) {
+            rem -= nT - tr;
+            ++tr;
+        }
+        const int r0 = tr * T, c0 = (tr + rem) * T;
+        double acc[MI][MI], old[MI][MI];
+#pragma unroll
+        for (int i = 0; i < MI; ++i)
+#pragma unroll
+            for (int j = 0; j < MI; ++j) {
+                acc[i][j] = 0.0;
+                const int r = r0 + ty + 16 * i, cc = c0 + tx + 16 * j;
+                old[i][j] = (r < m && cc < m) ? C[(int64_t)r * ldc + cc] : 0.0;
+            }
+        double ra[QA], rb[QA];
+        auto fetch = [&](int k0) {
+#pragma unroll
+            for (int q = 0; q < QA; ++q) {
+                const int idx = t + q * 256, kk = idx / T, e = idx % T, k = k0 + kk;
+                ra[q] = (k < kdep && r0 + e < m) ? P[(int64_t)k * lda + r0 + e] : 0.0;
+                rb[q] = (k < kdep && c0 + e < m) ? P[(int64_t)k * lda + c0 + e] : 0.0;
+            }
+        };
+        auto stash = [&](int buf) {
+#pragma unroll
+            for (int q = 0; q < QA; ++q) {
+                const int idx = t + q * 256;
+                As[buf * TK * T + idx] = ra[q];
+                Bs[buf * TK * T + idx] = rb[q];
+            }
+        };
+        int buf = 0;
+        fetch(0);
+        stash(0);
+        group_bar(1 + g);
+        for (int k0 = 0; k0 < kdep; k0 += TK) {
+            const bool more = k0 + TK < kdep;
+            if (more) fetch(k0 + TK);
+#pragma unroll
+            for (int kk = 0; kk < TK; ++kk) {
+                double a[MI], b[MI];
+#pragma unroll
+                for (int i = 0; i < MI; ++i) a[i] = As[buf * TK * T + kk * T + ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < MI; ++j) b[j] = Bs[buf * TK * T + kk * T + tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < MI; ++i)
+#pragma unroll
+                    for (int j = 0; j < MI; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            }
+            if (more) stash(buf ^ 1);
+            group_bar(1 + g);
+            buf ^= 1;
+        }
+#pragma unroll
+        for (int i = 0; i < MI; ++i)
+#pragma unroll
+            for (int j = 0; j < MI; ++j) {
+                const int r = r0 + ty + 16 * i, cc = c0 + tx + 16 * j;
+                if (r < m && cc < m) C[(int64_t)r * ldc + cc] = old[i][j] - acc[i][j];
+            }
+    }
+}
+
 // ------------------------------------------------- shared-memory factorisations
 // In-place Cholesky of the symmetric n x n matrix held column-major in L
 // (L[j*ld + i] = A_ij); on exit the lower triangle holds the factor.  A pivot
@@ -565,6 +662,18 @@ void launch_gemm_tn(cudaStream_t st, int m, int ncol, int batch, const double* A
     }
 }
 
+void launch_syrk_tri_persist(cudaStream_t st, int m, int kdep, const double* P, int lda, double* C, int ldc, int* ctr,
+                             int grid) {
+    if (m <= 0 || grid <= 0) return;
+    if (!g_persist_ok) {   // a device without the shared memory to reserve an SM: the one-shot tiled kernel
+        dim3 g((m + 31) / 32, (m + 31) / 32, 1);
+        k_gemm_tn<32, 32><<<g, kThreads, 0, st>>>(m, m, P, lda, nullptr, 0, P, lda, nullptr, 0, nullptr, kdep, C, ldc,
+                                                  0, -1.0, 1.0, 1);
+        return;
+    }
+    k_syrk_tri_persist<<<grid, kPersistThreads, kPersistSmem, st>>>(m, kdep, P, lda, C, ldc, ctr);
+}
+
 void launch_block_chol_inv(cudaStream_t st, int nb, int n, const double* Z, double* Y, int* flag) {
     const size_t sm = smem_two_mats(n);
     k_block_chol_inv<<<nb, kThreads, sm, st>>>(n, Z, Y, flag);
@@ -608,6 +717,9 @@ double fp64_peak_probe(int device) {
 }
 
 void init_attrs_linalg(int smem_max) {
+    // the opt-in limit covers the reservation plus the static tile-index slots
+    g_persist_ok = (size_t)smem_max >= kPersistSmem + 64;
+    if (g_persist_ok) set_max_dynamic_smem((const void*)k_syrk_tri_persist, smem_max);
     set_max_dynamic_smem((const void*)k_block_chol_inv, smem_max);
     set_max_dynamic_smem((const void*)k_block_maxstep, smem_max);
     set_max_dynamic_smem((const void*)k_block_mineig, smem_max);

@@ -106,6 +106,7 @@ struct psdp_ctx {
     double *d_Linv = nullptr;         // diagonal-block inverses of the dense factor [npanel][nb][nb]
     double *d_Linv64 = nullptr;       // the same paired into 64 x 64 blocks for the sweeps [ceil(K/64)][64][64]
     unsigned *d_trsv_sync = nullptr;  // tickets and ready flags of the triangular sweeps
+    int *d_chol_ctr = nullptr;        // tile counters of the persistent FP64 trailing updates, one per panel
     int nb_chol = 32;
     double flops_schur = 0, flops_chol = 0, flops_schur_dense = 0;
 
@@ -175,6 +176,11 @@ void launch_bgemm(cudaStream_t st, int n, int count,
 // batched TN GEMM: C_b[r][c] = alpha * sum_{k<kd_b} A_b[k*lda + r] * B_b[k*ldb + c] + beta * C_b[r*ldc + c]
 // for r < m, c < ncol; per-batch offsets (elements) and contraction lengths from device arrays
 // (or uniform when the arrays are null).  tri: only tiles with tile_c >= tile_r.
+// Persistent FP64 Cholesky trailing update C[r][c] -= sum_k P[k*lda+r] P[k*lda+c]
+// on the c >= r 32 x 32 tiles of the m x m matrix (depth kdep); grid CTAs of two
+// 256-thread groups each reserve a whole SM; *ctr must be zero at launch.
+void launch_syrk_tri_persist(cudaStream_t st, int m, int kdep, const double* P, int lda, double* C, int ldc, int* ctr,
+                             int grid);
 void launch_gemm_tn(cudaStream_t st, int m, int ncol, int batch,
                     const double* A, int lda, const int32_t* a_off, int64_t a_stride,
                     const double* B, int ldb, const int32_t* b_off, int64_t b_stride,
