@@ -342,10 +342,12 @@ k_syrk_tri_persist(int m, int kdep, const double* __restrict__ P, int lda, doubl
 
 // ------------------------------------------------- shared-memory factorisations
 // In-place Cholesky of the symmetric n x n matrix held column-major in L
-// (L[j*ld + i] = A_ij); on exit the lower triangle holds the factor.  A pivot
-// that is not positive and finite sets *bad and is replaced by 1 so the sweep
-// still terminates deterministically.
-__device__ void chol_smem(double* L, int ld, int n, int* bad) {
+// (L[j*ld + i] = A_ij); on exit the lower triangle holds the factor and rd[j]
+// = 1/L_jj.  A pivot that is not positive and finite sets *bad and is replaced
+// by 1 so the sweep still terminates deterministically.  The pivot goes through
+// one rsqrt (L_jj = d r, the column scaled by r), as a division and a sqrt cost
+// ~440 and ~620 cycles of dependent FP64 latency on GB300 against ~375.
+__device__ void chol_smem(double* L, int ld, int n, int* bad, double* rd) {
     for (int j = 0; j < n; ++j) {
         if (threadIdx.x == 0) {
             double d = L[j * ld + j];
@@ -353,11 +355,13 @@ __device__ void chol_smem(double* L, int ld, int n, int* bad) {
                 *bad = 1;
                 d = 1.0;
             }
-            L[j * ld + j] = sqrt(d);
+            const double r = rsqrt(d);
+            L[j * ld + j] = d * r;
+            rd[j] = r;
         }
         __syncthreads();
-        const double piv = L[j * ld + j];
-        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) L[j * ld + i] /= piv;
+        const double rj = rd[j];
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) L[j * ld + i] *= rj;
         __syncthreads();
         const int m = n - j - 1;
         for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
@@ -368,55 +372,69 @@ __device__ void chol_smem(double* L, int ld, int n, int* bad) {
     }
 }
 
-// I = L^{-1} (both column-major, lower); one thread per column.
-__device__ void trinv_smem(const double* L, double* I, int ld, int n) {
+// I = L^{-1} (both column-major, lower), rd[r] = 1/L_rr; one thread per column.
+__device__ void trinv_smem(const double* L, const double* rd, double* I, int ld, int n) {
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
         for (int r = 0; r < c; ++r) I[c * ld + r] = 0.0;
         for (int r = c; r < n; ++r) {
             double s = (r == c) ? 1.0 : 0.0;
             for (int k = c; k < r; ++k) s -= L[k * ld + r] * I[c * ld + k];
-            I[c * ld + r] = s / L[r * ld + r];
+            I[c * ld + r] = s * rd[r];
         }
     }
     __syncthreads();
 }
 
 // Householder reduction of the symmetric n x n matrix S (row-major, full storage,
-// destroyed) to tridiagonal form: diagonal dv[0..n-1], off-diagonal ev[0..n-2].
-__device__ void tridiag_smem(double* S, int ld, int n, double* dv, double* ev, double* v, double* p, double* red) {
-    const int tid = threadIdx.x, nt = blockDim.x;
+// destroyed) to tridiagonal form: diagonal dv[0..n-1], off-diagonal ev[0..n-2];
+// v, p are n-long scratch and dv doubles as scratch until the end.  All threads
+// of the CTA call it.  GB300's FP64 latencies (a dependent DFMA ~65 cycles, a
+// shuffle-add level ~95, sqrt ~620, rsqrt ~375) make every step a latency
+// chain, so the scalar reductions (sigma = |x|^2, K = v.p) are computed by every
+// warp redundantly (no barrier round trip, identical results), the product
+// p = S v uses eight lanes per row, and 1/sqrt(2(sigma - alpha x0)) is one rsqrt.
+__device__ void tridiag_smem(double* S, int ld, int n, double* dv, double* ev, double* v, double* p) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    const int g = tid >> 3, gl = tid & 7, ng = nt >> 3;
+    double* w = dv;
     for (int k = 0; k + 2 < n; ++k) {
         double part = 0.0;
-        for (int i = k + 1 + tid; i < n; i += nt) {
+        for (int i = k + 1 + lane; i < n; i += 32) {
             const double x = S[i * ld + k];
-            part += x * x;
+            part = fma(x, x, part);
         }
-        const double sigma = block_sum(part, red);
+        const double sigma = warp_sum(part);
         const double x0 = S[(k + 1) * ld + k];
-        if (sigma == 0.0) {
+        if (sigma == 0.0) {                       // uniform over the CTA
             if (tid == 0) ev[k] = 0.0;
-            __syncthreads();
-            continue;
+            continue;                             // S is not written in this step
         }
         const double alpha = -copysign(sqrt(sigma), x0);
-        const double inv = 1.0 / sqrt(2.0 * (sigma - alpha * x0));
+        const double inv = rsqrt(2.0 * (sigma - alpha * x0));
         for (int i = k + 1 + tid; i < n; i += nt) v[i] = (i == k + 1 ? x0 - alpha : S[i * ld + k]) * inv;
         __syncthreads();
-        for (int i = k + 1 + tid; i < n; i += nt) {
+        // p_i = sum_j S_ij v_j over rows and columns k+1..n-1; the loop bound is
+        // uniform so every lane reaches the shuffles
+        for (int base = k + 1; base < n; base += ng) {
+            const int i = base + g;
             double s = 0.0;
-            for (int j = k + 1; j < n; ++j) s = fma(S[i * ld + j], v[j], s);
-            p[i] = s;
+            if (i < n)
+                for (int j = k + 1 + gl; j < n; j += 8) s = fma(S[i * ld + j], v[j], s);
+            s += __shfl_xor_sync(0xffffffffu, s, 4);
+            s += __shfl_xor_sync(0xffffffffu, s, 2);
+            s += __shfl_xor_sync(0xffffffffu, s, 1);
+            if (i < n && gl == 0) p[i] = s;
         }
         __syncthreads();
         part = 0.0;
-        for (int i = k + 1 + tid; i < n; i += nt) part += v[i] * p[i];
-        const double kc = block_sum(part, red);
-        for (int i = k + 1 + tid; i < n; i += nt) p[i] = 2.0 * (p[i] - kc * v[i]);
+        for (int i = k + 1 + lane; i < n; i += 32) part = fma(v[i], p[i], part);
+        const double kc = warp_sum(part);
+        for (int i = k + 1 + tid; i < n; i += nt) w[i] = 2.0 * (p[i] - kc * v[i]);
         __syncthreads();
         const int m = n - k - 1;
         for (int idx = tid; idx < m * m; idx += nt) {
             const int i = k + 1 + idx / m, j = k + 1 + idx % m;
-            S[i * ld + j] -= v[i] * p[j] + p[i] * v[j];
+            S[i * ld + j] -= fma(v[i], w[j], w[i] * v[j]);
         }
         if (tid == 0) ev[k] = alpha;
         __syncthreads();
@@ -426,12 +444,26 @@ __device__ void tridiag_smem(double* S, int ld, int n, double* dv, double* ev, d
     __syncthreads();
 }
 
-// Smallest eigenvalue of the symmetric tridiagonal (dv, ev) by Sturm counts:
-// 32 lanes of one warp evaluate 32 interior points per round (multisection).
-// Bounded: at most 80 rounds.  Must be called by a whole warp.
-__device__ double sturm_min(const double* dv, const double* ev, int n) {
-    const int lane = threadIdx.x & 31;
+// Smallest eigenvalue of the symmetric tridiagonal (dv, ev) by multisection:
+// each of the first 64 threads tests one interior point x per round (GB300
+// issues a warp's FP64 instructions about every 65 cycles and two CTAs share an
+// SM here, so more points per round cost more than the rounds they save:
+// measured 141k cycles with 64 points, 150k with 32, 167k with 128), and x lies
+// above the smallest eigenvalue iff T - xI is not positive definite, i.e. iff
+// one of the leading principal minors p_i = det(T_i - xI) is <= 0.  The minors
+// follow the three-term recurrence p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2}
+// (one dependent DFMA per step, where the pivot form d_i - x - e^2/q_{i-1}
+// needs a division), rescaled by a power of two every four steps (exact, sign
+// preserving).  A zero minor counts as not positive definite, as a pivot
+// replaced by -pivmin does in the pivot form.  Bounded: at most 80 rounds.
+// All threads of the CTA call it (blockDim a multiple of 32, at least 32);
+// e2n holds n-1 doubles of scratch (-e_i^2) and red 8 ints.
+__device__ double sturm_min(const double* dv, const double* ev, int n, double* e2n, int* red) {
+    constexpr int kPts = 64;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int np = blockDim.x < kPts ? (int)blockDim.x : kPts, nw = np >> 5;
     if (n == 1) return dv[0];
+    for (int i = tid; i < n - 1; i += blockDim.x) e2n[i] = -(ev[i] * ev[i]);
     double lo = INFINITY, hi = -INFINITY, e2max = 0.0;
     for (int i = lane; i < n; i += 32) {
         const double r = (i > 0 ? fabs(ev[i - 1]) : 0.0) + (i < n - 1 ? fabs(ev[i]) : 0.0);
@@ -446,27 +478,40 @@ __device__ double sturm_min(const double* dv, const double* ev, int n) {
     const double sc = fmax(fabs(lo), fabs(hi));
     lo -= 4.0 * DBL_EPSILON * sc + pivmin;
     hi += 4.0 * DBL_EPSILON * sc + pivmin;
+    __syncthreads();
     for (int it = 0; it < 80; ++it) {
         if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 2.0 * pivmin) break;
-        const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-        int cnt = 0;
-        double q = dv[0] - x;
-        if (fabs(q) < pivmin) q = -pivmin;
-        cnt += q < 0.0;
-        for (int i = 1; i < n; ++i) {
-            q = dv[i] - x - ev[i - 1] * ev[i - 1] / q;
-            if (fabs(q) < pivmin) q = -pivmin;
-            cnt += q < 0.0;
+        int* slot = red + (it & 1) * 4;
+        if (wid < nw) {
+            const double x = lo + (hi - lo) * (double)(tid + 1) / (double)(np + 1);
+            double pm = 1.0, pc = dv[0] - x;
+            long long bad = __double_as_longlong(pc) <= 0;
+            for (int i = 1; i < n; ++i) {
+                const double pn = fma(dv[i] - x, pc, e2n[i - 1] * pm);
+                bad |= __double_as_longlong(pn) <= 0;
+                pm = pc;
+                pc = pn;
+                if ((i & 3) == 3) {
+                    long long be = (__double_as_longlong(pc) >> 52) & 0x7ff;
+                    be = be > 2045 ? 2045 : be;
+                    const double f = __longlong_as_double((2046 - be) << 52);   // 2^(1023 - be)
+                    pc *= f;
+                    pm *= f;
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, bad != 0);
+            if (lane == 0) slot[wid] = bal ? wid * 32 + __ffs(bal) - 1 : np;
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, cnt >= 1);
-        const int j = bal ? __ffs(bal) - 1 : 31;
-        const double xj = __shfl_sync(0xffffffffu, x, j);
-        const double xjm = __shfl_sync(0xffffffffu, x, j > 0 ? j - 1 : 0);
-        if (bal == 0) {
-            lo = xj;
+        __syncthreads();
+        int kmin = np;
+        for (int q = 0; q < nw; ++q) kmin = min(kmin, slot[q]);
+        const double span = hi - lo;
+        if (kmin == np) {
+            lo = lo + span * (double)np / (double)(np + 1);
         } else {
-            hi = xj;
-            if (j > 0) lo = xjm;
+            const double xk = lo + span * (double)(kmin + 1) / (double)(np + 1);
+            if (kmin > 0) lo = lo + span * (double)kmin / (double)(np + 1);
+            hi = xk;
         }
     }
     return 0.5 * (lo + hi);
@@ -479,6 +524,7 @@ k_block_chol_inv(int n, const double* __restrict__ Z, double* __restrict__ Y, in
     const int ld = n + 1;
     double* L = sm;
     double* I = sm + (size_t)n * ld;
+    double* rd = I + (size_t)n * ld;
     __shared__ int bad;
     const int g = blockIdx.x;
     const double* Zg = Z + (size_t)g * n * n;
@@ -488,8 +534,8 @@ k_block_chol_inv(int n, const double* __restrict__ Z, double* __restrict__ Y, in
         L[j * ld + i] = Zg[idx];   // symmetric: column-major copy equals row-major copy
     }
     __syncthreads();
-    chol_smem(L, ld, n, &bad);
-    trinv_smem(L, I, ld, n);
+    chol_smem(L, ld, n, &bad, rd);
+    trinv_smem(L, rd, I, ld, n);
     double* Yg = Y + (size_t)g * n * n;
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
         const int i = idx / n, j = idx % n;
@@ -511,7 +557,7 @@ k_block_maxstep(int nb, int n, const double* __restrict__ X, const double* __res
     double* ev = dv + n;
     double* v = ev + n;
     double* p = v + n;
-    __shared__ double red[32];
+    __shared__ int ired[8];
     __shared__ int bad;
     const int g = blockIdx.x;
     const size_t off = (size_t)(g % nb) * n * n;
@@ -524,13 +570,14 @@ k_block_maxstep(int nb, int n, const double* __restrict__ X, const double* __res
         S[i * ld + j] = Dg[idx];
     }
     __syncthreads();
-    chol_smem(L, ld, n, &bad);
+    double* rd = p;                          // 1/L_jj until the tridiagonal reduction
+    chol_smem(L, ld, n, &bad, rd);
     // S <- L^{-1} S (forward substitution, one thread per column)
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         for (int i = 0; i < n; ++i) {
             double s = S[i * ld + j];
             for (int k = 0; k < i; ++k) s -= L[k * ld + i] * S[k * ld + j];
-            S[i * ld + j] = s / L[i * ld + i];
+            S[i * ld + j] = s * rd[i];
         }
     }
     __syncthreads();
@@ -539,7 +586,7 @@ k_block_maxstep(int nb, int n, const double* __restrict__ X, const double* __res
         for (int j = 0; j < n; ++j) {
             double s = S[i * ld + j];
             for (int k = 0; k < j; ++k) s -= L[k * ld + j] * S[i * ld + k];
-            S[i * ld + j] = s / L[j * ld + j];
+            S[i * ld + j] = s * rd[j];
         }
     }
     __syncthreads();
@@ -552,15 +599,13 @@ k_block_maxstep(int nb, int n, const double* __restrict__ X, const double* __res
         }
     }
     __syncthreads();
-    tridiag_smem(S, ld, n, dv, ev, v, p, red);
-    if (threadIdx.x < 32) {
-        const double lam = sturm_min(dv, ev, n);
-        if (threadIdx.x == 0) {
-            tstep[g] = (lam < 0.0) ? -1.0 / lam : 1e300;
-            if (bad) {
-                tstep[g] = 0.0;
-                atomicOr(flag, (int)FL_CHOL_BLOCK);
-            }
+    tridiag_smem(S, ld, n, dv, ev, v, p);
+    const double lam = sturm_min(dv, ev, n, v, ired);
+    if (threadIdx.x == 0) {
+        tstep[g] = (lam < 0.0) ? -1.0 / lam : 1e300;
+        if (bad) {
+            tstep[g] = 0.0;
+            atomicOr(flag, (int)FL_CHOL_BLOCK);
         }
     }
 }
@@ -575,6 +620,7 @@ k_block_mineig(int n, const double* __restrict__ M, double sign, double* out) {
     double* v = ev + n;
     double* p = v + n;
     __shared__ double red[32];
+    __shared__ int ired[8];
     const int g = blockIdx.x;
     const double* Mg = M + (size_t)g * n * n;
     double part = 0.0;
@@ -586,13 +632,11 @@ k_block_mineig(int n, const double* __restrict__ M, double sign, double* out) {
     }
     const double fro = sqrt(block_sum(part, red));
     __syncthreads();
-    tridiag_smem(S, ld, n, dv, ev, v, p, red);
-    if (threadIdx.x < 32) {
-        const double lam = sturm_min(dv, ev, n);
-        if (threadIdx.x == 0) {
-            out[2 * g] = lam;
-            out[2 * g + 1] = fro;
-        }
+    tridiag_smem(S, ld, n, dv, ev, v, p);
+    const double lam = sturm_min(dv, ev, n, v, ired);
+    if (threadIdx.x == 0) {
+        out[2 * g] = lam;
+        out[2 * g + 1] = fro;
     }
 }
 
@@ -675,7 +719,7 @@ void launch_syrk_tri_persist(cudaStream_t st, int m, int kdep, const double* P, 
 }
 
 void launch_block_chol_inv(cudaStream_t st, int nb, int n, const double* Z, double* Y, int* flag) {
-    const size_t sm = smem_two_mats(n);
+    const size_t sm = smem_two_mats(n) + (size_t)n * sizeof(double);
     k_block_chol_inv<<<nb, kThreads, sm, st>>>(n, Z, Y, flag);
 }
 
