@@ -195,6 +195,14 @@ psdp_status psdp_get_iterate(psdp_ctx* c, double* X, double* Z, double* y);
  * authoritative; FP64 in both precision modes).  Test and inspection hook. */
 psdp_status psdp_get_schur(psdp_ctx* c, double* Omega);
 
+/* Selected columns of the same FP64 Omega (Sec. IV-A) at the current iterate,
+ * for parity checks at sizes where the full K x K copy does not fit the host:
+ * out[q*K + i] = Omega_{i, cols[q]} for q < ncols, i < K.  cols: host int32,
+ * each in [0, K) (else EINVAL); out: host, ncols*K doubles, caller-owned.
+ * Forms Omega on the device like psdp_get_schur (ECHOL_BLOCK if a block of Z is
+ * not positive definite). */
+psdp_status psdp_get_schur_cols(psdp_ctx* c, const int32_t* cols, int ncols, double* out);
+
 /* The same Omega as computed by the mixed-precision path (PSDP_MIXED contexts only,
  * else ESTATE): operands rounded to FP32 and contracted on the tensor cores in
  * 3xTF32 with FP32 accumulation; K x K float32, full (upper triangle computed,

@@ -26,7 +26,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ECHOL_BLOCK", 5: "E
 # every symbol the header declares
 EXPORTS = ("psdp_default_opts", "psdp_setup", "psdp_sizes", "psdp_step", "psdp_solve", "psdp_certify",
            "psdp_grid_check", "psdp_get_P", "psdp_get_y", "psdp_get_tables", "psdp_load_iterate",
-           "psdp_get_iterate", "psdp_get_schur", "psdp_apply_BT", "psdp_apply_B", "psdp_profile_enable",
+           "psdp_get_iterate", "psdp_get_schur", "psdp_get_schur_cols", "psdp_apply_BT", "psdp_apply_B", "psdp_profile_enable",
            "psdp_profile_reset", "psdp_profile_get", "psdp_work", "psdp_stream", "psdp_fp64_peak",
            "psdp_destroy", "psdp_strerror", "psdp_tc_gemm_check", "psdp_tc_gemm_persist_check", "psdp_trsv_timeout_check", "psdp_get_schur_mixed",
            "psdp_tc_gemm_noalloc", "psdp_solve_batch", "psdp_autotune", "psdp_set_start", "psdp_mlp_create",
@@ -73,6 +73,7 @@ def _lib():
             "psdp_load_iterate": (C.c_int, [vp, dp, dp, dp]),
             "psdp_get_iterate": (C.c_int, [vp, dp, dp, dp]),
             "psdp_get_schur": (C.c_int, [vp, dp]),
+            "psdp_get_schur_cols": (C.c_int, [vp, ip, C.c_int, dp]),
             "psdp_apply_BT": (C.c_int, [vp, dp, dp]),
             "psdp_apply_B": (C.c_int, [vp, dp, dp]),
             "psdp_profile_enable": (C.c_int, [vp, C.c_int]),
@@ -212,6 +213,16 @@ def psdp_get_schur(h) -> np.ndarray:
     Om = np.zeros((K, K))
     _check(_lib().psdp_get_schur(h, _dp(Om)), "psdp_get_schur")
     return Om
+
+
+def psdp_get_schur_cols(h, cols) -> np.ndarray:
+    """Columns cols of the FP64 Schur complement at the current iterate, shape (len(cols), K)."""
+    cols = np.ascontiguousarray(cols, dtype=np.int32)
+    K = psdp_sizes(h)["K"]
+    out = np.zeros((len(cols), K))
+    _check(_lib().psdp_get_schur_cols(h, cols.ctypes.data_as(C.POINTER(C.c_int32)), len(cols), _dp(out)),
+           "psdp_get_schur_cols")
+    return out
 
 
 def psdp_get_schur_mixed(h) -> np.ndarray:

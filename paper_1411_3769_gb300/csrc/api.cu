@@ -1308,6 +1308,41 @@ psdp_status psdp_get_schur(psdp_ctx* c, double* Om) {
     return PSDP_OK;
 }
 
+psdp_status psdp_get_schur_cols(psdp_ctx* c, const int32_t* cols, int ncols, double* out) {
+    if (!c || !cols || !out || ncols < 0) return PSDP_EINVAL;
+    for (int q = 0; q < ncols; ++q)
+        if (cols[q] < 0 || cols[q] >= c->K) return PSDP_EINVAL;
+    cudaSetDevice(c->device);
+    TRY(alloc_fp64(c));
+    cudaStream_t st = c->stream;
+    cudaMemsetAsync(c->d_flag, 0, sizeof(int), st);
+    launch_block_chol_inv(st, c->nblk, c->n, c->d_Z, c->d_Y, c->d_flag);
+    const bool on = c->prof_on;
+    c->prof_on = false;
+    enqueue_schur(c);
+    c->prof_on = on;
+    // Omega is row-major with its upper triangle filled: column j holds
+    // Omega[i][j] (i < j) in rows above j and Omega[j][i] (i >= j) in row j
+    const size_t K = c->K;
+    for (int q = 0; q < ncols; ++q) {
+        const size_t j = cols[q];
+        double* o = out + (size_t)q * K;
+        if (j > 0)
+            cudaMemcpy2DAsync(o, sizeof(double), c->d_Om + j, K * sizeof(double), sizeof(double), j,
+                              cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(o + j, c->d_Om + j * K + j, (K - j) * sizeof(double), cudaMemcpyDeviceToHost, st);
+    }
+    int flag = 0;
+    cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    TRY(sync_check(c));
+    if (flag) {
+        cudaMemsetAsync(c->d_flag, 0, sizeof(int), st);
+        sync_check(c);
+        return PSDP_ECHOL_BLOCK;
+    }
+    return PSDP_OK;
+}
+
 psdp_status psdp_apply_BT(psdp_ctx* c, const double* v, double* out) {
     if (!c || !v || !out) return PSDP_EINVAL;
     cudaSetDevice(c->device);
