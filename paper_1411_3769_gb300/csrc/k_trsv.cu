@@ -15,8 +15,8 @@
 // is bit-reproducible.  A finished block is published with a release store of
 // its ready flag; readers acquire the flag and read the solved values through
 // L2.  Warp 0 polls, the CTA synchronises once per batch of newly solved
-// blocks, and the tile of the last predecessor is in registers before the
-// wait, so the critical path per block is the flag latency, one W x W tile
+// blocks, and the tile of the last predecessor is loaded into registers before
+// the wait, so the critical path per block is the flag latency, one W x W tile
 // product from registers and the diagonal-block product.  Every wait is
 // bounded (2 s without progress): the CTA sets FL_TIMEOUT and finishes with
 // what it has, so its dependants finish too.
@@ -75,6 +75,10 @@ __device__ __forceinline__ void load_vec_cg(const T* p, T* o) {
         o[0] = v.x; o[1] = v.y;
     }
 }
+
+// values of the last predecessor's tile a thread keeps in registers
+template <typename T>
+constexpr int kPreVals = sizeof(T) == 4 ? 64 : 16;
 
 template <typename T>
 size_t trsv_smem(int W) { return ((size_t)W * W + (size_t)(TT / W) * W + W) * sizeof(T); }
@@ -183,7 +187,7 @@ __device__ __forceinline__ int wait_suffix(const unsigned* ready, int qd, int p,
 // the rows j = qW + g + G t of every solved block q, U rows in flight.  The
 // tile of block p-1, the last to be solved, is loaded before the first wait.
 template <typename T, int W, int V>
-__global__ void __launch_bounds__(TT)
+__global__ void __launch_bounds__(TT, sizeof(T) == 4 ? 2 : 1)
 k_trsv_fwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, const double* __restrict__ bin, T* x,
            unsigned* sync, int* flag, const int* skip) {
     if (skip && *skip) return;
@@ -209,7 +213,10 @@ k_trsv_fwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, const dou
     // this block's right-hand side, read before any wait
     const T bown = (threadIdx.x < w) ? (T)(bin ? bin[j0 + threadIdx.x] : (double)ldcg(x + j0 + threadIdx.x)) : T(0);
     const int c = (threadIdx.x % R) * V, g = threadIdx.x / R;
-    constexpr bool PRE = RPB * V <= 16;    // register budget: prefetch small tiles only
+    // the last predecessor's tile is held in registers before the wait: 16 values
+    // a thread for FP64, 64 for the FP32 preconditioner's 128-row blocks (at
+    // most 128 registers, so two CTAs still fit an SM)
+    constexpr bool PRE = RPB * V <= kPreVals<T>;
     T last[PRE ? RPB : 1][V];
     if (PRE && p > 0 && c < w) {
 #pragma unroll
@@ -293,7 +300,7 @@ k_trsv_fwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, const dou
 // row group g owns rows k = g + G t.  The tile of block p+1, the last to be
 // solved, is loaded before the first wait.
 template <typename T, int W, int V>
-__global__ void __launch_bounds__(TT)
+__global__ void __launch_bounds__(TT, sizeof(T) == 4 ? 2 : 1)
 k_trsv_bwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, T* x, double* xout, unsigned* sync, int* flag,
            const int* skip) {
     if (skip && *skip) return;
@@ -317,7 +324,7 @@ k_trsv_bwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, T* x, dou
     for (int i = threadIdx.x; i < W * W; i += TT) Ls[i] = Lp[i];
     if (threadIdx.x < W) acc[threadIdx.x] = (threadIdx.x < w) ? ldcg(x + j0 + threadIdx.x) : T(0);   // z_p
     const int cl = (threadIdx.x % R) * V, g = threadIdx.x / R;
-    constexpr bool PRE = SEG * RPB * V <= 16;   // register budget: prefetch small tiles only
+    constexpr bool PRE = SEG * RPB * V <= kPreVals<T>;   // as in the forward sweep
     T last[PRE ? SEG : 1][PRE ? RPB : 1][V];
     if (PRE && p + 1 < npanel) {
 #pragma unroll
