@@ -363,10 +363,11 @@ __device__ void chol_smem(double* L, int ld, int n, int* bad, double* rd) {
         const double rj = rd[j];
         for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) L[j * ld + i] *= rj;
         __syncthreads();
-        const int m = n - j - 1;
-        for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-            const int c = j + 1 + idx / m, r = j + 1 + idx % m;
-            if (r >= c) L[c * ld + r] -= L[j * ld + r] * L[j * ld + c];
+        // rank-1 update of the trailing lower triangle: warps over columns c,
+        // lanes over rows r >= c
+        for (int c = j + 1 + (threadIdx.x >> 5); c < n; c += blockDim.x >> 5) {
+            const double lc = L[j * ld + c];
+            for (int r = c + (threadIdx.x & 31); r < n; r += 32) L[c * ld + r] -= L[j * ld + r] * lc;
         }
         __syncthreads();
     }
@@ -387,31 +388,42 @@ __device__ void trinv_smem(const double* L, const double* rd, double* I, int ld,
 
 // Householder reduction of the symmetric n x n matrix S (row-major, full storage,
 // destroyed) to tridiagonal form: diagonal dv[0..n-1], off-diagonal ev[0..n-2];
-// v, p are n-long scratch and dv doubles as scratch until the end.  All threads
-// of the CTA call it.  GB300's FP64 latencies (a dependent DFMA ~65 cycles, a
-// shuffle-add level ~95, sqrt ~620, rsqrt ~375) make every step a latency
-// chain, so the scalar reductions (sigma = |x|^2, K = v.p) are computed by every
-// warp redundantly (no barrier round trip, identical results), the product
-// p = S v uses eight lanes per row, and 1/sqrt(2(sigma - alpha x0)) is one rsqrt.
-__device__ void tridiag_smem(double* S, int ld, int n, double* dv, double* ev, double* v, double* p) {
+// v, p are n-long scratch and dv doubles as scratch until the end; sc holds 4
+// doubles.  All threads of the CTA call it.  GB300 issues a warp's FP64
+// instruction about every 65 cycles per SMSP and two CTAs share an SM here, so
+// the kernel is bound by FP64 issue: the scalars (sigma = |x|^2, alpha,
+// 1/sqrt(2(sigma - alpha x0)) as one rsqrt, K = v.p) are formed by warp 0 alone
+// and broadcast through shared memory (a barrier costs ~20 cycles, a redundant
+// FP64 op ~65 per warp on the pipe), and p = S v uses eight lanes a row.
+__device__ void tridiag_smem(double* S, int ld, int n, double* dv, double* ev, double* v, double* p, double* sc) {
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
     const int g = tid >> 3, gl = tid & 7, ng = nt >> 3;
     double* w = dv;
     for (int k = 0; k + 2 < n; ++k) {
-        double part = 0.0;
-        for (int i = k + 1 + lane; i < n; i += 32) {
-            const double x = S[i * ld + k];
-            part = fma(x, x, part);
+        if (tid < 32) {
+            double part = 0.0;
+            for (int i = k + 1 + lane; i < n; i += 32) {
+                const double x = S[i * ld + k];
+                part = fma(x, x, part);
+            }
+            const double sigma = warp_sum(part);
+            if (lane == 0) {
+                const double x0 = S[(k + 1) * ld + k];
+                double alpha = 0.0, inv = 0.0;
+                if (sigma != 0.0) {
+                    alpha = -copysign(sqrt(sigma), x0);
+                    inv = rsqrt(2.0 * (sigma - alpha * x0));
+                }
+                sc[2 * (k & 1)] = alpha;       // alternate slots: a step with sigma = 0 has
+                sc[2 * (k & 1) + 1] = inv;     // no second barrier before the next write
+                ev[k] = alpha;
+            }
         }
-        const double sigma = warp_sum(part);
-        const double x0 = S[(k + 1) * ld + k];
-        if (sigma == 0.0) {                       // uniform over the CTA
-            if (tid == 0) ev[k] = 0.0;
-            continue;                             // S is not written in this step
-        }
-        const double alpha = -copysign(sqrt(sigma), x0);
-        const double inv = rsqrt(2.0 * (sigma - alpha * x0));
-        for (int i = k + 1 + tid; i < n; i += nt) v[i] = (i == k + 1 ? x0 - alpha : S[i * ld + k]) * inv;
+        __syncthreads();
+        const double alpha = sc[2 * (k & 1)], inv = sc[2 * (k & 1) + 1];
+        if (inv == 0.0) continue;                 // sigma = 0: S is not written in this step
+        for (int i = k + 1 + tid; i < n; i += nt)
+            v[i] = (i == k + 1 ? S[(k + 1) * ld + k] - alpha : S[i * ld + k]) * inv;
         __syncthreads();
         // p_i = sum_j S_ij v_j over rows and columns k+1..n-1; the loop bound is
         // uniform so every lane reaches the shuffles
@@ -426,17 +438,18 @@ __device__ void tridiag_smem(double* S, int ld, int n, double* dv, double* ev, d
             if (i < n && gl == 0) p[i] = s;
         }
         __syncthreads();
-        part = 0.0;
-        for (int i = k + 1 + lane; i < n; i += 32) part = fma(v[i], p[i], part);
-        const double kc = warp_sum(part);
-        for (int i = k + 1 + tid; i < n; i += nt) w[i] = 2.0 * (p[i] - kc * v[i]);
-        __syncthreads();
-        const int m = n - k - 1;
-        for (int idx = tid; idx < m * m; idx += nt) {
-            const int i = k + 1 + idx / m, j = k + 1 + idx % m;
-            S[i * ld + j] -= fma(v[i], w[j], w[i] * v[j]);
+        if (tid < 32) {
+            double part = 0.0;
+            for (int i = k + 1 + lane; i < n; i += 32) part = fma(v[i], p[i], part);
+            const double kc = warp_sum(part);
+            for (int i = k + 1 + lane; i < n; i += 32) w[i] = 2.0 * (p[i] - kc * v[i]);
         }
-        if (tid == 0) ev[k] = alpha;
+        __syncthreads();
+        // rank-2 update of rows/columns k+1..n-1: warps over rows, lanes over columns
+        for (int i = k + 1 + (tid >> 5); i < n; i += nt >> 5) {
+            const double vi = v[i], wi = w[i];
+            for (int j = k + 1 + lane; j < n; j += 32) S[i * ld + j] -= fma(vi, w[j], wi * v[j]);
+        }
         __syncthreads();
     }
     for (int i = tid; i < n; i += nt) dv[i] = S[i * ld + i];
@@ -462,6 +475,7 @@ __device__ double sturm_min(const double* dv, const double* ev, int n, double* e
     constexpr int kPts = 64;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int np = blockDim.x < kPts ? (int)blockDim.x : kPts, nw = np >> 5;
+    const double inv_np1 = 1.0 / (double)(np + 1);
     if (n == 1) return dv[0];
     for (int i = tid; i < n - 1; i += blockDim.x) e2n[i] = -(ev[i] * ev[i]);
     double lo = INFINITY, hi = -INFINITY, e2max = 0.0;
@@ -480,10 +494,13 @@ __device__ double sturm_min(const double* dv, const double* ev, int n, double* e
     hi += 4.0 * DBL_EPSILON * sc + pivmin;
     __syncthreads();
     for (int it = 0; it < 80; ++it) {
-        if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 2.0 * pivmin) break;
+        // relative to the eigenvalue and absolute at 2 eps ||T|| (the accuracy
+        // the count itself has), so an eigenvalue near zero does not run all
+        // 80 rounds
+        if (hi - lo <= 2.0 * DBL_EPSILON * (fmax(fabs(lo), fabs(hi)) + sc) + 2.0 * pivmin) break;
         int* slot = red + (it & 1) * 4;
         if (wid < nw) {
-            const double x = lo + (hi - lo) * (double)(tid + 1) / (double)(np + 1);
+            const double x = fma(hi - lo, (double)(tid + 1) * inv_np1, lo);
             double pm = 1.0, pc = dv[0] - x;
             long long bad = __double_as_longlong(pc) <= 0;
             for (int i = 1; i < n; ++i) {
@@ -505,12 +522,14 @@ __device__ double sturm_min(const double* dv, const double* ev, int n, double* e
         __syncthreads();
         int kmin = np;
         for (int q = 0; q < nw; ++q) kmin = min(kmin, slot[q]);
+        // the same expression as the tested points, so the new bounds are exactly
+        // the points the counts were taken at
         const double span = hi - lo;
         if (kmin == np) {
-            lo = lo + span * (double)np / (double)(np + 1);
+            lo = fma(span, (double)np * inv_np1, lo);
         } else {
-            const double xk = lo + span * (double)(kmin + 1) / (double)(np + 1);
-            if (kmin > 0) lo = lo + span * (double)kmin / (double)(np + 1);
+            const double xk = fma(span, (double)(kmin + 1) * inv_np1, lo);
+            if (kmin > 0) lo = fma(span, (double)kmin * inv_np1, lo);
             hi = xk;
         }
     }
@@ -558,6 +577,7 @@ k_block_maxstep(int nb, int n, const double* __restrict__ X, const double* __res
     double* v = ev + n;
     double* p = v + n;
     __shared__ int ired[8];
+    __shared__ double scal2[4];
     __shared__ int bad;
     const int g = blockIdx.x;
     const size_t off = (size_t)(g % nb) * n * n;
@@ -599,7 +619,7 @@ k_block_maxstep(int nb, int n, const double* __restrict__ X, const double* __res
         }
     }
     __syncthreads();
-    tridiag_smem(S, ld, n, dv, ev, v, p);
+    tridiag_smem(S, ld, n, dv, ev, v, p, scal2);
     const double lam = sturm_min(dv, ev, n, v, ired);
     if (threadIdx.x == 0) {
         tstep[g] = (lam < 0.0) ? -1.0 / lam : 1e300;
@@ -621,6 +641,7 @@ k_block_mineig(int n, const double* __restrict__ M, double sign, double* out) {
     double* p = v + n;
     __shared__ double red[32];
     __shared__ int ired[8];
+    __shared__ double scal2[4];
     const int g = blockIdx.x;
     const double* Mg = M + (size_t)g * n * n;
     double part = 0.0;
@@ -632,7 +653,7 @@ k_block_mineig(int n, const double* __restrict__ M, double sign, double* out) {
     }
     const double fro = sqrt(block_sum(part, red));
     __syncthreads();
-    tridiag_smem(S, ld, n, dv, ev, v, p);
+    tridiag_smem(S, ld, n, dv, ev, v, p, scal2);
     const double lam = sturm_min(dv, ev, n, v, ired);
     if (threadIdx.x == 0) {
         out[2 * g] = lam;
