@@ -1,7 +1,8 @@
 // Dense FP64 building blocks: batched n x n GEMM, the tiled TN GEMM used by the
-// Schur-complement contraction and the Cholesky trailing update, per-block
-// Cholesky / inverse, per-block smallest eigenvalue (Householder
-// tridiagonalisation + Sturm-count multisection) and the per-block maximum step.
+// Schur-complement contraction and the Cholesky's thin and one-shot updates,
+// the persistent Cholesky trailing update, per-block Cholesky / inverse,
+// per-block smallest eigenvalue (Householder tridiagonalisation + multisection
+// on leading minors) and the per-block maximum step.
 #include <cfloat>
 #include <cmath>
 
@@ -471,7 +472,7 @@ __device__ void tridiag_smem(double* S, int ld, int n, double* dv, double* ev, d
 // replaced by -pivmin does in the pivot form.  Bounded: at most 80 rounds.
 // All threads of the CTA call it (blockDim a multiple of 32, at least 32);
 // e2n holds n-1 doubles of scratch (-e_i^2) and red 8 ints.
-__device__ double sturm_min(const double* dv, const double* ev, int n, double* e2n, int* red) {
+__device__ double minor_multisection_min(const double* dv, const double* ev, int n, double* e2n, int* red) {
     constexpr int kPts = 64;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int np = blockDim.x < kPts ? (int)blockDim.x : kPts, nw = np >> 5;
@@ -620,7 +621,7 @@ k_block_maxstep(int nb, int n, const double* __restrict__ X, const double* __res
     }
     __syncthreads();
     tridiag_smem(S, ld, n, dv, ev, v, p, scal2);
-    const double lam = sturm_min(dv, ev, n, v, ired);
+    const double lam = minor_multisection_min(dv, ev, n, v, ired);
     if (threadIdx.x == 0) {
         tstep[g] = (lam < 0.0) ? -1.0 / lam : 1e300;
         if (bad) {
@@ -654,7 +655,7 @@ k_block_mineig(int n, const double* __restrict__ M, double sign, double* out) {
     const double fro = sqrt(block_sum(part, red));
     __syncthreads();
     tridiag_smem(S, ld, n, dv, ev, v, p, scal2);
-    const double lam = sturm_min(dv, ev, n, v, ired);
+    const double lam = minor_multisection_min(dv, ev, n, v, ired);
     if (threadIdx.x == 0) {
         out[2 * g] = lam;
         out[2 * g + 1] = fro;
