@@ -308,7 +308,7 @@ template <int SPLIT, int STAGES>
 __global__ void __launch_bounds__(kPersistThreads, 1)
 k_tc_gemm_persist(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
                   const __grid_constant__ CUtensorMap mAlo, const __grid_constant__ CUtensorMap mBlo, int M, int N,
-                  int Kd, float* C, int64_t ldc, float alpha, float beta, int tri, int* flag, TcAux aux) {
+                  int Kd, float* C, int64_t ldc, float alpha, float beta, int tri, int* flag) {
     constexpr int STAGE_BYTES = (SPLIT == 3) ? 2 * (TILE_A + TILE_B) : (TILE_A + TILE_B);
     constexpr int BK = 32;                        // TF32 elements per 128-byte row
     constexpr int KSTEP_BYTES = 32;
@@ -448,26 +448,10 @@ k_tc_gemm_persist(const __grid_constant__ CUtensorMap mA, const __grid_constant_
                 uint32_t r[16];
                 tmem_ld16(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(b * BN + c0), r);
                 if (m < M) {
-                    float v[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int n = n0 + c0 + j;
-                        v[j] = alpha * __uint_as_float(r[j]) + beta * old[c0 + j];
-                        if (n < N) C[(int64_t)n * ldc + m] = v[j];
-                    }
-                    if (aux.hi && m >= aux.m0) {
-                        // the same values as (hi, lo) TF32 pairs, row-major [m - m0][n], n < n1
-                        float* ph = aux.hi + (int64_t)(m - aux.m0) * aux.ld + n0 + c0;
-                        float* pl = aux.lo + (int64_t)(m - aux.m0) * aux.ld + n0 + c0;
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            if (n0 + c0 + j < N && n0 + c0 + j < aux.n1) {
-                                uint32_t h;
-                                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v[j]));
-                                ph[j] = __uint_as_float(h);
-                                pl[j] = v[j] - __uint_as_float(h);
-                            }
-                        }
+                        if (n < N) C[(int64_t)n * ldc + m] = alpha * __uint_as_float(r[j]) + beta * old[c0 + j];
                     }
                 }
             }
@@ -559,8 +543,7 @@ bool launch_tc_gemm(cudaStream_t st, bool bf16, int split, const CUtensorMap& A,
 // only when tri.  ctas = number of persistent CTAs (at most the tile count).
 bool launch_tc_gemm_persist(cudaStream_t st, int split, const CUtensorMap& A, const CUtensorMap& B,
                             const CUtensorMap* Alo, const CUtensorMap* Blo, int M, int N, int kd, float* C,
-                            int64_t ldc, float alpha, float beta, int tri, int ctas, int* flag, TcAux aux) {
-    if (aux.hi && aux.n1 <= 0) aux.n1 = N;
+                            int64_t ldc, float alpha, float beta, int tri, int ctas, int* flag) {
     if (M <= 0 || N <= 0 || kd <= 0) return true;
     const int64_t MT = (M + BM - 1) / BM, NT = (N + BN - 1) / BN;
     int64_t tiles = 0;
@@ -569,10 +552,10 @@ bool launch_tc_gemm_persist(cudaStream_t st, int split, const CUtensorMap& A, co
     const int grid = (int)std::min<int64_t>(tiles, std::max(1, ctas));
     if (split == 3)
         k_tc_gemm_persist<3, 3><<<grid, kPersistThreads, smem_bytes_persist<3, 3>(), st>>>(A, B, *Alo, *Blo, M, N, kd, C, ldc,
-                                                                              alpha, beta, tri, flag, aux);
+                                                                              alpha, beta, tri, flag);
     else
         k_tc_gemm_persist<1, 4><<<grid, kPersistThreads, smem_bytes_persist<1, 4>(), st>>>(A, B, A, B, M, N, kd, C, ldc, alpha,
-                                                                              beta, tri, flag, aux);
+                                                                              beta, tri, flag);
     return true;
 }
 

@@ -248,16 +248,9 @@ bool launch_tc_gemm(cudaStream_t st, bool bf16, int split, const CUtensorMap& A,
                     float beta, int tri, int* flag, float* aux_hi = nullptr, float* aux_lo = nullptr,
                     int aux_ld = 0, int aux_m0 = 0, int aux_n1 = 0);
 void launch_split_tf32(cudaStream_t st, int64_t n, const float* x, float* hi, float* lo);
-// optional second output of the tensor-core update: the values as TF32 (hi, lo)
-// pairs, row-major [m - m0][n] with row length ld, for m >= m0 and n < n1
-struct TcAux {
-    float* hi = nullptr;
-    float* lo = nullptr;
-    int ld = 0, m0 = 0, n1 = 0;
-};
 bool launch_tc_gemm_persist(cudaStream_t st, int split, const CUtensorMap& A, const CUtensorMap& B,
                             const CUtensorMap* Alo, const CUtensorMap* Blo, int M, int N, int kd, float* C,
-                            int64_t ldc, float alpha, float beta, int tri, int ctas, int* flag, TcAux aux = TcAux());
+                            int64_t ldc, float alpha, float beta, int tri, int ctas, int* flag);
 void init_attrs_tc(int smem_optin);
 
 // mixed precision (k_mixed.cu)
