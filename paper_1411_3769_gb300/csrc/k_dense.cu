@@ -4,71 +4,17 @@
 // memory as a column-major matrix with its lower triangle filled: element
 // (i, j), i >= j, of the column-major view sits at A[j*K + i].  The factor is
 // L with Omega = L L^T, overwriting that lower triangle.  Right-looking blocked
-// algorithm with panels of nb columns (orchestrated in api.cu): (1) factor the
-// nb x nb diagonal block in shared memory and invert it (this file), (2) panel
-// <- panel * L_jj^{-T} as a GEMM with the inverse, (3) symmetric rank-nb
-// update of the trailing lower triangle with the FP64 TN GEMM.  The
-// diagonal-block inverses are kept for the triangular sweeps (k_trsv.cu).
+// algorithm with panels of nb = 32 columns (orchestrated in api.cu): (1) factor
+// the diagonal block in shared memory and invert it (this file), (2) panel <-
+// panel * L_jj^{-T} as a GEMM with the inverse, (3) symmetric rank-32 update of
+// the trailing lower triangle (next panel's rows by the thin GEMM, the rest by
+// the persistent update in k_linalg.cu).  The diagonal-block inverses are kept
+// for the triangular sweeps (k_trsv.cu).
 #include <cmath>
 
 #include "psdp_internal.h"
 
 namespace {
-
-constexpr int kThreads = 256;
-
-__global__ void __launch_bounds__(kThreads)
-k_potrf_diag(double* A, int K, int j0, int w, int nb, double* Linv, int* flag) {
-    extern __shared__ double sm[];
-    const int ld = w + 1;
-    double* L = sm;
-    double* I = sm + (size_t)w * ld;
-    __shared__ int bad;
-    if (threadIdx.x == 0) bad = 0;
-    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
-        const int j = idx / w, i = idx % w;
-        L[j * ld + i] = (i >= j) ? A[(int64_t)(j0 + j) * K + j0 + i] : 0.0;
-    }
-    __syncthreads();
-    for (int j = 0; j < w; ++j) {
-        if (threadIdx.x == 0) {
-            double d = L[j * ld + j];
-            if (!(d > 0.0) || !isfinite(d)) {
-                bad = 1;
-                d = 1.0;
-            }
-            L[j * ld + j] = sqrt(d);
-        }
-        __syncthreads();
-        const double piv = L[j * ld + j];
-        for (int i = j + 1 + threadIdx.x; i < w; i += blockDim.x) L[j * ld + i] /= piv;
-        __syncthreads();
-        const int m = w - j - 1;
-        for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-            const int c = j + 1 + idx / m, r = j + 1 + idx % m;
-            if (r >= c) L[c * ld + r] -= L[j * ld + r] * L[j * ld + c];
-        }
-        __syncthreads();
-    }
-    for (int c = threadIdx.x; c < w; c += blockDim.x) {
-        for (int r = 0; r < c; ++r) I[c * ld + r] = 0.0;
-        for (int r = c; r < w; ++r) {
-            double s = (r == c) ? 1.0 : 0.0;
-            for (int k = c; k < r; ++k) s -= L[k * ld + r] * I[c * ld + k];
-            I[c * ld + r] = s / L[r * ld + r];
-        }
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
-        const int j = idx / w, i = idx % w;
-        if (i >= j) A[(int64_t)(j0 + j) * K + j0 + i] = L[j * ld + i];
-    }
-    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
-        const int j = idx / nb, i = idx % nb;
-        Linv[idx] = (j < w && i < w) ? I[j * ld + i] : 0.0;
-    }
-    if (threadIdx.x == 0 && bad) atomicOr(flag, (int)FL_CHOL_SCHUR);
-}
 
 // Diagonal block of at most 32 columns, four warps, factor and inverse in one
 // sweep with one CTA barrier per column.  On GB300 a dependent FP64 operation
@@ -159,16 +105,10 @@ k_potrf_diag32x4(double* A, int K, int j0, int w, int nb, double* Linv, int* fla
 
 }  // namespace
 
+// nb is the Cholesky's panel width, 32 (the kernel's block size)
 void launch_potrf_diag(cudaStream_t st, double* A, int K, int j0, int nb, double* Linv, int* flag) {
     const int w = (K - j0 < nb) ? K - j0 : nb;
-    if (w <= 32) {
-        k_potrf_diag32x4<<<1, 128, 0, st>>>(A, K, j0, w, nb, Linv, flag);
-        return;
-    }
-    const size_t sm = (size_t)2 * w * (w + 1) * sizeof(double);
-    k_potrf_diag<<<1, kThreads, sm, st>>>(A, K, j0, w, nb, Linv, flag);
+    k_potrf_diag32x4<<<1, 128, 0, st>>>(A, K, j0, w, nb, Linv, flag);
 }
 
-void init_attrs_dense(int smem_max) {
-    set_max_dynamic_smem((const void*)k_potrf_diag, smem_max);
-}
+void init_attrs_dense(int) {}

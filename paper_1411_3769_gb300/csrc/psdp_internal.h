@@ -107,7 +107,7 @@ struct psdp_ctx {
     double *d_Linv64 = nullptr;       // the same paired into 64 x 64 blocks for the sweeps [ceil(K/64)][64][64]
     unsigned *d_trsv_sync = nullptr;  // tickets and ready flags of the triangular sweeps
     int *d_chol_ctr = nullptr;        // tile counters of the persistent FP64 trailing updates, one per panel
-    int nb_chol = 32;
+    int nb_chol = 32;                 // FP64 Cholesky panel width (the diagonal factor's block size)
     double flops_schur = 0, flops_chol = 0, flops_schur_dense = 0;
 
     // ----- misc
