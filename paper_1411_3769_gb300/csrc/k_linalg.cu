@@ -106,6 +106,74 @@ k_bgemm(int n, int count, const double* __restrict__ A, const int32_t* __restric
     }
 }
 
+// n > 32 with a divisor TB in [16, 32]: TB x TB tiles that cover the product
+// exactly (no DFMA on padding: a 100 x 100 product on 32 x 32 tiles issues
+// 128^2/100^2 = 1.64x the useful DFMAs), the TB^2 outputs of a tile packed
+// densely onto the threads (GB300 charges a warp's DFMA whatever its active
+// lanes), k-slabs of TB through shared memory.
+__global__ void __launch_bounds__(kThreads, 2)
+k_bgemm_exact(int n, int tb, int count, const double* __restrict__ A, const int32_t* __restrict__ ia, int sa,
+              int ta, const double* __restrict__ B, const int32_t* __restrict__ ib, int sb, int tb_,
+              double* C, const int32_t* __restrict__ ic, int sc, int tc, double alpha, double beta, const int* skip,
+              int nsum, int qa, int qb) {
+    if (skip && *skip) return;
+    __shared__ double As[BG][BG + 1];   // As[i][k] = op(A)(i0 + i, k0 + k)
+    __shared__ double Bs[BG][BG + 1];   // Bs[k][j] = op(B)(k0 + k, j0 + j)
+    constexpr int RMAX = (BG * BG + kThreads - 1) / kThreads;
+    const int tiles = n / tb, nout = tb * tb;
+    const int i0 = (blockIdx.x / tiles) * tb, j0 = (blockIdx.x % tiles) * tb;
+    const size_t n2 = (size_t)n * n;
+    int oi[RMAX], oj[RMAX];
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+        const int o = threadIdx.x + r * kThreads;
+        oi[r] = o < nout ? o / tb : 0;
+        oj[r] = o < nout ? o - (o / tb) * tb : 0;
+    }
+    for (int e = blockIdx.y; e < count; e += gridDim.y) {
+        const double* Ae = A + (size_t)(ia ? ia[e] : e * sa) * n2;
+        const double* Be = B + (size_t)(ib ? ib[e] : e * sb) * n2;
+        double* Ce = C + (size_t)(ic ? ic[e] : e * sc) * n2;
+        double acc[RMAX];
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) acc[r] = 0.0;
+        for (int q = 0; q < nsum; ++q) {
+            const double* Aq = Ae + (size_t)q * qa * n2;
+            const double* Bq = Be + (size_t)q * qb * n2;
+            for (int k0 = 0; k0 < n; k0 += tb) {
+                for (int idx = threadIdx.x; idx < nout; idx += kThreads) {
+                    const int a = idx / tb, b = idx - (idx / tb) * tb;
+                    // a row, b column of the slab, read along rows of memory
+                    if (!ta) As[a][b] = Aq[(size_t)(i0 + a) * n + k0 + b];
+                    else As[b][a] = Aq[(size_t)(k0 + a) * n + i0 + b];
+                    if (!tb_) Bs[a][b] = Bq[(size_t)(k0 + a) * n + j0 + b];
+                    else Bs[b][a] = Bq[(size_t)(j0 + a) * n + k0 + b];
+                }
+                __syncthreads();
+#pragma unroll
+                for (int r = 0; r < RMAX; ++r) {
+                    if (threadIdx.x + r * kThreads < nout) {
+                        double s = acc[r];
+                        for (int kk = 0; kk < tb; ++kk) s = fma(As[oi[r]][kk], Bs[kk][oj[r]], s);
+                        acc[r] = s;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) {
+            if (threadIdx.x + r * kThreads < nout) {
+                const int i = i0 + oi[r], j = j0 + oj[r];
+                const size_t o = tc ? (size_t)j * n + i : (size_t)i * n + j;
+                double val = alpha * acc[r];
+                if (beta != 0.0) val += beta * Ce[o];
+                Ce[o] = val;
+            }
+        }
+    }
+}
+
 // n <= 32: one CTA per product, one thread per output element and an exact
 // k loop, so no FP64 issue slot is spent on padding (a 32 x 32 tile over a
 // 20 x 20 product would issue 4x the useful DFMAs).
@@ -566,7 +634,7 @@ k_block_chol_inv(int n, const double* __restrict__ Z, double* __restrict__ Y, in
     if (threadIdx.x == 0 && bad) atomicOr(flag, (int)FL_CHOL_BLOCK);
 }
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 k_block_maxstep(int nb, int n, const double* __restrict__ X, const double* __restrict__ dX,
                 const double* __restrict__ Z, const double* __restrict__ dZ, double* tstep, int* flag) {
     extern __shared__ double sm[];
@@ -631,7 +699,7 @@ k_block_maxstep(int nb, int n, const double* __restrict__ X, const double* __res
     }
 }
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 k_block_mineig(int n, const double* __restrict__ M, double sign, double* out) {
     extern __shared__ double sm[];
     const int ld = n + 1;
@@ -688,6 +756,17 @@ void launch_bgemm(cudaStream_t st, int n, int count, const double* A, const int3
         const int threads = (n * n + 31) / 32 * 32;
         k_bgemm_small<<<count < 65535 ? count : 65535, threads, 0, st>>>(n, count, A, ia, sa, ta, B, ib, sb, tb, C, ic,
                                                                          sc, tc, alpha, beta, skip, nsum, qa, qb);
+        return;
+    }
+    int tbx = 0;
+    if (n % BG != 0)
+        for (int d = BG; d >= 16 && !tbx; --d)
+            if (n % d == 0) tbx = d;
+    if (tbx) {
+        const int tiles = n / tbx;
+        dim3 grid(tiles * tiles, count < 65535 ? count : 65535);
+        k_bgemm_exact<<<grid, kThreads, 0, st>>>(n, tbx, count, A, ia, sa, ta, B, ib, sb, tb, C, ic, sc, tc, alpha,
+                                                 beta, skip, nsum, qa, qb);
         return;
     }
     const int tiles = (n + BG - 1) / BG;
