@@ -80,8 +80,9 @@ __device__ __forceinline__ void load_vec_cg(const T* p, T* o) {
 template <typename T>
 constexpr int kPreVals = sizeof(T) == 4 ? 64 : 16;
 
+// the backward sweep keeps the inverse transposed with padded rows, W (W + 1)
 template <typename T>
-size_t trsv_smem(int W) { return ((size_t)W * W + (size_t)(TT / W) * W + W) * sizeof(T); }
+size_t trsv_smem(int W) { return ((size_t)W * (W + 1) + (size_t)(TT / W) * W + W) * sizeof(T); }
 
 // Pairwise sum of v[0], v[stride], ..., v[(G-1) stride] in a fixed order (G a power of two).
 template <typename T, int G>
@@ -310,8 +311,12 @@ k_trsv_bwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, T* x, dou
     constexpr int G2 = TT / W;
     static_assert(32 % R == 0 && W % G == 0 && W % (R * V) == 0, "thread layout");
     extern __shared__ __align__(16) unsigned char smraw[];
-    T* Ls = reinterpret_cast<T*>(smraw);
-    T* red = Ls + W * W;
+    // LsT[r (W + 1) + k] = Linv_p(r, k): the diagonal-block product runs threads
+    // over k, so the row-major copy with a padded row keeps both this fill and
+    // that product free of bank conflicts (the column-major copy put every
+    // thread of a warp in one bank)
+    T* LsT = reinterpret_cast<T*>(smraw);
+    T* red = LsT + W * (W + 1);
     T* acc = red + G2 * W;
     __shared__ int s_ticket, s_q[2];
     const int npanel = (K + W - 1) / W;
@@ -321,7 +326,7 @@ k_trsv_bwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, T* x, dou
     const int p = npanel - 1 - s_ticket, j0 = p * W, w = min(W, K - j0);
     const T* Lp = Linv + (size_t)p * W * W;
 #pragma unroll 8
-    for (int i = threadIdx.x; i < W * W; i += TT) Ls[i] = Lp[i];
+    for (int i = threadIdx.x; i < W * W; i += TT) LsT[(i % W) * (W + 1) + i / W] = Lp[i];
     if (threadIdx.x < W) acc[threadIdx.x] = (threadIdx.x < w) ? ldcg(x + j0 + threadIdx.x) : T(0);   // z_p
     const int cl = (threadIdx.x % R) * V, g = threadIdx.x / R;
     constexpr bool PRE = SEG * RPB * V <= kPreVals<T>;   // as in the forward sweep
@@ -387,7 +392,7 @@ k_trsv_bwd(const T* __restrict__ A, int K, const T* __restrict__ Linv, T* x, dou
     T s = T(0);
     if (k < w)
         for (int rr = g2; rr < w; rr += G2)
-            if (rr >= k) s = fma(Ls[k * W + rr], acc[rr], s);
+            if (rr >= k) s = fma(LsT[rr * (W + 1) + k], acc[rr], s);
     red[g2 * W + k] = s;
     __syncthreads();
     if (threadIdx.x < w) {
