@@ -100,9 +100,13 @@ __global__ void k_schur_pack32(int n, int tpad, const int32_t* __restrict__ term
 constexpr int PB = 32;
 constexpr int kPotrfThreads = 256;
 
+// scratch after L and L^{-1}: the panel's solved rows k-major, [PB][kSLD]
+// (float4-aligned rows of up to 96 solved rows), reused as [3][32][33] by the
+// inverse's off-diagonal levels
+constexpr int kSLD = 100;
 size_t potrf32_smem(int w) {
     const int wp = (w + PB - 1) / PB * PB;
-    return ((size_t)2 * wp * (wp + 1) + 96 * 33) * sizeof(float);
+    return ((size_t)2 * wp * (wp + 1) + PB * kSLD) * sizeof(float);
 }
 
 // Column J of the in-register factor of a 32 x 32 block (lane = row), then
@@ -138,7 +142,7 @@ k_potrf_diag32(float* A, int K, int j0, int w, int nb, float* Linv, float* LtHi,
     const int wp = (w + PB - 1) / PB * PB, ld = wp + 1, nsub = wp / PB;
     float* L = smf;                        // [wp][ld] column-major: L(r, c) = L[c*ld + r]
     float* X = L + (size_t)wp * ld;        // L^{-1}, same layout
-    float* S = X + (size_t)wp * ld;        // [96][33] scratch
+    float* S = X + (size_t)wp * ld;        // [PB][kSLD] scratch, S[k*kSLD + i] = row i of the solved panel
     __shared__ float rinv[128], ldiag[128];
     __shared__ int bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -223,7 +227,7 @@ k_potrf_diag32(float* A, int K, int j0, int w, int nb, float* Linv, float* LtHi,
                     for (int t = 0; t < 4; ++t) acc4[t] = fmaf(bik, X[(c0 + k) * ld + c0 + jg + 8 * t], acc4[t]);
                 }
 #pragma unroll
-                for (int t = 0; t < 4; ++t) S[i * 33 + jg + 8 * t] = acc4[t];
+                for (int t = 0; t < 4; ++t) S[(jg + 8 * t) * kSLD + i] = acc4[t];
             }
             __syncthreads();
             // (d) A22 -= S S^T on the lower 4 x 4 tiles; S back into the panel
@@ -237,12 +241,11 @@ k_potrf_diag32(float* A, int K, int j0, int w, int nb, float* Linv, float* LtHi,
                 float acc[4][4] = {};
 #pragma unroll 4
                 for (int k = 0; k < PB; ++k) {
-                    float a[4], bb[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        a[u] = S[(4 * ti + u) * 33 + k];
-                        bb[u] = S[(4 * tc + u) * 33 + k];
-                    }
+                    // 16-byte reads of four consecutive rows: neighbouring tiles are
+                    // 16 bytes apart, no bank conflict
+                    const float4 a4 = *reinterpret_cast<const float4*>(S + k * kSLD + 4 * ti);
+                    const float4 b4 = *reinterpret_cast<const float4*>(S + k * kSLD + 4 * tc);
+                    const float a[4] = {a4.x, a4.y, a4.z, a4.w}, bb[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -258,7 +261,7 @@ k_potrf_diag32(float* A, int K, int j0, int w, int nb, float* Linv, float* LtHi,
             }
             for (int idx = tid; idx < rest * PB; idx += kPotrfThreads) {
                 const int i = idx % rest, j = idx / rest;
-                L[(c0 + j) * ld + c0 + PB + i] = S[i * 33 + j];
+                L[(c0 + j) * ld + c0 + PB + i] = S[j * kSLD + i];
             }
             __syncthreads();
         }
@@ -269,7 +272,7 @@ k_potrf_diag32(float* A, int K, int j0, int w, int nb, float* Linv, float* LtHi,
         const int npair = nsub - lev;      // pairs (bi, bj) = (q + lev, q)
         // T_q = sum_{k=bj}^{bi-1} L_{bi,k} X_{k,bj}: 64 tiles of 4 x 4 per pair
         for (int idx = tid; idx < npair * 64; idx += kPotrfThreads) {
-            const int q = idx >> 6, tt = idx & 63, tr = tt >> 3, tcl = tt & 7;
+            const int q = idx >> 6, tt = idx & 63, tr = tt & 7, tcl = tt >> 3;
             const int bj = q, bi = q + lev;
             float acc[4][4] = {};
             for (int k = bj * PB; k < bi * PB; ++k) {
@@ -292,7 +295,7 @@ k_potrf_diag32(float* A, int K, int j0, int w, int nb, float* Linv, float* LtHi,
         __syncthreads();
         // X_{bi,bj} = -X_{bi,bi} T_q
         for (int idx = tid; idx < npair * 64; idx += kPotrfThreads) {
-            const int q = idx >> 6, tt = idx & 63, tr = tt >> 3, tcl = tt & 7;
+            const int q = idx >> 6, tt = idx & 63, tr = tt & 7, tcl = tt >> 3;
             const int bj = q, bi = q + lev;
             float acc[4][4] = {};
 #pragma unroll 4
