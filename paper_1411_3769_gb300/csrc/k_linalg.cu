@@ -112,23 +112,23 @@ k_bgemm(int n, int count, const double* __restrict__ A, const int32_t* __restric
 // densely onto the threads (GB300 charges a warp's DFMA whatever its active
 // lanes), k-slabs of TB through shared memory.
 __global__ void __launch_bounds__(kThreads, 2)
-k_bgemm_exact(int n, int tb, int count, const double* __restrict__ A, const int32_t* __restrict__ ia, int sa,
-              int ta, const double* __restrict__ B, const int32_t* __restrict__ ib, int sb, int tb_,
+k_bgemm_exact(int n, int tile, int count, const double* __restrict__ A, const int32_t* __restrict__ ia, int sa,
+              int ta, const double* __restrict__ B, const int32_t* __restrict__ ib, int sb, int tb,
               double* C, const int32_t* __restrict__ ic, int sc, int tc, double alpha, double beta, const int* skip,
               int nsum, int qa, int qb) {
     if (skip && *skip) return;
     __shared__ double As[BG][BG + 1];   // As[i][k] = op(A)(i0 + i, k0 + k)
     __shared__ double Bs[BG][BG + 1];   // Bs[k][j] = op(B)(k0 + k, j0 + j)
     constexpr int RMAX = (BG * BG + kThreads - 1) / kThreads;
-    const int tiles = n / tb, nout = tb * tb;
-    const int i0 = (blockIdx.x / tiles) * tb, j0 = (blockIdx.x % tiles) * tb;
+    const int tiles = n / tile, nout = tile * tile;
+    const int i0 = (blockIdx.x / tiles) * tile, j0 = (blockIdx.x % tiles) * tile;
     const size_t n2 = (size_t)n * n;
     int oi[RMAX], oj[RMAX];
 #pragma unroll
     for (int r = 0; r < RMAX; ++r) {
         const int o = threadIdx.x + r * kThreads;
-        oi[r] = o < nout ? o / tb : 0;
-        oj[r] = o < nout ? o - (o / tb) * tb : 0;
+        oi[r] = o < nout ? o / tile : 0;
+        oj[r] = o < nout ? o - (o / tile) * tile : 0;
     }
     for (int e = blockIdx.y; e < count; e += gridDim.y) {
         const double* Ae = A + (size_t)(ia ? ia[e] : e * sa) * n2;
@@ -140,13 +140,13 @@ k_bgemm_exact(int n, int tb, int count, const double* __restrict__ A, const int3
         for (int q = 0; q < nsum; ++q) {
             const double* Aq = Ae + (size_t)q * qa * n2;
             const double* Bq = Be + (size_t)q * qb * n2;
-            for (int k0 = 0; k0 < n; k0 += tb) {
+            for (int k0 = 0; k0 < n; k0 += tile) {
                 for (int idx = threadIdx.x; idx < nout; idx += kThreads) {
-                    const int a = idx / tb, b = idx - (idx / tb) * tb;
+                    const int a = idx / tile, b = idx - (idx / tile) * tile;
                     // a row, b column of the slab, read along rows of memory
                     if (!ta) As[a][b] = Aq[(size_t)(i0 + a) * n + k0 + b];
                     else As[b][a] = Aq[(size_t)(k0 + a) * n + i0 + b];
-                    if (!tb_) Bs[a][b] = Bq[(size_t)(k0 + a) * n + j0 + b];
+                    if (!tb) Bs[a][b] = Bq[(size_t)(k0 + a) * n + j0 + b];
                     else Bs[b][a] = Bq[(size_t)(j0 + a) * n + k0 + b];
                 }
                 __syncthreads();
@@ -154,7 +154,7 @@ k_bgemm_exact(int n, int tb, int count, const double* __restrict__ A, const int3
                 for (int r = 0; r < RMAX; ++r) {
                     if (threadIdx.x + r * kThreads < nout) {
                         double s = acc[r];
-                        for (int kk = 0; kk < tb; ++kk) s = fma(As[oi[r]][kk], Bs[kk][oj[r]], s);
+                        for (int kk = 0; kk < tile; ++kk) s = fma(As[oi[r]][kk], Bs[kk][oj[r]], s);
                         acc[r] = s;
                     }
                 }
