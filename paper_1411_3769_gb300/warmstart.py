@@ -1,4 +1,4 @@
-"""Learned warm start for a family of Polya SDPs (driver; every computation
+"""Learned warm start for a family of Polya SDPs (orchestration; every computation
 runs in the library: solves, training, inference, start repair).
 
 Family: fixed (n, l, d_p, d1), systems drawn by ``synth.system`` with the
@@ -7,7 +7,7 @@ A_1..A_l; targets are the optimal dual y* (K values) and log(tr(X*_g) / n) per
 block (L + M values).  A prediction becomes a start through ``psdp_set_start``
 (y0, X_g = exp(pred_g) I, Z lifted to lambda_min >= theta / x_g); the plain
 cold start is the fallback whenever the warm-started solve does not end in the
-same kind of outcome, and the cold solve is the judge of every verdict.
+same kind of outcome, and every verdict is checked against the cold solve.
 """
 
 from __future__ import annotations
