@@ -1,4 +1,4 @@
-"""Example 2 of Sec. V on the GPU: the bisection driver over the library
+"""Example 2 of Sec. V on the GPU: the bisection search over the library
 against the oracle's bisection on the same scales (same verdicts, so the same
 bound), and the batched multisection against the same bound."""
 
