@@ -1,6 +1,7 @@
 """Example 2 of Sec. V on the GPU: the bisection search over the library
-against the oracle's bisection on the same scales (same verdicts, so the same
-bound), and the batched multisection against the same bound."""
+against the oracle's bisection (the same verdicts away from the certifiability
+threshold, the same bound to within the band where verdicts near it flip under
+rounding), and the batched multisection against the same bound."""
 
 import numpy as np
 import pytest
