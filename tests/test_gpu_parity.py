@@ -63,7 +63,9 @@ def test_tables_bit_exact(bd, cs):
 
 
 @pytest.mark.parametrize("cs", [dict(n=5, l=2, d_p=1, d1=1), dict(n=7, l=3, d_p=2, d1=2), dict(n=4, l=2, d_p=2, d1=1, d_a=2),
-                                dict(n=20, l=4, d_p=2, d1=3), dict(n=33, l=2, d_p=1, d1=1)])
+                                dict(n=20, l=4, d_p=2, d1=3), dict(n=33, l=2, d_p=1, d1=1),
+                                # exact-tile block products: n = 40 (20 x 20 tiles), 50 (25 x 25)
+                                dict(n=40, l=2, d_p=1, d1=1), dict(n=50, l=3, d_p=1, d1=1)])
 def test_operators_match_oracle(bd, cs):
     cs = dict(cs)
     d_a = cs.pop("d_a", 1)
@@ -83,7 +85,7 @@ def test_operators_match_oracle(bd, cs):
 
 SCHUR_CASES = [dict(n=5, l=2, d_p=1, d1=1), dict(n=6, l=3, d_p=2, d1=2), dict(n=9, l=2, d_p=1, d1=3),
                dict(n=20, l=4, d_p=2, d1=3), dict(n=13, l=3, d_p=0, d1=2), dict(n=3, l=2, d_p=2, d1=1, d_a=2),
-               dict(n=1, l=3, d_p=1, d1=1), dict(n=70, l=1, d_p=0, d1=0)]
+               dict(n=1, l=3, d_p=1, d1=1), dict(n=70, l=1, d_p=0, d1=0), dict(n=40, l=2, d_p=1, d1=1)]
 
 
 @pytest.mark.parametrize("cs", SCHUR_CASES)
