@@ -246,6 +246,13 @@ void* psdp_stream(psdp_ctx* c);
  * Errors: EINVAL on bad sizes/flags, ETIMEOUT if a bounded device wait expired. */
 psdp_status psdp_tc_gemm_check(int M, int N, int K, int dtype, int split, const void* A, const void* B, float* C);
 
+/* Self-test of the bounded device waits (no counterpart in the paper): runs a
+ * triangular sweep in which one block is never solved, so every waiting CTA
+ * gives up after its 2 s limit.  Returns PSDP_ETIMEOUT when the wait gave up as
+ * designed (the context stays usable), PSDP_OK if it did not; waited_ms (may be
+ * NULL) receives the kernel's duration. */
+psdp_status psdp_trsv_timeout_check(float* waited_ms);
+
 /* Self-test of the persistent tcgen05 update used for the FP32 Cholesky trailing
  * update (no counterpart in the paper).  A: M x K, B: N x K row-major float32;
  * C: M x N column-major (C[n*M + m]), in/out.  On every 128 x 128 tile (mt, nt)
@@ -254,32 +261,28 @@ psdp_status psdp_tc_gemm_check(int M, int N, int K, int dtype, int split, const 
  * persistent CTAs (>= 1; fewer CTAs walk more tiles each).  ms (may be NULL)
  * receives the kernel's duration from CUDA events around the launch.  Allocates
  * its own scratch.  Errors: EINVAL on bad sizes, ETIMEOUT if a bounded wait expired. */
-/* Self-test of the bounded device waits (no counterpart in the paper): runs a
- * triangular sweep in which one block is never solved, so every waiting CTA
- * gives up after its 2 s limit.  Returns PSDP_ETIMEOUT when the wait gave up as
- * designed (the context stays usable), PSDP_OK if it did not; waited_ms (may be
- * NULL) receives the kernel's duration. */
-psdp_status psdp_trsv_timeout_check(float* waited_ms);
-
 psdp_status psdp_tc_gemm_persist_check(int M, int N, int K, int split, int tri, int ctas, const float* A,
                                        const float* B, float* C, float* ms);
 
 /* Allocation-free variant of psdp_tc_gemm_check (dtype 0); the paper has no
  * counterpart.  For callers that cannot allocate device memory where they need
- * the product: code inside a CUDA graph capture in global mode, allocator or
- * pool callbacks, hosts with a fixed device budget.
+ * the product: allocator or memory-pool callbacks (an allocation there would
+ * re-enter the allocator) and hosts that give the library a fixed device budget.
  *  A: DEVICE pointer, M x K float32 row-major;  B: DEVICE pointer, N x K;
  *  C: DEVICE pointer receiving D = A B^T column-major (C[n*M + m]), M*N floats;
  *  split: 1 (TF32) or 3 (3xTF32);  stream: cudaStream_t (NULL = legacy stream).
  * The scratch (padded, TF32-split copies of A and B) is one static device array
  * of 8 MiB + 256 B that every GPU loading the library holds until exit, so
  * (M + N) * Kpad must not exceed 2^20, Kpad = K rounded up to 64: larger sizes
- * give EINVAL.  Nothing is allocated: no cudaMalloc/cudaFree, no allocating
- * library routine.  The first call on a device resolves the array's device
- * address and sets the GEMM kernel's shared-memory limit: make it before any
- * stream capture.  Every call shares the array and the call returns after the
- * product is complete on `stream`; calls that overlap on the GPU (other host
- * threads, other streams) race.  Errors: EINVAL, ECUDA, ETIMEOUT (bounded wait). */
+ * give EINVAL before any device work.  Nothing is allocated: no cudaMalloc or
+ * cudaFree, no allocating library routine.  Every call looks up the array's
+ * device address on the current device and sets the GEMM kernel's shared-memory
+ * limit there.  The call is synchronous: it returns after the product is
+ * complete on `stream` (it reads the kernel's timeout flag back), so it cannot
+ * be recorded into a stream capture.  Every call shares the array; calls that
+ * overlap on the GPU (other host threads, other streams) race.  An unread CUDA
+ * error left by earlier work gives ECUDA before anything is enqueued and stays
+ * pending for its owner.  Errors: EINVAL, ECUDA, ETIMEOUT (bounded wait). */
 psdp_status psdp_tc_gemm_noalloc(int M, int N, int K, int split, const float* A, const float* B, float* C,
                                  void* stream);
 

@@ -1,15 +1,14 @@
 // Allocation-free variant of the tensor-core GEMM entry point.
 //
 // Some callers cannot call cudaMalloc at the point where they need the
-// product.  Examples: code running while a CUDA graph is captured in global
-// mode (allocation is illegal there), allocator or memory-pool callbacks, and
-// hosts that hand the library a fixed device budget up front.  This entry point
-// takes device pointers for its inputs and its output.  Its scratch is the
-// 16-byte-padded, TF32-split copy of A and B that the TMA loads read.  That
-// scratch lives in one file-scope device array below, which every GPU that
-// loads the library holds until the process exits.
-#include <mutex>
-
+// product: allocator or memory-pool callbacks (allocating there re-enters the
+// allocator), and hosts that hand the library a fixed device budget up front
+// and account for every byte.  This entry point takes device pointers for its
+// inputs and its output.  Its scratch is the 16-byte-padded, TF32-split copy of
+// A and B that the TMA loads read.  That scratch lives in one file-scope device
+// array below, which every GPU that loads the library holds until the process
+// exits.  The call is synchronous (it reads the kernel's timeout flag back and
+// waits for its stream), so it cannot be recorded into a stream capture.
 #include "psdp_internal.h"
 
 // Largest (M + N) * Kpad the scratch holds, Kpad = K rounded up to 64:
@@ -21,29 +20,19 @@ static __device__ __align__(256) float g_noalloc_scratch[2 * PSDP_NOALLOC_FLOATS
 
 namespace {
 
-std::mutex g_noalloc_mu;
-float* g_noalloc_addr[64] = {};
-
-// Device address of the scratch array for device `dev` (that device current).
-// Resolved once per device; the host-side name of the array is only a stand-in
-// and must never be passed to a kernel.
-psdp_status noalloc_scratch(int dev, float** out) {
-    if (dev < 0 || dev >= 64) return PSDP_EINVAL;
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return PSDP_ECUDA;
-        }
-        int optin = 0;
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        init_attrs_tc(optin);
-        cudaGetLastError();
-        g_noalloc_addr[dev] = static_cast<float*>(p);
-    }
-    *out = g_noalloc_addr[dev];
+// Device address of the scratch array on the current device, looked up on every
+// call (a host-side table lookup), so a context that was reset and re-created
+// never sees a stale address.  The host-side name of the array is only a
+// stand-in and must never be passed to a kernel.  Also sets the GEMM kernels'
+// shared-memory limit on the current device.
+psdp_status noalloc_scratch(float** out) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return PSDP_ECUDA;
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PSDP_ECUDA;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return PSDP_ECUDA;
+    if (set_attrs_tc_gemm_fp32(optin) != cudaSuccess) return PSDP_ECUDA;
+    *out = static_cast<float*>(p);
     return PSDP_OK;
 }
 
@@ -76,19 +65,18 @@ void pack(cudaStream_t st, const float* src, int rows, int k, int kpad, float* h
 
 // Same product as psdp_tc_gemm_check (dtype 0), on device buffers and without
 // allocating: C[n*M + m] = sum_k A[m*K + k] * B[n*K + k].  Synchronous on
-// `stream`.  Calls that overlap on the GPU share the scratch and race.
+// `stream`.  Calls that overlap on the GPU share the scratch and race.  A CUDA
+// error that earlier work left unread is reported as ECUDA before anything is
+// enqueued and is left for its owner to read; a failure of this call's own
+// runtime calls or launches gives ECUDA too.
 extern "C" psdp_status psdp_tc_gemm_noalloc(int M, int N, int K, int split, const float* A, const float* B, float* C,
                                             void* stream) {
     if (M < 1 || N < 1 || K < 1 || !A || !B || !C || (split != 1 && split != 3)) return PSDP_EINVAL;
     const int64_t kpad = ((int64_t)K + 63) / 64 * 64;
     if (((int64_t)M + N) * kpad > PSDP_NOALLOC_FLOATS) return PSDP_EINVAL;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
-        cudaGetLastError();
-        return PSDP_ECUDA;
-    }
+    if (cudaPeekAtLastError() != cudaSuccess) return PSDP_ECUDA;
     float* base = nullptr;
-    const psdp_status s0 = noalloc_scratch(dev, &base);
+    const psdp_status s0 = noalloc_scratch(&base);
     if (s0 != PSDP_OK) return s0;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     float* hiA = base;
@@ -96,18 +84,20 @@ extern "C" psdp_status psdp_tc_gemm_noalloc(int M, int N, int K, int split, cons
     float* loA = base + PSDP_NOALLOC_FLOATS;
     float* loB = loA + (int64_t)M * kpad;
     int* flag = reinterpret_cast<int*>(base + 2 * PSDP_NOALLOC_FLOATS);
-    cudaMemsetAsync(flag, 0, sizeof(int), st);   // the scratch keeps the previous call's contents
-    pack(st, A, M, K, (int)kpad, hiA, split == 3 ? loA : nullptr);
-    pack(st, B, N, K, (int)kpad, hiB, split == 3 ? loB : nullptr);
+    // the scratch keeps the previous call's contents: the timeout flag starts at zero
+    if (cudaMemsetAsync(flag, 0, sizeof(int), st) != cudaSuccess) return PSDP_ECUDA;
     CUtensorMap mA, mB, mAl, mBl;
     bool ok = tc_make_map(&mA, hiA, false, K, M, 1, kpad, 0, 128) && tc_make_map(&mB, hiB, false, K, N, 1, kpad, 0, 128);
     if (ok && split == 3)
         ok = tc_make_map(&mAl, loA, false, K, M, 1, kpad, 0, 128) && tc_make_map(&mBl, loB, false, K, N, 1, kpad, 0, 128);
     if (!ok) return PSDP_ECUDA;
+    pack(st, A, M, K, (int)kpad, hiA, split == 3 ? loA : nullptr);
+    pack(st, B, N, K, (int)kpad, hiB, split == 3 ? loB : nullptr);
     launch_tc_gemm(st, false, split, mA, mB, split == 3 ? &mAl : nullptr, split == 3 ? &mBl : nullptr, M, N, 1, 0,
                    nullptr, K, C, M, 0, 1.f, 0.f, 0, flag);
+    if (cudaGetLastError() != cudaSuccess) return PSDP_ECUDA;   // the three launches above
     int h_flag = 0;
-    cudaMemcpyAsync(&h_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return PSDP_ECUDA;
+    if (cudaMemcpyAsync(&h_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return PSDP_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return PSDP_ECUDA;
     return h_flag ? PSDP_ETIMEOUT : PSDP_OK;
 }

@@ -567,6 +567,20 @@ void init_attrs_tc(int smem_optin) {
     set_max_dynamic_smem((const void*)k_tc_gemm<false, 1, 4>, smem_optin);
 }
 
+// The same limit for the two FP32 forms of k_tc_gemm only, reporting the first
+// failing runtime call instead of clearing it.
+cudaError_t set_attrs_tc_gemm_fp32(int smem_optin) {
+    const void* fns[2] = {(const void*)k_tc_gemm<false, 3, 3>, (const void*)k_tc_gemm<false, 1, 4>};
+    for (const void* f : fns) {
+        cudaFuncAttributes a;
+        cudaError_t e = cudaFuncGetAttributes(&a, f);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin - (int)a.sharedSizeBytes);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 namespace {
 // hi = tf32(x) (round to nearest, ties away), lo = x - hi, both FP32
 __global__ void k_split_tf32(int64_t n, const float* __restrict__ x, float* hi, float* lo) {

@@ -252,6 +252,7 @@ bool launch_tc_gemm_persist(cudaStream_t st, int split, const CUtensorMap& A, co
                             const CUtensorMap* Alo, const CUtensorMap* Blo, int M, int N, int kd, float* C,
                             int64_t ldc, float alpha, float beta, int tri, int ctas, int* flag);
 void init_attrs_tc(int smem_optin);
+cudaError_t set_attrs_tc_gemm_fp32(int smem_optin);
 
 // mixed precision (k_mixed.cu)
 void launch_schur_pack32(cudaStream_t st, psdp_ctx* c);
