@@ -67,14 +67,67 @@ def certified(L, d_p, d1):
     return certify.certify(prob, st.y)["verdict"] == 1, prob, st
 
 
-def oracle_bisect(d_p, d1, lo=-0.2, hi=1.0, iters=10):
+def oracle_bisect(d_p, d1, lo=-0.2, hi=1.0, iters=10, trace=None):
     for _ in range(iters):
         mid = 0.5 * (lo + hi)
-        if certified(mid, d_p, d1)[0]:
+        v = certified(mid, d_p, d1)[0]
+        if trace is not None:
+            trace.append((mid, int(v)))
+        if v:
             hi = mid
         else:
             lo = mid
     return hi
+
+
+def certificate_margin(L, d_p, d1, eps):
+    """Signed margin of the certificate (reading R-A5) at scale L after an oracle
+    solve to tolerance eps: min over every coefficient matrix M of
+    lambda_min(M) - tau_c(M); certified exactly when it is positive."""
+    prob = sdp.Problem(coeffs_on_simplex(L), d_p, d1, d_a=3)
+    _, st = ipm.solve(prob, ipm.Options(eps=eps))
+    coefP, coefL = certify.coefficient_matrices(prob, st.y)
+    return min(float(np.linalg.eigvalsh(M).min()) - certify.tau_c(M) for M in list(coefP) + list(coefL))
+
+
+def verdict_is_determined(L, d_p, d1, eps=1e-8, factor=4.0):
+    """(determined, verdict) at scale L.  The stopping rule accepts any iterate
+    whose gap and residuals are below eps, and at a certified scale near the
+    threshold the margin of the final iterate shrinks with the iterate's distance
+    to the optimum (the optimal dual has a singular Lyapunov coefficient), so two
+    correct solvers can stop on iterates of different verdicts.  The change of the
+    margin when the stopping tolerance moves by one decade (10 eps to eps) measures
+    that dependence; the verdict is determined when the margin at eps exceeds
+    `factor` times it."""
+    m = certificate_margin(L, d_p, d1, eps)
+    m_loose = certificate_margin(L, d_p, d1, 10.0 * eps)
+    return abs(m) > factor * abs(m - m_loose), int(m > 0)
+
+
+def determined_many(points, processes=None):
+    """verdict_is_determined for many (L, d_p, d1) in a process pool started
+    with spawn (safe next to a process that already uses a GPU)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    points = list(points)
+    if not points:
+        return []
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+    os.environ["OMP_NUM_THREADS"] = os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    try:
+        workers = processes or max(1, min(len(points), os.cpu_count() or 1, 16))
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            return list(ex.map(_determined_star, points))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def _determined_star(args):
+    return verdict_is_determined(*args)
 
 
 def test_transcription_reproduces_the_printed_threshold():
