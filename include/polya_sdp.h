@@ -72,7 +72,14 @@ typedef struct {
     int    crit_sms;    /* SMs the persistent Cholesky trailing update leaves to the
                            critical path (panel factor, panel solve, next-rows
                            update); 0 = the default (8 in FP64, 16 in the mixed form) */
+    int    fp64_gemm;   /* engine of the FP64 form's two large contractions, the Schur
+                           complement and the Cholesky trailing updates:
+                           PSDP_GEMM_AUTO (default: by size), PSDP_GEMM_DFMA (FP64 FMA),
+                           PSDP_GEMM_OZAKI (FP64-accurate products from exact BF16
+                           tensor-core slice products, Ozaki et al. 2012) */
 } psdp_opts;
+
+enum { PSDP_GEMM_AUTO = 0, PSDP_GEMM_DFMA = 1, PSDP_GEMM_OZAKI = 2 };
 
 /* Number of doubles psdp_step / psdp_solve write to their info array. */
 #define PSDP_INFO_LEN 16
@@ -289,6 +296,26 @@ psdp_status psdp_tc_gemm_noalloc(int M, int N, int K, int split, const float* A,
 /* Measure this GPU's FP64 FMA throughput with a short dependent-chain kernel;
  * *tflops receives FP64 TFLOP/s (2 flops per FMA). */
 psdp_status psdp_fp64_peak(int device, double* tflops);
+
+/* FP64 throughput of this GPU by two short kernels: *dfma_tflops from
+ * independent FMA chains on the FP64 pipe, *dmma_tflops from the FP64
+ * tensor-core instruction (mma.sync m8n8k4 .f64, 512 flops a warp each).  The
+ * FP64 roofline of the library's kernels takes the larger. */
+psdp_status psdp_fp64_peaks(int device, double* dfma_tflops, double* dmma_tflops);
+
+/* Self-test of the FP64 product by the Ozaki scheme on the BF16 tensor cores
+ * (Ozaki, Ogita, Oishi & Rump 2012; the engine of the FP64 contractions of the
+ * large workloads; no counterpart in the paper).  A: M x K, B: N x K row-major
+ * float64 host arrays, K <= 2048; C: N x M column-major (C[j*M + i]), in/out:
+ * C <- alpha A B^T + beta C, only the elements with i >= j when lower.  Each
+ * row is split into eight BF16 digits of 7 bits below its own power-of-two
+ * scale; the 36 digit-pair products are exact in the tensor cores' FP32
+ * accumulation and are summed in int64 and FP64 (depth windows of 256, summed
+ * in FP64): the error of each element is at most about
+ * K 2^-56 max|A_i| max|B_j| + 2^-52 |(AB^T)_ij| per window.  Allocates its
+ * own scratch.  Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT (bounded wait). */
+psdp_status psdp_ozaki_gemm_check(int M, int N, int K, const double* A, const double* B, double* C, double alpha,
+                                  double beta, int lower);
 
 void psdp_destroy(psdp_ctx* c);
 const char* psdp_strerror(psdp_status s);

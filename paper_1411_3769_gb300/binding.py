@@ -30,14 +30,15 @@ EXPORTS = ("psdp_default_opts", "psdp_setup", "psdp_sizes", "psdp_step", "psdp_s
            "psdp_profile_reset", "psdp_profile_get", "psdp_work", "psdp_stream", "psdp_fp64_peak",
            "psdp_destroy", "psdp_strerror", "psdp_tc_gemm_check", "psdp_tc_gemm_persist_check", "psdp_trsv_timeout_check", "psdp_get_schur_mixed",
            "psdp_tc_gemm_noalloc", "psdp_solve_batch", "psdp_autotune", "psdp_set_start", "psdp_mlp_create",
-           "psdp_mlp_destroy", "psdp_mlp_params", "psdp_mlp_grads", "psdp_mlp_train", "psdp_mlp_predict")
+           "psdp_mlp_destroy", "psdp_mlp_params", "psdp_mlp_grads", "psdp_mlp_train", "psdp_mlp_predict",
+           "psdp_fp64_peaks", "psdp_ozaki_gemm_check")
 
 
 class Opts(C.Structure):
     _fields_ = [("delta", C.c_double), ("delta_L", C.c_double), ("eps", C.c_double), ("sigma", C.c_double),
                 ("tau", C.c_double), ("max_iter", C.c_int), ("d2", C.c_int), ("d_a", C.c_int),
                 ("precision", C.c_int), ("use_graph", C.c_int), ("stream", C.c_void_p), ("device", C.c_int),
-                ("crit_sms", C.c_int)]
+                ("crit_sms", C.c_int), ("fp64_gemm", C.c_int)]
 
 
 class PsdpError(RuntimeError):
@@ -100,6 +101,9 @@ def _lib():
             "psdp_mlp_train": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_float, C.c_uint64,
                                          C.POINTER(C.c_float)]),
             "psdp_mlp_predict": (C.c_int, [vp, vp, C.c_int, vp]),
+            "psdp_fp64_peaks": (C.c_int, [C.c_int, dp, dp]),
+            "psdp_ozaki_gemm_check": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_double, C.c_double,
+                                                C.c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -285,6 +289,26 @@ def psdp_fp64_peak(device: int = 0) -> float:
     v = np.zeros(1)
     _check(_lib().psdp_fp64_peak(device, _dp(v)), "psdp_fp64_peak")
     return float(v[0])
+
+
+def psdp_fp64_peaks(device: int = 0) -> tuple[float, float]:
+    """(DFMA, DMMA) FP64 TFLOP/s of this GPU."""
+    a, b = np.zeros(1), np.zeros(1)
+    _check(_lib().psdp_fp64_peaks(device, _dp(a), _dp(b)), "psdp_fp64_peaks")
+    return float(a[0]), float(b[0])
+
+
+def psdp_ozaki_gemm_check(A: np.ndarray, B: np.ndarray, C0: np.ndarray | None = None, alpha: float = 1.0,
+                          beta: float = 0.0, lower: bool = False) -> np.ndarray:
+    """alpha A B^T + beta C0 (M x N, FP64) through the Ozaki-scheme tensor-core product."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    M, K = A.shape
+    N = B.shape[0]
+    Ct = np.ascontiguousarray((np.zeros((M, N)) if C0 is None else np.asarray(C0, dtype=np.float64)).T)
+    _check(_lib().psdp_ozaki_gemm_check(M, N, K, _dp(A), _dp(B), _dp(Ct), alpha, beta, int(lower)),
+           "psdp_ozaki_gemm_check")
+    return Ct.T
 
 
 def psdp_tc_gemm_check(A: np.ndarray, B: np.ndarray, split: int = 1) -> np.ndarray:

@@ -107,7 +107,25 @@ void enqueue_schur(psdp_ctx* c) {
     }
     for (int p0 = 0; p0 < c->npairs; p0 += c->pairs_per_chunk) {
         const int np = std::min(c->pairs_per_chunk, c->npairs - p0);
-        {
+        if (c->oz_schur) {
+            // T_b[r][c] = sum_k Aop_b[k][r] Bop_b[k][c] by the Ozaki scheme: Bop's rows
+            // are the tile rows (TMEM lanes), so the column-major store is T_b row-major;
+            // depth windows of 256 terms summed in FP64
+            const int dpad = std::min(c->tpad, kOzakiMaxDepth);
+            for (int k0 = 0; k0 < c->tpad; k0 += kOzakiMaxDepth) {
+                {
+                    ProfScope p(c, "schur_oz_split");
+                    launch_ozaki_split(st, c->d_Aop, c->n2, 0, c->d_term_off + p0, c->n2, c->d_term_cnt + p0, 0, k0,
+                                       dpad, np, c->d_oz_sa, c->d_oz_ea);
+                    launch_ozaki_split(st, c->d_Bop, c->n2, 0, c->d_term_off + p0, c->n2, c->d_term_cnt + p0, 0, k0,
+                                       dpad, np, c->d_oz_sb, c->d_oz_eb);
+                }
+                ProfScope p(c, "schur_gemm");
+                launch_ozaki_gemm(st, c->d_oz_sb, c->n2, c->d_oz_eb, c->d_oz_sa, c->n2, c->d_oz_ea, dpad, np,
+                                  c->d_term_cnt + p0, 0, k0, c->d_Tbuf, c->n2, (int64_t)c->n2 * c->n2, 1.0,
+                                  k0 == 0 ? 0.0 : 1.0, 0, c->d_flag);
+            }
+        } else {
             ProfScope p(c, "schur_gemm");
             launch_gemm_tn(st, c->n2, c->n2, np, c->d_Aop, c->n2, c->d_term_off + p0, 0, c->d_Bop, c->n2,
                            c->d_term_off + p0, 0, c->d_term_cnt + p0, 0, c->d_Tbuf, c->n2, (int64_t)c->n2 * c->n2,
@@ -145,7 +163,61 @@ constexpr int kCritSms64 = 8;
 // for the persistent one on 144)
 constexpr int kOneShotWaves = 64;
 
+// Omega = L L^T with the trailing updates by the Ozaki scheme: outer panels of
+// kOzakiMaxDepth (256) columns, each factored as 32-column inner panels by the
+// FP64 kernels (diagonal factor and inverse, panel solve, update of the outer
+// panel's remaining columns), then one FP64-accurate update of the whole
+// trailing matrix of depth 256 from the outer panel's slices.  Every element
+// receives its updates in panel order, and the 32 x 32 diagonal inverses are
+// those the triangular solves use.
+void enqueue_cholesky_ozaki(psdp_ctx* c) {
+    cudaStream_t st = c->stream;
+    const int K = c->K, nb = c->nb_chol, OB = kOzakiMaxDepth;
+    double* A = c->d_Om;
+    for (int J0 = 0; J0 < K; J0 += OB) {
+        const int wo = std::min(OB, K - J0);
+        for (int j0 = J0; j0 < J0 + wo; j0 += nb) {
+            const int w = std::min(nb, K - j0);
+            double* Lp = c->d_Linv + (size_t)(j0 / nb) * nb * nb;
+            {
+                ProfScope q(c, "chol_potrf_diag", st);
+                launch_potrf_diag(st, A, K, j0, nb, Lp, c->d_flag);
+            }
+            const int rest = K - j0 - w;
+            if (rest <= 0) break;
+            double* panel = A + (int64_t)j0 * K + j0 + w;
+            {
+                ProfScope q(c, "chol_trsm_gemm", st);
+                launch_gemm_tn(st, w, rest, 1, Lp, nb, nullptr, 0, panel, K, nullptr, 0, nullptr, w, panel, K, 0, 1.0,
+                               0.0, 0);
+            }
+            const int nrem = J0 + wo - (j0 + w);      // outer-panel columns right of this inner panel
+            if (nrem > 0) {
+                ProfScope q(c, "chol_syrk_next", st);
+                launch_gemm_tn(st, nrem, rest, 1, panel, K, nullptr, 0, panel, K, nullptr, 0, nullptr, w,
+                               A + (int64_t)(j0 + w) * K + j0 + w, K, 0, -1.0, 1.0, 1);
+            }
+        }
+        const int rest = K - (J0 + wo);
+        if (rest <= 0) break;
+        // L(J0+wo+r, J0+k) at P[k*K + r]: rows of the outer panel below it
+        const double* P = A + (int64_t)J0 * K + J0 + wo;
+        const int dpad = (wo + 31) / 32 * 32;
+        {
+            ProfScope q(c, "chol_oz_split", st);
+            launch_ozaki_split(st, P, K, 0, nullptr, rest, nullptr, wo, 0, dpad, 1, c->d_oz_sa, c->d_oz_ea);
+        }
+        ProfScope q(c, "chol_syrk_gemm", st);
+        launch_ozaki_gemm(st, c->d_oz_sa, rest, c->d_oz_ea, c->d_oz_sa, rest, c->d_oz_ea, dpad, 1, nullptr, wo, 0,
+                          A + (int64_t)(J0 + wo) * K + J0 + wo, K, 0, -1.0, 1.0, 1, c->d_flag);
+    }
+}
+
 void enqueue_cholesky(psdp_ctx* c) {
+    if (c->oz_chol) {
+        enqueue_cholesky_ozaki(c);
+        return;
+    }
     cudaStream_t st = c->stream, cs = c->crit;
     const int K = c->K, nb = c->nb_chol;
     double* A = c->d_Om;
@@ -505,7 +577,8 @@ void free_ctx(psdp_ctx* c) {
                     c->d_Tbuf, c->d_Om, c->d_Linv, c->d_Linv64, c->d_chol_ctr, c->d_grid, c->d_svec, c->d_cert, c->d_term_off_t,
                     c->d_opA_hi, c->d_opA_lo, c->d_opB_hi, c->d_opB_lo, c->d_prodA, c->d_prodB, c->d_T32,
                     c->d_Om32, c->d_Linv32, c->d_Pt_hi, c->d_Pt_lo, c->d_z32, c->d_trsv_sync, c->d_Pk_hi, c->d_Pk_lo, c->d_Lt_hi, c->d_Lt_lo, c->d_pcg_x, c->d_pcg_r,
-                    c->d_pcg_z, c->d_pcg_p, c->d_pcg_q, c->d_pcg_state, c->d_pcg_done, c->d_M1, c->d_M2};
+                    c->d_pcg_z, c->d_pcg_p, c->d_pcg_q, c->d_pcg_state, c->d_pcg_done, c->d_M1, c->d_M2,
+                    c->d_oz_sa, c->d_oz_sb, c->d_oz_ea, c->d_oz_eb};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_info) cudaFreeHost(c->h_info);
@@ -629,6 +702,26 @@ psdp_status alloc_fp64(psdp_ctx* c) {
     TRY(dalloc(&c->d_Linv, (size_t)npanel * nbc * nbc));
     TRY(dalloc(&c->d_Linv64, (size_t)((c->K + 63) / 64) * 64 * 64));
     TRY(dalloc(&c->d_chol_ctr, (size_t)npanel));
+    // Ozaki slices: the Schur operands of one chunk of pairs (both sides), or one
+    // outer Cholesky panel's rows, whichever is larger
+    size_t sa = 0, sb = 0, ea = 0;
+    if (c->oz_schur) {
+        const int dpad = std::min(c->tpad, kOzakiMaxDepth);
+        sa = sb = ozaki_slice_elems(c->n2, dpad, c->pairs_per_chunk);
+        ea = (size_t)c->pairs_per_chunk * c->n2;
+    }
+    if (c->oz_chol) {
+        sa = std::max(sa, ozaki_slice_elems(c->K, kOzakiMaxDepth, 1));
+        ea = std::max(ea, (size_t)c->K);
+    }
+    if (sa) {
+        TRY(dalloc(&c->d_oz_sa, sa));
+        TRY(dalloc(&c->d_oz_ea, ea));
+    }
+    if (sb) {
+        TRY(dalloc(&c->d_oz_sb, sb));
+        TRY(dalloc(&c->d_oz_eb, ea));
+    }
     c->have_fp64 = true;
     return PSDP_OK;
 }
@@ -672,6 +765,17 @@ psdp_status alloc_mixed(psdp_ctx* c) {
     return ok ? PSDP_OK : PSDP_ECUDA;
 }
 
+// Engines of the FP64 contractions.  Automatic: the Ozaki scheme where its
+// tiles (128 x 64, depth 256) are well filled and the DFMA work is large: the
+// Cholesky from K >= kOzakiCholMinK, the Schur contraction from n^2 >= 1024
+// (n >= 32); DFMA below.
+constexpr int kOzakiCholMinK = 8192;
+void choose_fp64_engines(psdp_ctx* c) {
+    const int e = c->opt.fp64_gemm;
+    c->oz_chol = e == PSDP_GEMM_OZAKI || (e == PSDP_GEMM_AUTO && c->K >= kOzakiCholMinK);
+    c->oz_schur = e == PSDP_GEMM_OZAKI || (e == PSDP_GEMM_AUTO && c->n2 >= 1024);
+}
+
 psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psdp_opts* o, psdp_ctx** out) {
     psdp_opts opt;
     psdp_default_opts(&opt);
@@ -683,7 +787,8 @@ psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psd
         return PSDP_EINVAL;
     if (!(opt.tau > 0 && opt.tau < 1) || !(opt.sigma >= 0 && opt.sigma < 1) || !(opt.eps > 0) || opt.max_iter < 1 ||
         !std::isfinite(opt.delta) || !std::isfinite(opt.delta_L) ||
-        (opt.precision != PSDP_FP64 && opt.precision != PSDP_MIXED) || opt.crit_sms < 0)
+        (opt.precision != PSDP_FP64 && opt.precision != PSDP_MIXED) || opt.crit_sms < 0 || opt.fp64_gemm < 0 ||
+        opt.fp64_gemm > PSDP_GEMM_OZAKI)
         return PSDP_EINVAL;
     const int64_t Na = hcard(l, d_a), L0 = hcard(l, d_p), L = hcard(l, d_p + d1), M = hcard(l, d_p + d_a + d2);
     const int64_t Nt = (int64_t)n * (n + 1) / 2, K = L0 * Nt;
@@ -701,6 +806,7 @@ psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psd
     init_attrs_tc(smem_max);
     init_attrs_mixed(smem_max);
     init_attrs_trsv(smem_max);
+    init_attrs_ozaki(smem_max);
     cudaGetLastError();
 
     psdp_ctx* c = new (std::nothrow) psdp_ctx();
@@ -790,6 +896,7 @@ psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psd
         for (int r = 0; r + off < n; ++r) { sv.push_back(r); sv.push_back(r + off); }
     cudaMemcpy(c->d_svec, sv.data(), sv.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     if ((s = build_schur_lists(c))) return fail(s);
+    choose_fp64_engines(c);
     if ((s = c->mixed ? alloc_mixed(c) : alloc_fp64(c))) return fail(s);
     launch_identity(st, c->nblk, n, c->d_X);
     launch_identity(st, c->nblk, n, c->d_Z);
@@ -920,6 +1027,7 @@ void psdp_default_opts(psdp_opts* o) {
     o->stream = nullptr;
     o->device = 0;
     o->crit_sms = 0;
+    o->fp64_gemm = PSDP_GEMM_AUTO;
 }
 
 psdp_status psdp_setup(int n, int l, int d_p, int d1, const double* A, const psdp_opts* o, psdp_ctx** out) {
@@ -1417,6 +1525,16 @@ psdp_status psdp_fp64_peak(int device, double* tflops) {
     const double v = fp64_peak_probe(device);
     if (v <= 0) return PSDP_ECUDA;
     *tflops = v;
+    return PSDP_OK;
+}
+
+psdp_status psdp_fp64_peaks(int device, double* dfma_tflops, double* dmma_tflops) {
+    if (!dfma_tflops || !dmma_tflops) return PSDP_EINVAL;
+    const double v = fp64_peak_probe(device);
+    const double w = dmma_peak_probe(device);
+    if (v <= 0 || w <= 0) return PSDP_ECUDA;
+    *dfma_tflops = v;
+    *dmma_tflops = w;
     return PSDP_OK;
 }
 

@@ -743,6 +743,26 @@ __global__ void k_fp64_probe(double* out, int iters, double seed) {
     if (s == 123.456) out[0] = s;   // keeps the chain live
 }
 
+// The same with the FP64 tensor-core instruction (DMMA, m8n8k4): eight
+// independent accumulator fragments per warp, 512 flops per instruction.
+__global__ void k_dmma_probe(double* out, int iters, double seed) {
+    const double a = seed + threadIdx.x * 1e-3, b = 0.5 + threadIdx.x * 1e-4;
+    double d[8][2];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) d[j][0] = d[j][1] = 0.0;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                         : "+d"(d[j][0]), "+d"(d[j][1])
+                         : "d"(a), "d"(b));
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += d[j][0] + d[j][1];
+    if (s == 123.456) out[0] = s;   // keeps the chain live
+}
+
 size_t smem_two_mats(int n) { return (size_t)2 * n * (n + 1) * sizeof(double); }
 
 }  // namespace
@@ -866,6 +886,31 @@ double fp64_peak_probe(int device) {
     cudaFree(out);
     if (cudaGetLastError() != cudaSuccess || ms <= 0.f) return -1.0;
     const double flops = 2.0 * 8.0 * (double)iters * threads * (double)blocks;
+    return flops / (ms * 1e-3) / 1e12;
+}
+
+double dmma_peak_probe(int device) {
+    cudaSetDevice(device);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    double* out = nullptr;
+    if (cudaMalloc(&out, sizeof(double)) != cudaSuccess) return -1.0;
+    const int iters = 2048, threads = 256, blocks = sms * 8;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    k_dmma_probe<<<blocks, threads>>>(out, 64, 1.0);   // warm-up
+    cudaEventRecord(a);
+    k_dmma_probe<<<blocks, threads>>>(out, iters, 1.0);
+    cudaEventRecord(b);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(out);
+    if (cudaGetLastError() != cudaSuccess || ms <= 0.f) return -1.0;
+    const double flops = 512.0 * 8.0 * (double)iters * (threads / 32) * (double)blocks;
     return flops / (ms * 1e-3) / 1e12;
 }
 

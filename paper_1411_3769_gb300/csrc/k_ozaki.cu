@@ -1,0 +1,383 @@
+// FP64 matrix products on the BF16 tensor cores by the Ozaki scheme (Ozaki,
+// Ogita, Oishi & Rump, "Error-free transformations of matrix multiplication by
+// using fast routines of matrix multiplication and its applications", Numer.
+// Algorithms 59, 2012): the operands are split into slices whose products the
+// tensor cores form without rounding error, and the exact slice products are
+// summed in integer and FP64 arithmetic.  GB300's FP64 rate (~1.1 TFLOP/s) is
+// about 1/1700 of its BF16 rate, so the two large FP64 contractions of a Newton
+// step (the Schur complement and the trailing updates of its Cholesky factor)
+// run here at FP64 accuracy.
+//
+// Split.  Row i of an operand (depth Kd <= 256) is scaled by 2^-e_i, where
+// e_i is the exponent with max_k |a_ik| < 2^e_i, and rounded to the integer
+// X = round(a_ik 2^(56 - e_i)), |X| < 2^56.  X is written in balanced base-128
+// digits, X = sum_{p=1..8} s_p 128^(8-p): s_2..s_8 in [-64, 63] and s_1 in
+// [-128, 128].  Every digit is an integer of at most 8 significant bits, so it
+// is exact in BF16, and a_ik = 2^e_i sum_p s_p 2^(-7p) up to 2^(e_i - 57).
+//
+// Product.  sum_k a_ik b_jk = 2^(e_i + f_j) sum_{t=2..9} 2^(-7t) T_t with the
+// level sums T_t = sum_{p+q=t} sum_k s_p(a_ik) s_q(b_jk); the levels t > 9
+// carry less than 2^-63 of the scale and are left out.  Per k a level adds at
+// most 2 * 2^13 + (t - 3) * 2^12 <= 10 * 2^12 in magnitude, so over Kd <= 256
+// every partial sum is an integer below 2^24: the FP32 accumulation of the
+// tensor cores is exact.  Each level has its own TMEM accumulator (8 levels x
+// 64 columns fill the 512 columns of TMEM).
+//
+// Combination (epilogue).  H = T_2 128^2 + T_3 128 + T_4 and
+// L = T_5 128^4 + T_6 128^3 + T_7 128^2 + T_8 128 + T_9 in int64 (exact);
+// D_ij = 2^(e_i + f_j - 28) (H + 2^-35 L), rounded once when L is converted and
+// once in the FMA.  With the split's own rounding the error of D_ij is at most
+// about Kd 2^(e_i + f_j - 56) + 2^-52 |D_ij|, the accuracy of an FP64 GEMM.
+//
+// Tiles: 128 rows (TMEM lanes) x 64 columns; per stage 32 of k for all 8
+// slices of both operands (64-byte swizzled rows, 96 KB), two stages.  Warp 0
+// lane 0 issues the TMA loads, warp 1 lane 0 the 36 slice-pair MMAs per
+// 16-deep k step, all four warps drain TMEM.  Waits are bounded as in the other
+// tcgen05 kernels.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "psdp_internal.h"
+#include "tc_ptx.cuh"
+
+namespace {
+
+constexpr int OZ_S = 8;                         // slices per operand
+constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 32;
+constexpr int OZ_ROW = OZ_BK * 2;               // bytes of one slice row in a stage (64-byte swizzle)
+constexpr int OZ_TA = OZ_BM * OZ_ROW;           // 8 KB
+constexpr int OZ_TB = OZ_BN * OZ_ROW;           // 4 KB
+constexpr int OZ_STAGE = OZ_S * (OZ_TA + OZ_TB);  // 96 KB
+constexpr int OZ_STAGES = 2;
+constexpr int OZ_THREADS = 128;
+constexpr int OZ_SPLIT_THREADS = 256;
+
+constexpr size_t oz_smem_bytes() { return (size_t)OZ_STAGES * OZ_STAGE + 1024 + 8 * (2 * OZ_STAGES + 1) + 16; }
+constexpr size_t oz_split_smem_bytes() { return (size_t)kOzakiMaxDepth * 33 * sizeof(double); }
+
+// shared-memory matrix descriptor: K-major, SWIZZLE_64B (8-row groups of 64-byte rows, 512 B apart)
+__device__ __forceinline__ uint64_t sdesc64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;               // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512 >> 4) << 32;      // stride byte offset
+    d |= (uint64_t)1 << 46;               // descriptor version
+    d |= (uint64_t)4 << 61;               // SWIZZLE_64B
+    return d;
+}
+
+// instruction descriptor: F32 accumulate, BF16 A and B, both K-major, N = 64, M = 128
+constexpr uint32_t oz_idesc() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) | ((uint32_t)(OZ_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// 16 columns of 32 lanes from TMEM, without the wait (the caller waits once)
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+// Depth of batch b in the window [k_off, k_off + kOzakiMaxDepth) of its full depth.
+__device__ __forceinline__ int oz_depth(const int32_t* kdv, int kd_uniform, int b, int k_off) {
+    const int kd = (kdv ? kdv[b] : kd_uniform) - k_off;
+    return kd < 0 ? 0 : (kd > kOzakiMaxDepth ? kOzakiMaxDepth : kd);
+}
+
+// Slices of one batch of operands.  Element (r, k) of batch b is
+// src[off_b + (k_off + k) * ld + r], off_b = src_off[b] if given, else
+// b * src_batch (rows contiguous: a column-major block, or the stacked n x n
+// operand matrices of the Schur contraction); depth window oz_depth <=
+// kOzakiMaxDepth, padded with zeros to dpad.
+// out[(b * 8 + p) * rows * dpad + r * dpad + k] = digit p of (r, k) as BF16;
+// ex[b * rows + r] = e_r.  One CTA per 32 rows: the block is staged in shared
+// memory through coalesced row-contiguous loads, then every thread writes
+// digits along k (contiguous in the output).
+__global__ void __launch_bounds__(OZ_SPLIT_THREADS)
+k_ozaki_split(const double* __restrict__ src, int64_t ld, int64_t src_batch, const int32_t* __restrict__ src_off,
+              int rows, const int32_t* __restrict__ kdv, int kd_uniform, int k_off, int dpad,
+              __nv_bfloat16* __restrict__ out, int32_t* __restrict__ ex) {
+    extern __shared__ double tile[];            // [kd][33]
+    __shared__ int es[32];
+    const int b = blockIdx.y;
+    const int r0 = blockIdx.x * 32;
+    const int kd = oz_depth(kdv, kd_uniform, b, k_off);
+    src += (src_off ? (int64_t)src_off[b] : (int64_t)b * src_batch) + (int64_t)k_off * ld;
+    out += (int64_t)b * OZ_S * rows * dpad;
+    ex += (int64_t)b * rows;
+    for (int idx = threadIdx.x; idx < 32 * kd; idx += OZ_SPLIT_THREADS) {
+        const int k = idx >> 5, rr = idx & 31, r = r0 + rr;
+        tile[k * 33 + rr] = (r < rows) ? src[(int64_t)k * ld + r] : 0.0;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int rr = warp; rr < 32; rr += OZ_SPLIT_THREADS / 32) {
+        double m = 0.0;
+        for (int k = lane; k < kd; k += 32) m = fmax(m, fabs(tile[k * 33 + rr]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) {
+            int e = 0;
+            if (m > 0.0) frexp(m, &e);
+            es[rr] = e;
+            if (r0 + rr < rows) ex[r0 + rr] = e;
+        }
+    }
+    __syncthreads();
+    const int64_t slice = (int64_t)rows * dpad;
+    for (int idx = threadIdx.x; idx < 32 * dpad; idx += OZ_SPLIT_THREADS) {
+        const int rr = idx / dpad, k = idx - rr * dpad, r = r0 + rr;
+        if (r >= rows) continue;
+        const double x = (k < kd) ? tile[k * 33 + rr] : 0.0;
+        long long X = __double2ll_rn(ldexp(x, 56 - es[rr]));
+        int dig[OZ_S];
+#pragma unroll
+        for (int p = OZ_S - 1; p >= 1; --p) {
+            const int d = (int)((X + 64) & 127) - 64;
+            dig[p] = d;
+            X = (X - d) >> 7;
+        }
+        dig[0] = (int)X;
+        __nv_bfloat16* o = out + (int64_t)r * dpad + k;
+#pragma unroll
+        for (int p = 0; p < OZ_S; ++p) o[p * slice] = __float2bfloat16_rn((float)dig[p]);
+    }
+}
+
+// C_b = alpha * D_b + beta * C_b with D_b[i][j] = sum_k A_b[i][k] B_b[j][k] from
+// the slices of A_b (rows i < M) and B_b (rows j < N) over the depth window
+// oz_depth(kd, kd_uniform, b, k_off); C_b[j * ldc + i] (column-major in i).
+// lower: only elements with i >= j, tiles wholly above the diagonal are skipped.
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+k_ozaki_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
+             const int32_t* __restrict__ eA, const int32_t* __restrict__ eB, int M, int N,
+             const int32_t* __restrict__ kd, int kd_uniform, int k_off, double* C, int64_t ldc, int64_t c_batch,
+             double alpha, double beta, int lower, int* flag) {
+    extern __shared__ uint8_t smem_raw[];
+    const int nt = blockIdx.x, mt = blockIdx.y, b = blockIdx.z;
+    const int m0 = mt * OZ_BM, n0 = nt * OZ_BN;
+    if (lower && m0 + OZ_BM - 1 < n0) return;
+    const uint32_t base_raw = smem_u32(smem_raw);
+    const uint32_t base = (base_raw + 1023u) & ~1023u;
+    uint8_t* gbase = smem_raw + (base - base_raw);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + OZ_STAGES * OZ_STAGE);
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * OZ_STAGES + 1);
+    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * OZ_STAGES, accb = full0 + 16 * OZ_STAGES;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int Kd = oz_depth(kd, kd_uniform, b, k_off);
+    const int nk = (Kd + OZ_BK - 1) / OZ_BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < OZ_STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(accb, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(8 * OZ_BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_holder;
+
+    if (nk > 0) {
+        if (warp == 0 && lane == 0) {
+            // TMA producer: every slice of both operands for 32 of k per stage
+            int kt = 0;
+            for (; kt < nk; ++kt) {
+                const int s = kt & 1;
+                if (kt >= OZ_STAGES && !mbar_wait(empty0 + 8 * s, ((kt >> 1) - 1) & 1, flag)) break;
+                const uint32_t st = base + s * OZ_STAGE;
+                const uint32_t fb = full0 + 8 * s;
+                mbar_expect_tx(fb, OZ_STAGE);
+#pragma unroll
+                for (int p = 0; p < OZ_S; ++p) tma_load_3d(st + p * OZ_TA, &mA, fb, kt * OZ_BK, m0, b * OZ_S + p);
+#pragma unroll
+                for (int q = 0; q < OZ_S; ++q)
+                    tma_load_3d(st + OZ_S * OZ_TA + q * OZ_TB, &mB, fb, kt * OZ_BK, n0, b * OZ_S + q);
+            }
+            // every issued stage has landed before the CTA may exit
+            for (int q = (kt > OZ_STAGES ? kt - OZ_STAGES : 0); q < kt; ++q)
+                mbar_wait(full0 + 8 * (q & 1), (q >> 1) & 1, flag);
+        } else if (warp == 1 && lane == 0) {
+            // MMA issuer: level t = p + q + 2 (0-based slices) accumulates in TMEM columns [64 (t-2), 64 (t-1))
+            constexpr uint32_t idesc = oz_idesc();
+            int kt = 0;
+            for (; kt < nk; ++kt) {
+                const int s = kt & 1;
+                if (!mbar_wait(full0 + 8 * s, (kt >> 1) & 1, flag)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t st = base + s * OZ_STAGE;
+#pragma unroll
+                for (int kk = 0; kk < OZ_ROW / 32; ++kk) {
+#pragma unroll
+                    for (int p = 0; p < OZ_S; ++p) {
+#pragma unroll
+                        for (int q = 0; q < OZ_S - p; ++q) {
+                            const uint32_t acc = (kt > 0 || kk > 0 || p > 0) ? 1u : 0u;
+                            mma_bf16(tmem + (uint32_t)(OZ_BN * (p + q)), sdesc64(st + p * OZ_TA + kk * 32),
+                                     sdesc64(st + OZ_S * OZ_TA + q * OZ_TB + kk * 32), idesc, acc);
+                        }
+                    }
+                }
+                mma_commit(empty0 + 8 * s);
+            }
+            mma_commit(accb);
+        }
+    }
+    __syncwarp();
+    bool ok = true;
+    if (nk > 0) ok = mbar_wait(accb, 0, flag);
+    // warp-uniform decision: the TMEM loads below are warp-collective; after a
+    // timeout (FL_TIMEOUT raised) C is left as it is
+    ok = __all_sync(0xffffffffu, ok);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int i = m0 + 32 * warp + lane;
+        const int ei = (i < M) ? eA[(int64_t)b * M + i] : 0;
+        double* Cb = C + (int64_t)b * c_batch;
+        const int32_t* eBb = eB + (int64_t)b * N;
+#pragma unroll 1
+        for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
+            uint32_t r[OZ_S][16];
+            if (nk > 0) {
+#pragma unroll
+                for (int t = 0; t < OZ_S; ++t)
+                    tmem_ld16_nw(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(OZ_BN * t + c0), r[t]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            } else {
+#pragma unroll
+                for (int t = 0; t < OZ_S; ++t)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) r[t][j] = 0u;
+            }
+            if (i < M) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = n0 + c0 + j;
+                    if (col >= N || (lower && i < col)) continue;
+                    long long T[OZ_S];
+#pragma unroll
+                    for (int t = 0; t < OZ_S; ++t) T[t] = (long long)__float2int_rn(__uint_as_float(r[t][j]));
+                    const long long H = T[0] * 16384 + T[1] * 128 + T[2];
+                    const long long L = T[3] * 268435456LL + T[4] * 2097152LL + T[5] * 16384 + T[6] * 128 + T[7];
+                    const double v = fma((double)L, 0x1p-35, (double)H);
+                    const double w = ldexp(v, ei + eBb[col] - 28);
+                    double* cp = Cb + (int64_t)col * ldc + i;
+                    *cp = (beta == 0.0) ? alpha * w : fma(alpha, w, beta * *cp);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(8 * OZ_BN));
+    }
+}
+
+}  // namespace
+
+void init_attrs_ozaki(int smem_optin) {
+    set_max_dynamic_smem((const void*)k_ozaki_gemm, smem_optin);
+    set_max_dynamic_smem((const void*)k_ozaki_split, smem_optin);
+}
+
+size_t ozaki_slice_elems(int rows, int dpad, int batch) { return (size_t)batch * OZ_S * rows * dpad; }
+
+void launch_ozaki_split(cudaStream_t st, const double* src, int64_t ld, int64_t src_batch, const int32_t* src_off,
+                        int rows, const int32_t* kdv, int kd_uniform, int k_off, int dpad, int batch, uint16_t* out_bits,
+                        int32_t* ex) {
+    __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(out_bits);
+    if (rows <= 0 || batch <= 0) return;
+    dim3 grid((rows + 31) / 32, batch);
+    k_ozaki_split<<<grid, OZ_SPLIT_THREADS, oz_split_smem_bytes(), st>>>(src, ld, src_batch, src_off, rows, kdv,
+                                                                         kd_uniform, k_off, dpad, out, ex);
+}
+
+bool launch_ozaki_gemm(cudaStream_t st, const uint16_t* As, int M, const int32_t* eA, const uint16_t* Bs, int N,
+                       const int32_t* eB, int dpad, int batch, const int32_t* kd, int kd_uniform, int k_off, double* C,
+                       int64_t ldc, int64_t c_batch, double alpha, double beta, int lower, int* flag) {
+    if (M <= 0 || N <= 0 || batch <= 0) return true;
+    if (dpad % OZ_BK != 0 || dpad > kOzakiMaxDepth) return false;
+    CUtensorMap mA, mB;
+    if (!tc_make_map_swz(&mA, As, true, dpad, M, (int64_t)batch * OZ_S, dpad, (int64_t)M * dpad, OZ_BK, OZ_BM, 64) ||
+        !tc_make_map_swz(&mB, Bs, true, dpad, N, (int64_t)batch * OZ_S, dpad, (int64_t)N * dpad, OZ_BK, OZ_BN, 64))
+        return false;
+    dim3 grid((N + OZ_BN - 1) / OZ_BN, (M + OZ_BM - 1) / OZ_BM, batch);
+    k_ozaki_gemm<<<grid, OZ_THREADS, oz_smem_bytes(), st>>>(mA, mB, eA, eB, M, N, kd, kd_uniform, k_off, C, ldc,
+                                                             c_batch, alpha, beta, lower, flag);
+    return true;
+}
+
+// Self-test on host data: C (N x M column-major, C[j*M + i]) = alpha A B^T + beta C
+// with A: M x K, B: N x K row-major FP64, K <= kOzakiMaxDepth.
+extern "C" psdp_status psdp_ozaki_gemm_check(int M, int N, int K, const double* A, const double* B, double* C,
+                                             double alpha, double beta, int lower) {
+    if (M < 1 || N < 1 || K < 1 || K > 8 * kOzakiMaxDepth || !A || !B || !C) return PSDP_EINVAL;
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PSDP_ECUDA;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    init_attrs_ozaki(optin);
+    const int dpad = (std::min(K, kOzakiMaxDepth) + OZ_BK - 1) / OZ_BK * OZ_BK;
+    // the split reads (row, k) at k * rows + row: transpose on the host
+    std::vector<double> At((size_t)K * M), Bt((size_t)K * N);
+    for (int i = 0; i < M; ++i)
+        for (int k = 0; k < K; ++k) At[(size_t)k * M + i] = A[(size_t)i * K + k];
+    for (int j = 0; j < N; ++j)
+        for (int k = 0; k < K; ++k) Bt[(size_t)k * N + j] = B[(size_t)j * K + k];
+    double *dA = nullptr, *dB = nullptr, *dC = nullptr;
+    uint16_t *sA = nullptr, *sB = nullptr;
+    int32_t *eA = nullptr, *eB = nullptr;
+    int* dflag = nullptr;
+    psdp_status s = PSDP_OK;
+    auto al = [&](void** p, size_t bytes) { if (cudaMalloc(p, bytes) != cudaSuccess) s = PSDP_ENOMEM; };
+    al((void**)&dA, At.size() * 8);
+    al((void**)&dB, Bt.size() * 8);
+    al((void**)&dC, (size_t)M * N * 8);
+    al((void**)&sA, ozaki_slice_elems(M, dpad, 1) * 2);
+    al((void**)&sB, ozaki_slice_elems(N, dpad, 1) * 2);
+    al((void**)&eA, (size_t)M * 4);
+    al((void**)&eB, (size_t)N * 4);
+    al((void**)&dflag, 4);
+    if (s == PSDP_OK) {
+        cudaMemcpy(dA, At.data(), At.size() * 8, cudaMemcpyHostToDevice);
+        cudaMemcpy(dB, Bt.data(), Bt.size() * 8, cudaMemcpyHostToDevice);
+        cudaMemcpy(dC, C, (size_t)M * N * 8, cudaMemcpyHostToDevice);
+        cudaMemset(dflag, 0, 4);
+        // depth windows of 256: each window's product is exact, the windows are summed in FP64
+        for (int k0 = 0; k0 < K && s == PSDP_OK; k0 += kOzakiMaxDepth) {
+            launch_ozaki_split(0, dA, M, 0, nullptr, M, nullptr, K, k0, dpad, 1, sA, eA);
+            launch_ozaki_split(0, dB, N, 0, nullptr, N, nullptr, K, k0, dpad, 1, sB, eB);
+            if (!launch_ozaki_gemm(0, sA, M, eA, sB, N, eB, dpad, 1, nullptr, K, k0, dC, M, 0, alpha,
+                                   k0 == 0 ? beta : 1.0, lower, dflag))
+                s = PSDP_ECUDA;
+        }
+        int hflag = 0;
+        if (cudaDeviceSynchronize() != cudaSuccess) s = PSDP_ECUDA;
+        cudaMemcpy(&hflag, dflag, 4, cudaMemcpyDeviceToHost);
+        if (s == PSDP_OK && hflag) s = PSDP_ETIMEOUT;
+        if (s == PSDP_OK) cudaMemcpy(C, dC, (size_t)M * N * 8, cudaMemcpyDeviceToHost);
+    }
+    cudaFree(dA); cudaFree(dB); cudaFree(dC); cudaFree(sA); cudaFree(sB); cudaFree(eA); cudaFree(eB); cudaFree(dflag);
+    if (cudaGetLastError() != cudaSuccess && s == PSDP_OK) s = PSDP_ECUDA;
+    return s;
+}

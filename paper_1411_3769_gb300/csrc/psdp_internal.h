@@ -108,6 +108,10 @@ struct psdp_ctx {
     unsigned *d_trsv_sync = nullptr;  // tickets and ready flags of the triangular sweeps
     int *d_chol_ctr = nullptr;        // tile counters of the persistent FP64 trailing updates, one per panel
     int nb_chol = 32;                 // FP64 Cholesky panel width (the diagonal factor's block size)
+    // ----- Ozaki-scheme FP64 products (BF16 tensor-core slices)
+    bool oz_chol = false, oz_schur = false;   // engines chosen at set-up
+    uint16_t *d_oz_sa = nullptr, *d_oz_sb = nullptr;   // slices [batch][8][rows][dpad]
+    int32_t *d_oz_ea = nullptr, *d_oz_eb = nullptr;    // row exponents [batch][rows]
     double flops_schur = 0, flops_chol = 0, flops_schur_dense = 0;
 
     // ----- misc
@@ -238,10 +242,13 @@ void launch_grid_build(cudaStream_t st, psdp_ctx* c, int N, int64_t first, int c
 
 // FP64 throughput probe
 double fp64_peak_probe(int device);
+double dmma_peak_probe(int device);
 
 // tensor-core GEMM (k_tc_gemm.cu)
 bool tc_make_map(CUtensorMap* map, const void* base, bool bf16, int64_t kdim, int64_t rows, int64_t batch,
                  int64_t row_stride, int64_t batch_stride, int box_rows);
+bool tc_make_map_swz(CUtensorMap* map, const void* base, bool bf16, int64_t kdim, int64_t rows, int64_t batch,
+                     int64_t row_stride, int64_t batch_stride, int box_k, int box_rows, int swizzle_bytes);
 bool launch_tc_gemm(cudaStream_t st, bool bf16, int split, const CUtensorMap& A, const CUtensorMap& B,
                     const CUtensorMap* Alo, const CUtensorMap* Blo, int M, int N, int batch, int b0,
                     const int32_t* kd, int kd_uniform, float* C, int64_t ldc, int64_t c_batch, float alpha,
@@ -253,6 +260,25 @@ bool launch_tc_gemm_persist(cudaStream_t st, int split, const CUtensorMap& A, co
                             int64_t ldc, float alpha, float beta, int tri, int ctas, int* flag);
 void init_attrs_tc(int smem_optin);
 cudaError_t set_attrs_tc_gemm_fp32(int smem_optin);
+
+// FP64 products by the Ozaki scheme on the BF16 tensor cores (k_ozaki.cu).
+// Slices: 8 BF16 digits per element, [batch][8][rows][dpad] (uint16 bit
+// patterns), row exponents [batch][rows]; depth <= kOzakiMaxDepth, dpad a
+// multiple of 32.
+constexpr int kOzakiMaxDepth = 256;
+void init_attrs_ozaki(int smem_optin);
+size_t ozaki_slice_elems(int rows, int dpad, int batch);
+// Each call covers the depth window [k_off, k_off + kOzakiMaxDepth) of every batch
+// (depths per batch from kdv, else kd_uniform); deeper products sum the windows
+// with beta = 1.  Split: element (r, k) of batch b at src[off_b + k * ld + r],
+// off_b = src_off[b] (elements) if given, else b * src_batch.
+void launch_ozaki_split(cudaStream_t st, const double* src, int64_t ld, int64_t src_batch, const int32_t* src_off,
+                        int rows, const int32_t* kdv, int kd_uniform, int k_off, int dpad, int batch, uint16_t* out,
+                        int32_t* ex);
+// C_b[j * ldc + i] = alpha sum_k A_b[i][k] B_b[j][k] + beta C_b[...] (i >= j only when lower)
+bool launch_ozaki_gemm(cudaStream_t st, const uint16_t* As, int M, const int32_t* eA, const uint16_t* Bs, int N,
+                       const int32_t* eB, int dpad, int batch, const int32_t* kd, int kd_uniform, int k_off, double* C,
+                       int64_t ldc, int64_t c_batch, double alpha, double beta, int lower, int* flag);
 
 // mixed precision (k_mixed.cu)
 void launch_schur_pack32(cudaStream_t st, psdp_ctx* c);

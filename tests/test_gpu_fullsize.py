@@ -1,0 +1,155 @@
+"""Element-wise parity of whole Newton steps at sizes that reach the library's
+full-size code paths, and batched solves of instances shaped like the
+512-instance batch workload.
+
+* The mid workload (n=20, l=4, d_p=2, d1=3: K = 2100) runs the FP64 Cholesky's
+  66 panels with look-ahead, the persistent bulk trailing update, the 64 x 64
+  pair inverses and the 64-row flag-synchronised sweeps.
+* n=40, l=3, d_p=2, d1=1 (K = 4920): the early trailing matrices have more than
+  64 waves of 32 x 32 tiles, so the bulk update takes the one-shot tiled kernel
+  there and the persistent one later.
+From the same iterate (the oracle's k-th, loaded through the C ABI) one step of
+the library must match one step of the oracle (Sec. IV-A, Algorithm 2) to the
+1e-8 relative bound of the small-size step test: the step solves Omega dy = r
+(kappa(Omega) <= ~1e5 along these solves) and the rest is FP64 with another
+summation order.
+
+Batches: 20 uneven instances drawn like the batch workload (n 8..48, l 2..4,
+every d_p in {1, 2} and d1 in {1..4}, K up to 7410) must give bit-identical
+results to single solves; verdicts equal the oracle's solve where K <= 1500 (and
+the oracle's certificate margin is not within 100 x the stopping tolerance of
+zero) and, at every size, the oracle's certificate of the library's own y.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import certify, ipm, sdp
+from paper_1411_3769_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bd():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1411_3769_gb300 import build
+    build.build()
+    from paper_1411_3769_gb300 import binding
+    binding._lib()
+    return binding
+
+
+def _rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+
+def _step_parity(bd, A, d_p, d1, ks):
+    n, l = A.shape[-1], A.shape[0]
+    prob = sdp.Problem(A, d_p, d1)
+    st = ipm.start_point(prob)
+    h = bd.psdp_setup(n, l, d_p, d1, A)
+    try:
+        assert bd.psdp_sizes(h)["K"] == prob.K
+        done = 0
+        for k in ks:
+            while done < k:
+                assert ipm.newton_step(prob, st, ipm.Options())["status"] == ipm.OK
+                done += 1
+            bd.psdp_load_iterate(h, st.X, st.Z, st.y)
+            info_o = ipm.newton_step(prob, st, ipm.Options())
+            done += 1
+            s, info = bd.psdp_step(h)
+            assert s == 0
+            X, Z, y = bd.psdp_get_iterate(h)
+            assert abs(info[6] - info_o["tp"]) <= 1e-8 and abs(info[7] - info_o["td"]) <= 1e-8, k
+            assert _rel(y, st.y) <= 1e-8, k
+            assert _rel(X, st.X) <= 1e-8, k
+            assert _rel(Z, st.Z) <= 1e-8, k
+            sc = ipm.scalars(prob, st)
+            assert abs(info[0] - sc["phi"]) <= 1e-8 * (1 + abs(sc["phi"]))
+            assert abs(info[1] - sc["psi"]) <= 1e-8 * (1 + abs(sc["psi"]))
+    finally:
+        bd.psdp_destroy(h)
+
+
+def test_mid_newton_steps_match_oracle(bd):
+    w = synth.WORKLOADS["mid"]
+    _step_parity(bd, synth.system(w["n"], w["l"], w["s"], 0), w["d_p"], w["d1"], ks=(2, 10))
+
+
+def test_one_shot_bulk_update_newton_step_matches_oracle(bd):
+    A = synth.system(40, 3, 0.3, 3)
+    _step_parity(bd, A, 2, 1, ks=(1,))
+
+
+def _oracle_solve_verdict(args):
+    A, d_p, d1 = args
+    prob = sdp.Problem(A, d_p, d1)
+    status, st = ipm.solve(prob, ipm.Options(max_iter=60))
+    c = certify.certify(prob, st.y)
+    return status, c["verdict"], min(c["minP_margin"], -c["maxLyap_margin"])
+
+
+def test_batch_shaped_like_the_batch_workload(bd):
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+
+    inst = synth.batch_instances(20, base_seed=4160)
+    Ks = [sdp.Problem(d["A"], d["d_p"], d["d1"]).K for d in inst]
+    assert {d["d_p"] for d in inst} == {1, 2} and {d["d1"] for d in inst} == {1, 2, 3, 4}
+    assert max(Ks) > 5000
+    small = [i for i, K in enumerate(Ks) if K <= 1500]
+    # the oracle's own solves of the small instances, in spawned processes
+    # one BLAS thread per worker: the workers start at the first submit and read
+    # the variables when they load numpy
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        pool = cf.ProcessPoolExecutor(max_workers=min(len(small), os.cpu_count() or 1, 16),
+                                      mp_context=mp.get_context("spawn"))
+        futs = {i: pool.submit(_oracle_solve_verdict, (inst[i]["A"], inst[i]["d_p"], inst[i]["d1"])) for i in small}
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    handles = []
+    try:
+        for d in inst:
+            handles.append(bd.psdp_setup(d["n"], d["l"], d["d_p"], d["d1"], d["A"], bd.psdp_default_opts(max_iter=60)))
+        status, iters = bd.psdp_solve_batch(handles)
+        ys = [bd.psdp_get_y(h) for h in handles]
+        verdicts = [bd.psdp_certify(h)[0] for h in handles]
+    finally:
+        for h in handles:
+            bd.psdp_destroy(h)
+    for i, d in enumerate(inst):
+        with bd.Solver(d["A"], d["d_p"], d["d1"], max_iter=60) as s:
+            st1, it1, _ = s.solve()
+            y1 = bd.psdp_get_y(s.h)
+            v1 = s.certify()[0]
+        assert (status[i], iters[i]) == (st1, it1), i
+        assert np.array_equal(ys[i], y1), i
+        assert verdicts[i] == v1, i
+        prob = sdp.Problem(d["A"], d["d_p"], d["d1"])
+        cert = certify.certify(prob, ys[i])
+        assert verdicts[i] == cert["verdict"], i
+        if verdicts[i] == 1:
+            assert certify.grid_check(prob, ys[i], 6)["ok"], i
+    try:
+        for i in small:
+            st_o, v_o, m_o = futs[i].result()
+            # near the certifiability threshold the margin of a stopping iterate is
+            # of the order of the tolerance and the verdict depends on where a
+            # correct solver stops (reading R-A5); compare where it is 100 x larger
+            if abs(m_o) > 100 * 1e-7:
+                assert verdicts[i] == v_o, (i, status[i], st_o)
+    finally:
+        pool.shutdown()
