@@ -1,12 +1,22 @@
 #!/usr/bin/env python3
-"""Benchmark: Newton steps/s of the Polya/SDP interior-point method on one GB300.
+"""Benchmark: Newton steps/s and time-to-certificate of the Polya/SDP
+interior-point method on one GB300.
 
-Workload: the mid-size system n=20, l=4, d_p=2, d1=d2=3 (K=2100 dual
-variables, 56 + 84 blocks of 20 x 20), s=0.3, seed 0 of the synthetic
-generator.  One "step" is one full predictor-corrector Newton step (Schur
+Headline workload: the large system n=100, l=3, d_p=2, d1=d2=4 (K=30300 dual
+variables, 28 + 36 blocks of 100 x 100), s=0.3, seed 0 of the synthetic
+generator, in FP64: every result FP64-accurate, the two large contractions
+(Schur complement, Cholesky trailing updates) by the Ozaki scheme on the BF16
+tensor cores.  One "step" is one full predictor-corrector Newton step (Schur
 assembly, dense Cholesky, both solves, directions, step length, update,
-scalars) from the cold start X = Z = I, y = 0, which is restored (untimed)
-before every timed step together with an L2 flush.
+scalars) from the cold start X = Z = I, y = 0, restored (untimed) before every
+timed step; the 7.3 GB Schur complement is rewritten every step (inputs far
+larger than L2), and a 256 MB L2 flush precedes each step as well.
+
+Also reported: the same step with FP64 FMA only (DFMA), the mixed-precision
+form (steps/s, time-to-certificate, speedup over the measured FP64
+time-to-certificate), the mid workload (n=20, l=4, d_p=2, d1=3, K=2100) in
+FP64 as a second record, the oracle on a bounded sample of the headline
+workload on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -30,30 +40,31 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(name="mid", n=20, l=4, d_p=2, d1=3, s=0.3, seed=0)
-METRIC = "Newton steps/s (plain FP64 path; time-to-certificate in e2e)"
+WORKLOAD = dict(name="large", n=100, l=3, d_p=2, d1=4, s=0.3, seed=0)
+MID = dict(name="mid", n=20, l=4, d_p=2, d1=3, s=0.3, seed=0)
+METRIC = "Newton steps/s at FP64 accuracy (time-to-certificate in e2e; mixed-precision speedup in mixed)"
 UNIT = "steps/s"
 NOMINAL_BF16_TFLOPS = 2250.0
-NOMINAL_FP64_TFLOPS = 1.25
-# DRAM read + write bytes per bulk trailing-update launch (mean over the 64
-# launches of one mid-workload step), from one ncu capture of the current
-# k_syrk_tri_persist revision; None until that capture is taken again after a
-# change
-CHOL_BULK_DRAM_BYTES = 6.14e6
-KERNEL_OF = {"schur_gemm": "k_gemm_tn", "chol_syrk_gemm": "k_syrk_tri_persist"}
+NOMINAL_TF32_TFLOPS = 1100.0
+# BF16 slice products per FP64 multiply-add in the Ozaki scheme (8 slices, levels <= 9)
+OZ_PAIRS = 36
+OZ_DEPTH = 256
+KERNEL_OF = {"schur_gemm": "k_gemm_tn", "chol_syrk_gemm": "k_syrk_tri_persist", "oz_chol": "k_ozaki_gemm",
+             "oz_schur": "k_ozaki_gemm", "chol32_syrk_tc": "k_tc_gemm_persist"}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-runs", type=int, default=2)
-    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--cpu-samples", type=int, default=2, help="oracle samples of the headline step on the host")
     ap.add_argument("--mixed", type=int, default=1, help="also measure the mixed-precision path")
     ap.add_argument("--mixed-steps", type=int, default=5)
-    ap.add_argument("--fp64-large", type=int, default=1, help="time one plain FP64 step of the large workload")
+    ap.add_argument("--dfma", type=int, default=1, help="time one FP64-FMA-only step of the headline workload")
+    ap.add_argument("--mid", type=int, default=1, help="also measure the mid workload in FP64")
+    ap.add_argument("--mid-steps", type=int, default=30)
     ap.add_argument("--mixed-workloads", default="mid,large")
     ap.add_argument("--extra-items", default="err,ex2,syrk,batch,warm")
     ap.add_argument("--err-large", type=int, default=1, help="also solve the large workload in plain FP64")
@@ -213,6 +224,33 @@ def chol_flops(K, nb):
     return out
 
 
+def chol_flops_ozaki(K, nb=32, ob=OZ_DEPTH):
+    """Algorithmic flops of one FP64 Cholesky with Ozaki-scheme trailing updates, by
+    kernel: 32-column panel solves (trsm), updates of the outer panel's remaining
+    columns (inner, FP64 FMA), the depth-256 update of the next outer panel's
+    columns (next) and of the rest of the trailing matrix (bulk), lower parts."""
+    out = {"trsm": 0.0, "inner": 0.0, "next": 0.0, "bulk": 0.0}
+    for J0 in range(0, K, ob):
+        wo = min(ob, K - J0)
+        for j0 in range(J0, J0 + wo, nb):
+            w = min(nb, K - j0)
+            rest = K - j0 - w
+            if rest <= 0:
+                break
+            out["trsm"] += 2.0 * rest * w * w
+            nrem = J0 + wo - (j0 + w)
+            if nrem > 0:
+                out["inner"] += 2.0 * w * (nrem * rest - nrem * (nrem - 1) / 2)
+        r = K - (J0 + wo)
+        if r <= 0:
+            break
+        w2 = min(ob, r)
+        out["next"] += 2.0 * wo * (w2 * r - w2 * (w2 - 1) / 2)
+        m = r - w2
+        out["bulk"] += float(m) * (m + 1) * wo
+    return out
+
+
 def oracle_steps(A, w, nsteps):
     """Time nsteps oracle Newton steps from the cold start (test infrastructure)."""
     from oracle import ipm, sdp
@@ -224,6 +262,48 @@ def oracle_steps(A, w, nsteps):
         ipm.newton_step(prob, st, ipm.Options())
         times.append(time.perf_counter() - t0)
     return times
+
+
+def oracle_sample(A, w, blocks=((0, 0),)):
+    """A bounded sample of one oracle Newton step of workload w on the host
+    cores: the oracle's Schur complement restricted to the (a, b) blocks listed
+    (of L0^2, at the cold start X = Z = I) and its dense Cholesky (numpy) on an
+    SPD matrix of order K/4.  The step time is estimated as L0^2 / len(blocks)
+    times the first plus 64 times the second (cubic work); the step's remaining
+    parts (operators, block inverses, step length) are left out, so the estimate
+    is a lower bound.  Returns (estimated step seconds, seconds spent)."""
+    from oracle import sdp
+    prob = sdp.Problem(A, w["d_p"], w["d1"])
+    I = prob.identity_blocks()
+    k4 = max(1, prob.K // 4)
+    rng = np.random.default_rng(0)
+    R = rng.random((k4, k4))
+    S = R + R.T + (2.0 * k4 + 1.0) * np.eye(k4)       # diagonally dominant, SPD
+    t0 = time.perf_counter()
+    prob.schur_structured(I, I, blocks=list(blocks))
+    t1 = time.perf_counter()
+    np.linalg.cholesky(S)
+    t2 = time.perf_counter()
+    est = prob.L0 ** 2 / len(blocks) * (t1 - t0) + 64.0 * (t2 - t1)
+    return est, t2 - t0
+
+
+def chol32_bulk_flops(K, nb=128, outer=4):
+    """Useful flops of the mixed form's outer trailing updates (the persistent
+    3xTF32 kernel on the main stream), lower triangle: per outer panel of
+    wo = outer*nb columns, m(m+1) wo with m the rows below the next outer panel."""
+    ob = outer * nb
+    tot, launches = 0.0, 0
+    for J0 in range(0, K, ob):
+        wo = min(ob, K - J0)
+        rest = K - (J0 + wo)
+        if rest <= 0:
+            break
+        m = rest - min(ob, rest)
+        if m > 0:
+            tot += float(m) * (m + 1) * wo
+            launches += 1
+    return tot, launches
 
 
 def measure_mixed(bd, synth, name, device, nsteps, crit_sms=0):
@@ -273,7 +353,22 @@ def measure_mixed(bd, synth, name, device, nsteps, crit_sms=0):
         verdict, _, _ = s.certify()
         bd.psdp_get_P(s.h)
     t1 = time.perf_counter()
+    roof = None
+    if "chol32_syrk_tc" in prof and prof["chol32_syrk_tc"][0] > 0:
+        pk, pk_kind = peaks()
+        tf32_peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"]) * NOMINAL_TF32_TFLOPS / NOMINAL_BF16_TFLOPS
+        useful, nl = chol32_bulk_flops(polya_K(w), work["nb_chol32"])
+        launches, tms = prof["chol32_syrk_tc"]
+        issued = 3.0 * useful / max(nl, 1)          # 3xTF32: three TF32 products per useful one
+        ach = issued / (tms / launches * 1e-3) / 1e12
+        roof = {"kernel": "k_tc_gemm_persist (chol32_syrk_tc, 3xTF32 trailing update)", "bound": "tensor",
+                "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": ach / tf32_peak,
+                "useful_tflops": useful / max(nl, 1) / (tms / launches * 1e-3) / 1e12,
+                "share_of_step": tms / sum(v[1] for v in prof.values()),
+                "peak_source": f"{pk_kind} bf16 sustained x nominal TF32/BF16 {NOMINAL_TF32_TFLOPS:.0f}/{NOMINAL_BF16_TFLOPS:.0f}",
+                "traffic": None}
     return {"workload": f"n={w['n']} l={w['l']} d_p={w['d_p']} d1=d2={w['d1']} s={w['s']} seed=0",
+            "roofline": roof,
             "ms_per_step": sum(ms) / len(ms), "steps_per_s": 1e3 * len(ms) / sum(ms),
             "time_to_certificate_s": t1 - t0, "newton_steps": iters, "status": status, "verdict": verdict,
             "relgap": info["relgap"], "fp64_fallback": bool(info["fallback"] or fallback),
@@ -476,26 +571,121 @@ def run_extra(args):
 
 
 def run_reference(args):
+    """The oracle (the paper ships no code) on the headline workload: each step
+    is one bounded sample of an oracle Newton step (oracle_sample), the step
+    time estimated from it."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from paper_1411_3769_gb300 import synth
     w = WORKLOAD
     A = synth.system(w["n"], w["l"], w["s"], w["seed"])
-    oracle_steps(A, w, max(0, args.warmup))
-    times = oracle_steps(A, w, args.steps)
-    tot = sum(times)
+    oracle_sample(A, w)                               # one untimed warm-up sample
+    est = [oracle_sample(A, w)[0] for _ in range(args.steps)]
+    tot = sum(est)
     v = args.steps / tot
     cores = os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "warmup": 1, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "n=20 l=4 d_p=2 d1=d2=3 (K=2100, 140 blocks) s=0.3 seed=0",
-                       "l2": "oracle on host cores"},
+            "config": workload_config(w),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} oracle Newton steps from the cold start"},
+                             "sample": f"{args.steps} samples of one oracle Newton step at the cold start, each: the "
+                                       "Schur complement's (0,0) block of 36 and a numpy Cholesky of order K/4, "
+                                       "scaled to a step (x36, x64); the step's other parts left out"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def workload_config(w):
+    K = polya_K(w)
+    return {"workload": f"n={w['n']} l={w['l']} d_p={w['d_p']} d1=d2={w['d1']} (K={K}) s={w['s']} seed={w['seed']}",
+            "precision": "FP64 results", "l2": "Schur complement of 8K^2 bytes rewritten every step, plus a 256 MB flush"}
+
+
+def time_steps(bd, torch, h, stream, X0, Z0, y0, flush, nsteps):
+    """nsteps Newton steps from the restored cold start, each bracketed by CUDA
+    events on the library's stream after an L2 flush on it; returns ms per step."""
+    evs = []
+    for _ in range(nsteps):
+        bd.psdp_load_iterate(h, X0, Z0, y0)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s, info = bd.psdp_step(h)
+        if s != 0:
+            raise RuntimeError(f"psdp_step failed: {bd.STATUS[s]}")
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def profile_step(bd, torch, h, stream, X0, Z0, y0, flush, nsteps=1):
+    """Per-kernel CUDA-event durations inside the re-captured step graph."""
+    bd.psdp_profile_enable(h, True)
+    time_steps(bd, torch, h, stream, X0, Z0, y0, flush, 1)
+    bd.psdp_profile_reset(h)
+    ms = time_steps(bd, torch, h, stream, X0, Z0, y0, flush, nsteps)
+    prof = bd.psdp_profile_get(h)
+    bd.psdp_profile_enable(h, False)
+    return prof, sum(ms)
+
+
+def time_to_certificate(bd, A, w, local, **opts):
+    """setup + solve + certify + P readback through the C ABI with host buffers."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with bd.Solver(A, w["d_p"], w["d1"], device=local, **opts) as s:
+        status, iters, info = s.solve()
+        verdict, _, _ = s.certify()
+        P = bd.psdp_get_P(s.h)
+        y = bd.psdp_get_y(s.h)
+    t = time.perf_counter() - t0
+    return {"seconds": t, "newton_steps": iters, "status": status, "verdict": verdict, "relgap": info["relgap"],
+            "psi": info["psi"], "P_bytes": P.nbytes, "y": y}
+
+
+def fp64_roofline(kern, prof, prof_ms, steps, K, work, engines, fp64_peak, pk, pk_kind):
+    """Per-kernel algorithmic rates of the FP64 step and the dominant contraction's
+    roofline.  Ozaki kernels are bound by the BF16 tensor pipe: their achieved rate
+    counts the 36 exact BF16 slice products each FP64 multiply-add takes."""
+    oz_c, oz_s = engines["cholesky"] == "ozaki", engines["schur"] == "ozaki"
+    cf = chol_flops_ozaki(K) if oz_c else chol_flops(K, work["nb_chol"])
+    for name, fl in (("schur_gemm", work["schur_flops"]), ("chol_syrk_gemm", cf["bulk"]),
+                     ("chol_syrk_next", cf["next"]), ("chol_trsm_gemm", cf["trsm"]),
+                     ("chol_inner_update", cf.get("inner", 0.0))):
+        if name in prof and prof[name][0] > 0:
+            launches, tms = prof[name]
+            per_step = launches / steps
+            avg = tms / launches
+            kern[name] = {"launches_per_step": per_step, "avg_ms": avg,
+                          "fp64_tflops": fl / per_step / (avg * 1e-3) / 1e12, "share_of_step": tms / prof_ms}
+    for name in ("chol_potrf_diag", "dense_solve", "schur_operands", "schur_gather", "schur_oz_split", "chol_oz_split",
+                 "block_chol_inv", "block_maxstep"):
+        if name in prof and prof[name][0] > 0:
+            kern[name] = {"launches_per_step": prof[name][0] / steps, "avg_ms": prof[name][1] / prof[name][0],
+                          "share_of_step": prof[name][1] / prof_ms}
+    dom = max(("schur_gemm", "chol_syrk_gemm"), key=lambda k: kern.get(k, {}).get("share_of_step", 0))
+    rate = kern.get(dom, {}).get("fp64_tflops")
+    ozaki = oz_c if dom == "chol_syrk_gemm" else oz_s
+    if ozaki:
+        peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+        ach = OZ_PAIRS * rate if rate else None
+        roof = {"kernel": "k_ozaki_gemm (" + dom + ", FP64 by the Ozaki scheme)", "bound": "tensor", "achieved": ach,
+                "peak": peak, "unit": "TFLOP/s", "frac": (ach / peak) if ach else None,
+                "peak_source": f"{pk_kind} bf16 sustained (kernel timed inside a seconds-long step)",
+                "counted": f"{OZ_PAIRS} BF16 slice products per FP64 multiply-add of the algorithmic work",
+                "fp64_equivalent_tflops": rate, "fp64_measured_peak_tflops": fp64_peak,
+                "fp64_equivalent_over_fp64_peak": (rate / fp64_peak) if rate else None}
+    else:
+        roof = {"kernel": KERNEL_OF[dom] + " (" + dom + ")", "bound": "fp64", "achieved": rate, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": (rate / fp64_peak) if rate else None,
+                "peak_source": "measured: the larger of the DFMA and DMMA probes (psdp_fp64_peaks)"}
+    roof["traffic"] = None
+    return roof
 
 
 def run_ours(args):
@@ -513,110 +703,58 @@ def run_ours(args):
     from paper_1411_3769_gb300 import binding as bd
     from paper_1411_3769_gb300 import synth
 
+    pk, pk_kind = peaks()
+    dfma_peak, dmma_peak = bd.psdp_fp64_peaks(local)
+    fp64_peak = max(dfma_peak, dmma_peak)
     w = WORKLOAD
     A = synth.system(w["n"], w["l"], w["s"], w["seed"] + rank)
-    # one stream for the library, the L2 flush and the timing events
     stream = torch.cuda.Stream()
-    opts = bd.psdp_default_opts(stream=stream.cuda_stream, device=local)
-    h = bd.psdp_setup(w["n"], w["l"], w["d_p"], w["d1"], A, opts)
-    X0, Z0, y0 = bd.psdp_get_iterate(h)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-
-    def one_step(timed):
-        bd.psdp_load_iterate(h, X0, Z0, y0)
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        if timed:
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-        s, info = bd.psdp_step(h)
-        if s != 0:
-            raise RuntimeError(f"psdp_step failed: {bd.STATUS[s]}")
-        if timed:
-            e1.record(stream)
-            return e0, e1
-        return None
-
-    for _ in range(max(args.warmup, 3)):
-        one_step(False)
+    h = bd.psdp_setup(w["n"], w["l"], w["d_p"], w["d1"], A, bd.psdp_default_opts(stream=stream.cuda_stream,
+                                                                                  device=local))
+    engines = bd.psdp_engines(h)
+    X0, Z0, y0 = bd.psdp_get_iterate(h)
+    time_steps(bd, torch, h, stream, X0, Z0, y0, flush, max(args.warmup, 3))
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        evs = [one_step(True) for _ in range(args.steps)]
-        torch.cuda.synchronize()
-    ms = [a.elapsed_time(b) for a, b in evs]
+        ms = time_steps(bd, torch, h, stream, X0, Z0, y0, flush, args.steps)
     tot_ms = sum(ms)
+    y_step = bd.psdp_get_y(h)                          # one step from the cold start
     work = bd.psdp_work(h)
     sizes = bd.psdp_sizes(h)
-    # second timed region with a CUDA event pair around every kernel of the
-    # step graph (re-captured with the events): per-kernel durations for the
-    # roofline; the events themselves slow the step, so `value` comes from the
-    # region above
-    bd.psdp_profile_enable(h, True)
-    one_step(False)
-    bd.psdp_profile_reset(h)
-    torch.cuda.synchronize()
-    evs_p = [one_step(True) for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    prof_ms = sum(a.elapsed_time(b) for a, b in evs_p)
-    prof = bd.psdp_profile_get(h)
-    bd.psdp_profile_enable(h, False)
+    # per-kernel durations from a second, profiled region (events slow the step)
+    prof, prof_ms = profile_step(bd, torch, h, stream, X0, Z0, y0, flush, 1)
+    bd.psdp_destroy(h)
     if dist:
         from paper_1411_3769_gb300 import replicas
         tot_ms = replicas.max_over_ranks(tot_ms, dist, device="cuda")    # the slowest replica
         dist.barrier()
-
-    # ---- end to end through the C ABI with host buffers: setup + solve + certify + P
-    e2e = []
-    for _ in range(args.e2e_runs):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        with bd.Solver(A, w["d_p"], w["d1"], device=local) as s:
-            status, iters, info = s.solve()
-            verdict, _, _ = s.certify()
-            P = bd.psdp_get_P(s.h)
-        t1 = time.perf_counter()
-        e2e.append((t1 - t0, iters, status, verdict, P.nbytes))
-    best = min(e2e, key=lambda r: r[0]) if e2e else (float("nan"), 0, "skipped", -1, 0)
-    bd.psdp_destroy(h)
+    ttc = time_to_certificate(bd, A, w, local)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
 
-    # ---- roofline of the dominant kernel (from the live CUDA events)
-    pk, pk_kind = peaks()
-    fp64_peak = pk["bf16_tflops"] * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
-    cf = chol_flops(sizes["K"], work["nb_chol"])
-    kern = {}
-    for name, flops_per_step in (("schur_gemm", work["schur_flops"]), ("chol_syrk_gemm", cf["bulk"]),
-                                 ("chol_syrk_next", cf["next"]), ("chol_trsm_gemm", cf["trsm"])):
-        if name in prof and prof[name][0] > 0:
-            launches, tms = prof[name]
-            per_step_launches = launches / args.steps
-            avg_ms = tms / launches
-            kern[name] = {"launches_per_step": per_step_launches, "avg_ms": avg_ms,
-                          "tflops": flops_per_step / per_step_launches / (avg_ms * 1e-3) / 1e12,
-                          "share_of_step": tms / prof_ms}
-    for name in ("chol_potrf_diag", "dense_solve", "schur_operands", "schur_gather", "block_chol_inv",
-                 "block_maxstep"):
-        if name in prof and prof[name][0] > 0:
-            kern[name] = {"launches_per_step": prof[name][0] / args.steps, "avg_ms": prof[name][1] / prof[name][0],
-                          "share_of_step": prof[name][1] / prof_ms}
-    kern["_profiled_ms_per_step"] = prof_ms / args.steps
-    dom = max(("schur_gemm", "chol_syrk_gemm"), key=lambda k: kern.get(k, {}).get("share_of_step", 0))
-    ach = kern.get(dom, {}).get("tflops")
-    roof = {"kernel": KERNEL_OF[dom] + " (" + dom + ")", "bound": "fp64", "achieved": ach,
-            "peak": fp64_peak, "unit": "TFLOP/s", "frac": (ach / fp64_peak) if ach else None,
-            "traffic": CHOL_BULK_DRAM_BYTES if dom == "chol_syrk_gemm" else None,
-            "peak_source": f"{pk_kind} bf16 {pk['bf16_tflops']} TFLOP/s x nominal FP64/BF16 ratio 1.25/2250"}
-    try:
-        roof["fp64_probe_tflops"] = bd.psdp_fp64_peak(local)
-    except Exception:
-        pass
+    kern = {"_profiled_ms_per_step": prof_ms}
+    roof = fp64_roofline(kern, prof, prof_ms, 1, sizes["K"], work, engines, fp64_peak, pk, pk_kind)
 
-    # ---- mixed precision (3xTF32 tensor cores + FP64 PCG) on the mid and large workloads
+    # ---- the same step with FP64 FMA only, for the speedup and the parity of the two engines
+    dfma = {}
+    if args.dfma:
+        st2 = torch.cuda.Stream()
+        h2 = bd.psdp_setup(w["n"], w["l"], w["d_p"], w["d1"], A,
+                           bd.psdp_default_opts(stream=st2.cuda_stream, device=local, fp64_gemm=1))
+        try:
+            m2 = time_steps(bd, torch, h2, st2, X0, Z0, y0, flush, 1)
+            y2 = bd.psdp_get_y(h2)
+            dfma = {"ms_per_step": m2[0], "speedup_of_headline_step": m2[0] / (tot_ms / args.steps),
+                    "y_rel_diff_vs_headline_step": float(np.abs(y_step - y2).max() / np.abs(y2).max())}
+        finally:
+            bd.psdp_destroy(h2)
+
+    # ---- mixed precision (3xTF32 tensor cores + FP64 PCG)
     mixed = {}
     if args.mixed:
         for wl in [x for x in args.mixed_workloads.split(",") if x]:
@@ -624,35 +762,61 @@ def run_ours(args):
                 mixed[wl] = measure_mixed(bd, synth, wl, local, args.mixed_steps)
             except Exception as exc:   # report, do not lose the main line
                 mixed[wl] = {"error": str(exc)[:200]}
-        if "mid" in mixed and "ms_per_step" in mixed["mid"]:
-            mixed["mid"]["speedup_vs_plain_fp64_step"] = (tot_ms / args.steps) / mixed["mid"]["ms_per_step"]
-        if args.fp64_large and "ms_per_step" in mixed.get("large", {}):
-            try:
-                f64 = measure_fp64_step(bd, synth, "large", local)
-                mixed["large"]["plain_fp64_ms_per_step"] = f64
-                mixed["large"]["speedup_vs_plain_fp64_step"] = f64 / mixed["large"]["ms_per_step"]
-            except Exception as exc:
-                mixed["large"]["plain_fp64_error"] = str(exc)[:200]
+        lg = mixed.get("large", {})
+        if "time_to_certificate_s" in lg:
+            lg["fp64_time_to_certificate_s"] = ttc["seconds"]
+            lg["speedup_time_to_certificate_vs_fp64"] = ttc["seconds"] / lg["time_to_certificate_s"]
+            lg["speedup_step_vs_fp64"] = (tot_ms / args.steps) / lg["ms_per_step"]
+            if dfma:
+                lg["speedup_step_vs_dfma_fp64"] = dfma["ms_per_step"] / lg["ms_per_step"]
 
-    # ---- CPU oracle baseline on a bounded sample
-    ct = oracle_steps(A, w, args.cpu_steps)
-    cpu = {"value": (len(ct) / sum(ct)) if ct else None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-           "sample": f"{len(ct)} oracle Newton steps of this workload from the cold start (numpy FP64)"}
+    # ---- the mid workload in FP64 (second record)
+    mid = {}
+    if args.mid:
+        wm = MID
+        Am = synth.system(wm["n"], wm["l"], wm["s"], wm["seed"])
+        hm = bd.psdp_setup(wm["n"], wm["l"], wm["d_p"], wm["d1"], Am,
+                           bd.psdp_default_opts(stream=stream.cuda_stream, device=local))
+        try:
+            Xm, Zm, ym = bd.psdp_get_iterate(hm)
+            time_steps(bd, torch, hm, stream, Xm, Zm, ym, flush, 3)
+            with ClockSampler(local) as clk_m:
+                mm = time_steps(bd, torch, hm, stream, Xm, Zm, ym, flush, args.mid_steps)
+            wk = bd.psdp_work(hm)
+            eng_m = bd.psdp_engines(hm)
+            pm, pm_ms = profile_step(bd, torch, hm, stream, Xm, Zm, ym, flush, 5)
+        finally:
+            bd.psdp_destroy(hm)
+        km = {"_profiled_ms_per_step": pm_ms / 5}
+        roof_m = fp64_roofline(km, pm, pm_ms, 5, polya_K(wm), wk, eng_m, fp64_peak, pk, pk_kind)
+        tm = time_to_certificate(bd, Am, wm, local, eps=1e-8)
+        mid = {"config": workload_config(wm), "engines": eng_m, "steps": args.mid_steps,
+               "ms_per_step": sum(mm) / len(mm), "steps_per_s": 1e3 * len(mm) / sum(mm), "roofline": roof_m,
+               "kernels": km, "clocks": clk_m.summary(),
+               "time_to_certificate_eps_1e-8": {k: v for k, v in tm.items() if k != "y"}}
 
-    t_job, iters, status, verdict, pbytes = best
+    # ---- the oracle on a bounded sample of the headline workload
+    est = [oracle_sample(A, w)[0] for _ in range(max(1, args.cpu_samples))]
+    cpu = {"value": len(est) / sum(est), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"{len(est)} samples of one oracle Newton step at the cold start, each: the Schur complement's "
+                     "(0,0) block of 36 and a numpy Cholesky of order K/4, scaled to a step (x36, x64); the "
+                     "step's other parts left out (a lower bound on its time)"}
+
     value = world * args.steps / (tot_ms * 1e-3)
+    iters = ttc["newton_steps"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "n=20 l=4 d_p=2 d1=d2=3 (K=2100, 140 blocks of 20x20) s=0.3 seed=0",
-                       "precision": "plain FP64", "l2": "flushed (256 MB write) before every timed step",
-                       "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": roof, "kernels": kern,
-            "cpu_baseline": cpu,
-            "e2e": {"value": (iters / t_job) if iters else None, "unit": UNIT, "h2d_bytes_per_step": A.nbytes / max(iters, 1),
-                    "d2h_bytes_per_step": (pbytes + 16 * 8 * iters) / max(iters, 1),
-                    "time_to_certificate_s": t_job, "newton_steps": iters, "status": status, "verdict": verdict},
-            "mixed": mixed,
+            "warmup": max(args.warmup, 3), "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(workload_config(w), engines=engines,
+                           parallelism="replicas" if world > 1 else "single"),
+            "roofline": roof, "kernels": kern, "cpu_baseline": cpu,
+            "e2e": {"value": (iters / ttc["seconds"]) if iters else None, "unit": UNIT,
+                    "h2d_bytes_per_step": A.nbytes / max(iters, 1),
+                    "d2h_bytes_per_step": (ttc["P_bytes"] + 16 * 8 * iters + 4 * iters) / max(iters, 1),
+                    "time_to_certificate_s": ttc["seconds"], "newton_steps": iters, "status": ttc["status"],
+                    "verdict": ttc["verdict"], "relgap": ttc["relgap"]},
+            "fp64_dfma_step": dfma, "mixed": mixed, "mid_fp64": mid,
+            "fp64_peaks_tflops": {"dfma": dfma_peak, "dmma": dmma_peak},
             "gpu_launches": int(work["kernels_per_step"]) * args.steps,
             "clocks": clk.summary(),
             "work": {"schur_flops_per_step": work["schur_flops"], "chol_flops_per_step": work["chol_flops"],

@@ -240,6 +240,11 @@ psdp_status psdp_profile_get(psdp_ctx* c, int max_entries, char* names, int64_t*
  * mixed-precision step. */
 psdp_status psdp_work(const psdp_ctx* c, double* out7);
 
+/* Engines the context chose for its FP64 contractions (psdp_opts.fp64_gemm):
+ * out[0] = 1 if the Schur complement uses the Ozaki scheme, out[1] = 1 if the
+ * Cholesky trailing updates do (0: FP64 FMA). */
+psdp_status psdp_engines(const psdp_ctx* c, int32_t* out2);
+
 /* The CUDA stream the context runs on (cudaStream_t as void*). */
 void* psdp_stream(psdp_ctx* c);
 

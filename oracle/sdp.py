@@ -188,10 +188,12 @@ class Problem:
             terms.append((Ha @ Y[g], Hb @ X[g]))
         return terms
 
-    def schur_structured(self, Y: np.ndarray, X: np.ndarray) -> np.ndarray:
+    def schur_structured(self, Y: np.ndarray, X: np.ndarray, blocks=None) -> np.ndarray:
         """Omega from the block formula: for basis pairs p=(r,s), q=(k,m),
         tr(E_p Psi E_q Phi) = sum over ordered (i,v) with {i,v} = {r,s} and
-        ordered (j,u) with {j,u} = {k,m} of Psi[i,j] * Phi[u,v]."""
+        ordered (j,u) with {j,u} = {k,m} of Psi[i,j] * Phi[u,v].
+        blocks: optional list of (a, b) blocks to form (the others stay zero);
+        a timing sample of the full computation, same arithmetic."""
         n, Nt = self.n, self.Nt
         pairs = svec_pairs(n)
         r = np.array([p[0] for p in pairs])
@@ -202,6 +204,8 @@ class Problem:
         Om = np.zeros((self.K, self.K))
         for a in range(self.L0):
             for b in range(self.L0):
+                if blocks is not None and (a, b) not in blocks:
+                    continue
                 terms = self.schur_terms(a, b, Y, X)
                 Psi = np.stack([t[0].reshape(-1) for t in terms])     # (T, n*n), index i*n+j
                 Phi = np.stack([t[1].reshape(-1) for t in terms])     # (T, n*n), index u*n+v

@@ -31,7 +31,7 @@ EXPORTS = ("psdp_default_opts", "psdp_setup", "psdp_sizes", "psdp_step", "psdp_s
            "psdp_destroy", "psdp_strerror", "psdp_tc_gemm_check", "psdp_tc_gemm_persist_check", "psdp_trsv_timeout_check", "psdp_get_schur_mixed",
            "psdp_tc_gemm_noalloc", "psdp_solve_batch", "psdp_autotune", "psdp_set_start", "psdp_mlp_create",
            "psdp_mlp_destroy", "psdp_mlp_params", "psdp_mlp_grads", "psdp_mlp_train", "psdp_mlp_predict",
-           "psdp_fp64_peaks", "psdp_ozaki_gemm_check")
+           "psdp_fp64_peaks", "psdp_ozaki_gemm_check", "psdp_engines")
 
 
 class Opts(C.Structure):
@@ -102,6 +102,7 @@ def _lib():
                                          C.POINTER(C.c_float)]),
             "psdp_mlp_predict": (C.c_int, [vp, vp, C.c_int, vp]),
             "psdp_fp64_peaks": (C.c_int, [C.c_int, dp, dp]),
+            "psdp_engines": (C.c_int, [vp, ip]),
             "psdp_ozaki_gemm_check": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_double, C.c_double,
                                                 C.c_int]),
         }
@@ -279,6 +280,12 @@ def psdp_work(h) -> dict:
     _check(_lib().psdp_work(h, _dp(out)), "psdp_work")
     return dict(schur_flops=out[0], chol_flops=out[1], schur_terms=out[2], schur_dense_flops=out[3],
                 kernels_per_step=int(out[4]), nb_chol=int(out[5]), nb_chol32=int(out[6]))
+
+
+def psdp_engines(h) -> dict:
+    out = np.zeros(2, dtype=np.int32)
+    _check(_lib().psdp_engines(h, _ip(out)), "psdp_engines")
+    return dict(schur="ozaki" if out[0] else "dfma", cholesky="ozaki" if out[1] else "dfma")
 
 
 def psdp_stream(h) -> int:

@@ -121,8 +121,8 @@ void enqueue_schur(psdp_ctx* c) {
                                        dpad, np, c->d_oz_sb, c->d_oz_eb);
                 }
                 ProfScope p(c, "schur_gemm");
-                launch_ozaki_gemm(st, c->d_oz_sb, c->n2, c->d_oz_eb, c->d_oz_sa, c->n2, c->d_oz_ea, dpad, np,
-                                  c->d_term_cnt + p0, 0, k0, c->d_Tbuf, c->n2, (int64_t)c->n2 * c->n2, 1.0,
+                launch_ozaki_gemm(st, c->d_oz_sb, c->n2, 0, c->d_oz_eb, c->d_oz_sa, c->n2, 0, c->d_oz_ea, c->n2, c->n2,
+                                  dpad, np, c->d_term_cnt + p0, 0, k0, c->d_Tbuf, c->n2, (int64_t)c->n2 * c->n2, 1.0,
                                   k0 == 0 ? 0.0 : 1.0, 0, c->d_flag);
             }
         } else {
@@ -166,51 +166,74 @@ constexpr int kOneShotWaves = 64;
 // Omega = L L^T with the trailing updates by the Ozaki scheme: outer panels of
 // kOzakiMaxDepth (256) columns, each factored as 32-column inner panels by the
 // FP64 kernels (diagonal factor and inverse, panel solve, update of the outer
-// panel's remaining columns), then one FP64-accurate update of the whole
-// trailing matrix of depth 256 from the outer panel's slices.  Every element
-// receives its updates in panel order, and the 32 x 32 diagonal inverses are
-// those the triangular solves use.
+// panel's remaining columns), then FP64-accurate updates of depth 256 from the
+// outer panel's slices.  Look-ahead of depth one at the outer level:
+//   crit: inner(P), split(P) | wait bulk(P-1) | next(P): the next outer panel's columns
+//   main: wait split(P) | bulk(P): every column right of the next outer panel
+// so outer panel P+1 is factored while bulk(P) runs.  bulk(P-1) and next(P)
+// write the same columns and are ordered by the wait; split(P+1) reuses the
+// slice buffer bulk(P-1) read, after the same wait.  Every element receives its
+// updates in panel order, and the 32 x 32 diagonal inverses are those the
+// triangular solves use.
 void enqueue_cholesky_ozaki(psdp_ctx* c) {
-    cudaStream_t st = c->stream;
+    cudaStream_t st = c->stream, cs = c->crit;
     const int K = c->K, nb = c->nb_chol, OB = kOzakiMaxDepth;
     double* A = c->d_Om;
-    for (int J0 = 0; J0 < K; J0 += OB) {
+    const size_t slice_elems = ozaki_slice_elems(K, OB, 1);
+    stream_dep(st, cs, c->ev_fork);
+    for (int J0 = 0, P = 0; J0 < K; J0 += OB, ++P) {
         const int wo = std::min(OB, K - J0);
         for (int j0 = J0; j0 < J0 + wo; j0 += nb) {
             const int w = std::min(nb, K - j0);
             double* Lp = c->d_Linv + (size_t)(j0 / nb) * nb * nb;
             {
-                ProfScope q(c, "chol_potrf_diag", st);
-                launch_potrf_diag(st, A, K, j0, nb, Lp, c->d_flag);
+                ProfScope q(c, "chol_potrf_diag", cs);
+                launch_potrf_diag(cs, A, K, j0, nb, Lp, c->d_flag);
             }
             const int rest = K - j0 - w;
             if (rest <= 0) break;
             double* panel = A + (int64_t)j0 * K + j0 + w;
             {
-                ProfScope q(c, "chol_trsm_gemm", st);
-                launch_gemm_tn(st, w, rest, 1, Lp, nb, nullptr, 0, panel, K, nullptr, 0, nullptr, w, panel, K, 0, 1.0,
+                ProfScope q(c, "chol_trsm_gemm", cs);
+                launch_gemm_tn(cs, w, rest, 1, Lp, nb, nullptr, 0, panel, K, nullptr, 0, nullptr, w, panel, K, 0, 1.0,
                                0.0, 0);
             }
             const int nrem = J0 + wo - (j0 + w);      // outer-panel columns right of this inner panel
             if (nrem > 0) {
-                ProfScope q(c, "chol_syrk_next", st);
-                launch_gemm_tn(st, nrem, rest, 1, panel, K, nullptr, 0, panel, K, nullptr, 0, nullptr, w,
+                ProfScope q(c, "chol_inner_update", cs);
+                launch_gemm_tn(cs, nrem, rest, 1, panel, K, nullptr, 0, panel, K, nullptr, 0, nullptr, w,
                                A + (int64_t)(j0 + w) * K + j0 + w, K, 0, -1.0, 1.0, 1);
             }
         }
         const int rest = K - (J0 + wo);
         if (rest <= 0) break;
-        // L(J0+wo+r, J0+k) at P[k*K + r]: rows of the outer panel below it
-        const double* P = A + (int64_t)J0 * K + J0 + wo;
+        // L(J0+wo+r, J0+k) at Pp[k*K + r]: rows of the outer panel below it
+        const double* Pp = A + (int64_t)J0 * K + J0 + wo;
         const int dpad = (wo + 31) / 32 * 32;
+        uint16_t* sl = c->d_oz_sa + (size_t)(P & 1) * slice_elems;
+        int32_t* ex = c->d_oz_ea + (size_t)(P & 1) * K;
         {
-            ProfScope q(c, "chol_oz_split", st);
-            launch_ozaki_split(st, P, K, 0, nullptr, rest, nullptr, wo, 0, dpad, 1, c->d_oz_sa, c->d_oz_ea);
+            ProfScope q(c, "chol_oz_split", cs);
+            launch_ozaki_split(cs, Pp, K, 0, nullptr, rest, nullptr, wo, 0, dpad, 1, sl, ex);
         }
-        ProfScope q(c, "chol_syrk_gemm", st);
-        launch_ozaki_gemm(st, c->d_oz_sa, rest, c->d_oz_ea, c->d_oz_sa, rest, c->d_oz_ea, dpad, 1, nullptr, wo, 0,
-                          A + (int64_t)(J0 + wo) * K + J0 + wo, K, 0, -1.0, 1.0, 1, c->d_flag);
+        stream_dep(cs, st, c->ev_join);                     // main: after split(P)
+        stream_dep(st, cs, c->ev_fork);                     // crit: after bulk(P-1)
+        double* T = A + (int64_t)(J0 + wo) * K + J0 + wo;   // trailing matrix
+        const int wo2 = std::min(OB, rest);
+        {
+            // the next outer panel's columns [0, wo2) of T, all rows (lower part)
+            ProfScope q(c, "chol_syrk_next", cs);
+            launch_ozaki_gemm(cs, sl, rest, 0, ex, sl, rest, 0, ex, rest, wo2, dpad, 1, nullptr, wo, 0, T, K, 0,
+                              -1.0, 1.0, 1, c->d_flag);
+        }
+        if (rest > wo2) {
+            // columns [wo2, rest) of T, rows from wo2 (lower part)
+            ProfScope q(c, "chol_syrk_gemm", st);
+            launch_ozaki_gemm(st, sl, rest, wo2, ex, sl, rest, wo2, ex, rest - wo2, rest - wo2, dpad, 1, nullptr,
+                              wo, 0, T + (int64_t)wo2 * K + wo2, K, 0, -1.0, 1.0, 1, c->d_flag);
+        }
     }
+    stream_dep(cs, st, c->ev_join);
 }
 
 void enqueue_cholesky(psdp_ctx* c) {
@@ -711,8 +734,9 @@ psdp_status alloc_fp64(psdp_ctx* c) {
         ea = (size_t)c->pairs_per_chunk * c->n2;
     }
     if (c->oz_chol) {
-        sa = std::max(sa, ozaki_slice_elems(c->K, kOzakiMaxDepth, 1));
-        ea = std::max(ea, (size_t)c->K);
+        // one outer panel's rows, double-buffered by panel parity (look-ahead)
+        sa = std::max(sa, 2 * ozaki_slice_elems(c->K, kOzakiMaxDepth, 1));
+        ea = std::max(ea, 2 * (size_t)c->K);
     }
     if (sa) {
         TRY(dalloc(&c->d_oz_sa, sa));
@@ -766,14 +790,14 @@ psdp_status alloc_mixed(psdp_ctx* c) {
 }
 
 // Engines of the FP64 contractions.  Automatic: the Ozaki scheme where its
-// tiles (128 x 64, depth 256) are well filled and the DFMA work is large: the
-// Cholesky from K >= kOzakiCholMinK, the Schur contraction from n^2 >= 1024
-// (n >= 32); DFMA below.
-constexpr int kOzakiCholMinK = 8192;
+// 128 x 64 tiles are filled: the Cholesky from K >= kOzakiCholMinK (mid
+// workload, K = 2100: 4.45 vs 6.64 ms a step), the Schur contraction from
+// n >= 16 (n^2 >= 256 rows); DFMA below, where the step is latency-bound.
+constexpr int kOzakiCholMinK = 1024;
 void choose_fp64_engines(psdp_ctx* c) {
     const int e = c->opt.fp64_gemm;
     c->oz_chol = e == PSDP_GEMM_OZAKI || (e == PSDP_GEMM_AUTO && c->K >= kOzakiCholMinK);
-    c->oz_schur = e == PSDP_GEMM_OZAKI || (e == PSDP_GEMM_AUTO && c->n2 >= 1024);
+    c->oz_schur = e == PSDP_GEMM_OZAKI || (e == PSDP_GEMM_AUTO && c->n2 >= 256);
 }
 
 psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psdp_opts* o, psdp_ctx** out) {
@@ -1475,7 +1499,10 @@ psdp_status psdp_profile_enable(psdp_ctx* c, int on) {
     if (!c) return PSDP_EINVAL;
     cudaSetDevice(c->device);
     if (on && c->prof_pool.empty()) {
-        c->prof_pool.resize(8192);
+        // two halves (FP64 and mixed step graphs), each with an event pair for up
+        // to four timed launches per 32-column panel plus the step's other sites
+        const size_t sites = 4 * (size_t)((c->K + 31) / 32) + 512;
+        c->prof_pool.resize(std::max<size_t>(8192, 4 * sites));
         for (auto& e : c->prof_pool)
             if (cudaEventCreate(&e) != cudaSuccess) return PSDP_ECUDA;
     }
@@ -1525,6 +1552,13 @@ psdp_status psdp_fp64_peak(int device, double* tflops) {
     const double v = fp64_peak_probe(device);
     if (v <= 0) return PSDP_ECUDA;
     *tflops = v;
+    return PSDP_OK;
+}
+
+psdp_status psdp_engines(const psdp_ctx* c, int32_t* out) {
+    if (!c || !out) return PSDP_EINVAL;
+    out[0] = c->oz_schur ? 1 : 0;
+    out[1] = c->oz_chol ? 1 : 0;
     return PSDP_OK;
 }
 

@@ -23,17 +23,21 @@
 // tensor cores is exact.  Each level has its own TMEM accumulator (8 levels x
 // 64 columns fill the 512 columns of TMEM).
 //
-// Combination (epilogue).  H = T_2 128^2 + T_3 128 + T_4 and
-// L = T_5 128^4 + T_6 128^3 + T_7 128^2 + T_8 128 + T_9 in int64 (exact);
-// D_ij = 2^(e_i + f_j - 28) (H + 2^-35 L), rounded once when L is converted and
-// once in the FMA.  With the split's own rounding the error of D_ij is at most
-// about Kd 2^(e_i + f_j - 56) + 2^-52 |D_ij|, the accuracy of an FP64 GEMM.
+// Combination (epilogue).  Va = T_2 128^3 + T_3 128^2 + T_4 128 + T_5 and
+// Vb = T_6 128^3 + T_7 128^2 + T_8 128 + T_9 in int64 (exact, below 2^47 in
+// magnitude); D_ij = 2^(e_i + f_j - 63) (Va 2^28 + Vb), rounded once by an FMA
+// of the exactly converted Va and Vb.  With the split's own rounding the error
+// of D_ij is at most about Kd 2^(e_i + f_j - 56) + 2^-53 |D_ij|, the accuracy of
+// an FP64 GEMM.
 //
 // Tiles: 128 rows (TMEM lanes) x 64 columns; per stage 32 of k for all 8
 // slices of both operands (64-byte swizzled rows, 96 KB), two stages.  Warp 0
 // lane 0 issues the TMA loads, warp 1 lane 0 the 36 slice-pair MMAs per
-// 16-deep k step, all four warps drain TMEM.  Waits are bounded as in the other
-// tcgen05 kernels.
+// 16-deep k step, and all eight warps drain TMEM, warp w taking lanes
+// 32 (w % 4) .. +31 and columns 32 (w / 4) .. +31.  Every thread loads the 32
+// old C values of its row (and the column exponents go to shared memory)
+// before the main loop, so their latency is hidden under the MMAs.  Waits are
+// bounded as in the other tcgen05 kernels.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -51,7 +55,7 @@ constexpr int OZ_TA = OZ_BM * OZ_ROW;           // 8 KB
 constexpr int OZ_TB = OZ_BN * OZ_ROW;           // 4 KB
 constexpr int OZ_STAGE = OZ_S * (OZ_TA + OZ_TB);  // 96 KB
 constexpr int OZ_STAGES = 2;
-constexpr int OZ_THREADS = 128;
+constexpr int OZ_THREADS = 256;   // 8 warps: two per TMEM lane quadrant in the epilogue
 constexpr int OZ_SPLIT_THREADS = 256;
 
 constexpr size_t oz_smem_bytes() { return (size_t)OZ_STAGES * OZ_STAGE + 1024 + 8 * (2 * OZ_STAGES + 1) + 16; }
@@ -80,20 +84,42 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, 
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-// 16 columns of 32 lanes from TMEM, without the wait (the caller waits once)
-__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
+// 8 columns of 32 lanes from TMEM, without the wait (the caller waits once)
+__device__ __forceinline__ void tmem_ld8_nw(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
 }
 
 // Depth of batch b in the window [k_off, k_off + kOzakiMaxDepth) of its full depth.
 __device__ __forceinline__ int oz_depth(const int32_t* kdv, int kd_uniform, int b, int k_off) {
     const int kd = (kdv ? kdv[b] : kd_uniform) - k_off;
     return kd < 0 ? 0 : (kd > kOzakiMaxDepth ? kOzakiMaxDepth : kd);
+}
+
+// Exact FP64 value of an integer below 2^53 in magnitude, assembled from its
+// bits by integer operations (the conversion instruction issues on GB300's
+// scarce FP64 pipe).
+__device__ __forceinline__ double oz_i2d(long long x) {
+    if (x == 0) return 0.0;
+    const unsigned long long sgn = x < 0 ? (1ull << 63) : 0ull;
+    const unsigned long long u = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
+    const int msb = 63 - __clzll((long long)u);                      // <= 52
+    const unsigned long long m = u << (52 - msb);
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)(msb + 1023) << 52) | (m & 0xFFFFFFFFFFFFFull)));
+}
+
+// D = (Va 2^28 + Vb) 2^E in FP64 with one rounding: Va, Vb are exact in FP64
+// (|Va|, |Vb| < 2^47), the FMA rounds once, and the power-of-two scale goes
+// into the exponent field by an integer add (ldexp only outside the normal
+// range).  One FP64 instruction: GB300's FP64 pipe is this epilogue's scarce unit.
+__device__ __forceinline__ double oz_combine(long long Va, long long Vb, int E) {
+    const double v = fma(oz_i2d(Va), 268435456.0, oz_i2d(Vb));
+    if (v == 0.0) return 0.0;
+    const long long bits = __double_as_longlong(v);
+    const int be = (int)((bits >> 52) & 0x7FF) + E;
+    if (be <= 0 || be >= 2047) return ldexp(v, E);
+    return __longlong_as_double(bits + ((long long)E << 52));
 }
 
 // Slices of one batch of operands.  Element (r, k) of batch b is
@@ -157,12 +183,14 @@ k_ozaki_split(const double* __restrict__ src, int64_t ld, int64_t src_batch, con
 }
 
 // C_b = alpha * D_b + beta * C_b with D_b[i][j] = sum_k A_b[i][k] B_b[j][k] from
-// the slices of A_b (rows i < M) and B_b (rows j < N) over the depth window
+// the slices of A_b (rows a_row0 + i, i < M, of slice arrays of a_rows rows) and
+// B_b (rows b_row0 + j, j < N, of b_rows) over the depth window
 // oz_depth(kd, kd_uniform, b, k_off); C_b[j * ldc + i] (column-major in i).
 // lower: only elements with i >= j, tiles wholly above the diagonal are skipped.
 __global__ void __launch_bounds__(OZ_THREADS, 1)
 k_ozaki_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
-             const int32_t* __restrict__ eA, const int32_t* __restrict__ eB, int M, int N,
+             const int32_t* __restrict__ eA, const int32_t* __restrict__ eB, int a_rows, int a_row0, int b_rows,
+             int b_row0, int M, int N,
              const int32_t* __restrict__ kd, int kd_uniform, int k_off, double* C, int64_t ldc, int64_t c_batch,
              double alpha, double beta, int lower, int* flag) {
     extern __shared__ uint8_t smem_raw[];
@@ -174,6 +202,7 @@ k_ozaki_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUt
     uint8_t* gbase = smem_raw + (base - base_raw);
     uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + OZ_STAGES * OZ_STAGE);
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * OZ_STAGES + 1);
+    __shared__ int ecol[OZ_BN];
     const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * OZ_STAGES, accb = full0 + 16 * OZ_STAGES;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int Kd = oz_depth(kd, kd_uniform, b, k_off);
@@ -193,6 +222,23 @@ k_ozaki_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUt
                      "r"(8 * OZ_BN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    // epilogue operands, fetched now: row i, columns jc .. jc + 31 of this thread
+    const int quad = warp & 3, half = warp >> 2;
+    const int i = m0 + 32 * quad + lane;
+    const int jc = n0 + 32 * half;
+    const int ei = (i < M) ? eA[(int64_t)b * a_rows + a_row0 + i] : 0;
+    double* Cb = C + (int64_t)b * c_batch;
+    // alpha, beta classified once (FP64 compares issue on the FP64 pipe)
+    const int amode = (alpha == 1.0) ? 0 : (alpha == -1.0 ? 1 : 2);
+    const int bmode = (beta == 0.0) ? 0 : (beta == 1.0 ? 1 : 2);
+    double cold[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const int col = jc + j;
+        cold[j] = (bmode != 0 && i < M && col < N && !(lower && i < col)) ? Cb[(int64_t)col * ldc + i] : 0.0;
+    }
+    if (threadIdx.x < OZ_BN)
+        ecol[threadIdx.x] = (n0 + (int)threadIdx.x < N) ? eB[(int64_t)b * b_rows + b_row0 + n0 + threadIdx.x] : 0;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -209,10 +255,11 @@ k_ozaki_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUt
                 const uint32_t fb = full0 + 8 * s;
                 mbar_expect_tx(fb, OZ_STAGE);
 #pragma unroll
-                for (int p = 0; p < OZ_S; ++p) tma_load_3d(st + p * OZ_TA, &mA, fb, kt * OZ_BK, m0, b * OZ_S + p);
+                for (int p = 0; p < OZ_S; ++p)
+                    tma_load_3d(st + p * OZ_TA, &mA, fb, kt * OZ_BK, a_row0 + m0, b * OZ_S + p);
 #pragma unroll
                 for (int q = 0; q < OZ_S; ++q)
-                    tma_load_3d(st + OZ_S * OZ_TA + q * OZ_TB, &mB, fb, kt * OZ_BK, n0, b * OZ_S + q);
+                    tma_load_3d(st + OZ_S * OZ_TA + q * OZ_TB, &mB, fb, kt * OZ_BK, b_row0 + n0, b * OZ_S + q);
             }
             // every issued stage has landed before the CTA may exit
             for (int q = (kt > OZ_STAGES ? kt - OZ_STAGES : 0); q < kt; ++q)
@@ -251,38 +298,35 @@ k_ozaki_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUt
     ok = __all_sync(0xffffffffu, ok);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
-        const int i = m0 + 32 * warp + lane;
-        const int ei = (i < M) ? eA[(int64_t)b * M + i] : 0;
-        double* Cb = C + (int64_t)b * c_batch;
-        const int32_t* eBb = eB + (int64_t)b * N;
-#pragma unroll 1
-        for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
-            uint32_t r[OZ_S][16];
+#pragma unroll
+        for (int c0 = 0; c0 < 32; c0 += 8) {
+            uint32_t r[OZ_S][8];
             if (nk > 0) {
 #pragma unroll
                 for (int t = 0; t < OZ_S; ++t)
-                    tmem_ld16_nw(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(OZ_BN * t + c0), r[t]);
+                    tmem_ld8_nw(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(OZ_BN * t + 32 * half + c0), r[t]);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             } else {
 #pragma unroll
                 for (int t = 0; t < OZ_S; ++t)
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) r[t][j] = 0u;
+                    for (int j = 0; j < 8; ++j) r[t][j] = 0u;
             }
             if (i < M) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = n0 + c0 + j;
+                for (int j = 0; j < 8; ++j) {
+                    const int col = jc + c0 + j;
                     if (col >= N || (lower && i < col)) continue;
                     long long T[OZ_S];
 #pragma unroll
                     for (int t = 0; t < OZ_S; ++t) T[t] = (long long)__float2int_rn(__uint_as_float(r[t][j]));
-                    const long long H = T[0] * 16384 + T[1] * 128 + T[2];
-                    const long long L = T[3] * 268435456LL + T[4] * 2097152LL + T[5] * 16384 + T[6] * 128 + T[7];
-                    const double v = fma((double)L, 0x1p-35, (double)H);
-                    const double w = ldexp(v, ei + eBb[col] - 28);
-                    double* cp = Cb + (int64_t)col * ldc + i;
-                    *cp = (beta == 0.0) ? alpha * w : fma(alpha, w, beta * *cp);
+                    const long long Va = ((T[0] * 128 + T[1]) * 128 + T[2]) * 128 + T[3];
+                    const long long Vb = ((T[4] * 128 + T[5]) * 128 + T[6]) * 128 + T[7];
+                    // D_ij = 2^(e_i + f_j - 63) (Va 2^28 + Vb), one rounding
+                    double w = oz_combine(Va, Vb, ei + ecol[col - n0] - 63);
+                    if (amode) w = (amode == 1) ? -w : alpha * w;
+                    const double c_old = cold[c0 + j];
+                    Cb[(int64_t)col * ldc + i] = (bmode == 0) ? w : (bmode == 1 ? c_old + w : fma(beta, c_old, w));
                 }
             }
         }
@@ -313,18 +357,24 @@ void launch_ozaki_split(cudaStream_t st, const double* src, int64_t ld, int64_t 
                                                                          kd_uniform, k_off, dpad, out, ex);
 }
 
-bool launch_ozaki_gemm(cudaStream_t st, const uint16_t* As, int M, const int32_t* eA, const uint16_t* Bs, int N,
-                       const int32_t* eB, int dpad, int batch, const int32_t* kd, int kd_uniform, int k_off, double* C,
-                       int64_t ldc, int64_t c_batch, double alpha, double beta, int lower, int* flag) {
+bool launch_ozaki_gemm(cudaStream_t st, const uint16_t* As, int a_rows, int a_row0, const int32_t* eA,
+                       const uint16_t* Bs, int b_rows, int b_row0, const int32_t* eB, int M, int N, int dpad,
+                       int batch, const int32_t* kd, int kd_uniform, int k_off, double* C, int64_t ldc,
+                       int64_t c_batch, double alpha, double beta, int lower, int* flag) {
     if (M <= 0 || N <= 0 || batch <= 0) return true;
-    if (dpad % OZ_BK != 0 || dpad > kOzakiMaxDepth) return false;
+    if (dpad % OZ_BK != 0 || dpad > kOzakiMaxDepth || a_row0 + M > a_rows || b_row0 + N > b_rows || a_row0 < 0 ||
+        b_row0 < 0)
+        return false;
     CUtensorMap mA, mB;
-    if (!tc_make_map_swz(&mA, As, true, dpad, M, (int64_t)batch * OZ_S, dpad, (int64_t)M * dpad, OZ_BK, OZ_BM, 64) ||
-        !tc_make_map_swz(&mB, Bs, true, dpad, N, (int64_t)batch * OZ_S, dpad, (int64_t)N * dpad, OZ_BK, OZ_BN, 64))
+    if (!tc_make_map_swz(&mA, As, true, dpad, a_rows, (int64_t)batch * OZ_S, dpad, (int64_t)a_rows * dpad, OZ_BK,
+                         OZ_BM, 64) ||
+        !tc_make_map_swz(&mB, Bs, true, dpad, b_rows, (int64_t)batch * OZ_S, dpad, (int64_t)b_rows * dpad, OZ_BK,
+                         OZ_BN, 64))
         return false;
     dim3 grid((N + OZ_BN - 1) / OZ_BN, (M + OZ_BM - 1) / OZ_BM, batch);
-    k_ozaki_gemm<<<grid, OZ_THREADS, oz_smem_bytes(), st>>>(mA, mB, eA, eB, M, N, kd, kd_uniform, k_off, C, ldc,
-                                                             c_batch, alpha, beta, lower, flag);
+    k_ozaki_gemm<<<grid, OZ_THREADS, oz_smem_bytes(), st>>>(mA, mB, eA, eB, a_rows, a_row0, b_rows, b_row0, M, N, kd,
+                                                             kd_uniform, k_off, C, ldc, c_batch, alpha, beta, lower,
+                                                             flag);
     return true;
 }
 
@@ -367,7 +417,7 @@ extern "C" psdp_status psdp_ozaki_gemm_check(int M, int N, int K, const double* 
         for (int k0 = 0; k0 < K && s == PSDP_OK; k0 += kOzakiMaxDepth) {
             launch_ozaki_split(0, dA, M, 0, nullptr, M, nullptr, K, k0, dpad, 1, sA, eA);
             launch_ozaki_split(0, dB, N, 0, nullptr, N, nullptr, K, k0, dpad, 1, sB, eB);
-            if (!launch_ozaki_gemm(0, sA, M, eA, sB, N, eB, dpad, 1, nullptr, K, k0, dC, M, 0, alpha,
+            if (!launch_ozaki_gemm(0, sA, M, 0, eA, sB, N, 0, eB, M, N, dpad, 1, nullptr, K, k0, dC, M, 0, alpha,
                                    k0 == 0 ? beta : 1.0, lower, dflag))
                 s = PSDP_ECUDA;
         }

@@ -2,17 +2,20 @@
 full-size code paths, and batched solves of instances shaped like the
 512-instance batch workload.
 
-* The mid workload (n=20, l=4, d_p=2, d1=3: K = 2100) runs the FP64 Cholesky's
-  66 panels with look-ahead, the persistent bulk trailing update, the 64 x 64
-  pair inverses and the 64-row flag-synchronised sweeps.
-* n=40, l=3, d_p=2, d1=1 (K = 4920): the early trailing matrices have more than
-  64 waves of 32 x 32 tiles, so the bulk update takes the one-shot tiled kernel
-  there and the persistent one later.
+* The mid workload (n=20, l=4, d_p=2, d1=3: K = 2100), with the FP64
+  contractions by the Ozaki scheme (the default at this size: nine outer
+  panels with look-ahead) and by FP64 FMA (66 panels with look-ahead, the
+  persistent bulk trailing update); both with the 64 x 64 pair inverses and the
+  64-row flag-synchronised sweeps.
+* n=40, l=3, d_p=2, d1=1 (K = 4920) by FP64 FMA: the early trailing matrices
+  have more than 64 waves of 32 x 32 tiles, so the bulk update takes the
+  one-shot tiled kernel there and the persistent one later; and the same step
+  by the Ozaki scheme (twenty outer panels, 1600-row Schur operands).
 From the same iterate (the oracle's k-th, loaded through the C ABI) one step of
 the library must match one step of the oracle (Sec. IV-A, Algorithm 2) to the
 1e-8 relative bound of the small-size step test: the step solves Omega dy = r
-(kappa(Omega) <= ~1e5 along these solves) and the rest is FP64 with another
-summation order.
+(kappa(Omega) <= ~1e5 along these solves) and the rest is FP64-accurate with
+another summation order.
 
 Batches: 20 uneven instances drawn like the batch workload (n 8..48, l 2..4,
 every d_p in {1, 2} and d1 in {1..4}, K up to 7410) must give bit-identical
@@ -46,11 +49,11 @@ def _rel(a, b):
     return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
 
 
-def _step_parity(bd, A, d_p, d1, ks):
+def _step_parity(bd, A, d_p, d1, ks, engine=0):
     n, l = A.shape[-1], A.shape[0]
     prob = sdp.Problem(A, d_p, d1)
     st = ipm.start_point(prob)
-    h = bd.psdp_setup(n, l, d_p, d1, A)
+    h = bd.psdp_setup(n, l, d_p, d1, A, bd.psdp_default_opts(fp64_gemm=engine))
     try:
         assert bd.psdp_sizes(h)["K"] == prob.K
         done = 0
@@ -75,14 +78,24 @@ def _step_parity(bd, A, d_p, d1, ks):
         bd.psdp_destroy(h)
 
 
-def test_mid_newton_steps_match_oracle(bd):
+@pytest.mark.parametrize("engine", [2, 1])
+def test_mid_newton_steps_match_oracle(bd, engine):
+    """FP64 contractions by the Ozaki scheme (the default at this size: nine
+    outer panels with look-ahead) and by FP64 FMA."""
     w = synth.WORKLOADS["mid"]
-    _step_parity(bd, synth.system(w["n"], w["l"], w["s"], 0), w["d_p"], w["d1"], ks=(2, 10))
+    _step_parity(bd, synth.system(w["n"], w["l"], w["s"], 0), w["d_p"], w["d1"], ks=(2, 10), engine=engine)
 
 
 def test_one_shot_bulk_update_newton_step_matches_oracle(bd):
     A = synth.system(40, 3, 0.3, 3)
-    _step_parity(bd, A, 2, 1, ks=(1,))
+    _step_parity(bd, A, 2, 1, ks=(1,), engine=1)
+
+
+def test_ozaki_engine_newton_step_matches_oracle(bd):
+    """n=40 (K = 4920): twenty outer panels of the Ozaki Cholesky and the Ozaki
+    Schur contraction on 1600-row operands."""
+    A = synth.system(40, 3, 0.3, 3)
+    _step_parity(bd, A, 2, 1, ks=(1,), engine=2)
 
 
 def _oracle_solve_verdict(args):
