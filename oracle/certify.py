@@ -36,7 +36,8 @@ def tau_c(M: np.ndarray) -> float:
 
 
 def coefficient_matrices(prob: Problem, y: np.ndarray):
-    """The L P-side and M Lyapunov coefficient matrices built from y."""
+    """The L P-side and M Lyapunov coefficient matrices built from y (with the
+    generalised form's R(alpha), the Lyapunov ones are -(A^T P + P A + R))."""
     P = prob.P_from_y(y)
     coefP = np.einsum("hg,hij->gij", prob.beta.astype(np.float64), P)
     coefL = np.zeros((prob.M, prob.n, prob.n))
@@ -44,7 +45,7 @@ def coefficient_matrices(prob: Problem, y: np.ndarray):
         acc = np.zeros((prob.n, prob.n))
         for h in range(prob.L0):
             acc += prob.H[h, j].T @ P[h] + P[h] @ prob.H[h, j]
-        coefL[j] = -acc
+        coefL[j] = -acc - prob.CR[j]
     return coefP, coefL
 
 
@@ -72,12 +73,16 @@ def grid_check(prob: Problem, y: np.ndarray, N: int) -> dict:
     P = prob.P_from_y(y)
     W0 = polya.monomials(prob.l, prob.d_p)
     Wa = polya.monomials(prob.l, prob.d_a)
+    Wr = polya.monomials(prob.l, prob.d_r) if prob.R is not None else None
     minP, maxQ = np.inf, -np.inf
     for alpha in simplex_grid(prob.l, N):
         Pa = eval_poly(P, W0, alpha)
         Aa = eval_poly(prob.A, Wa, alpha)
+        Q = Aa.T @ Pa + Pa @ Aa
+        if Wr is not None:
+            Q = Q + eval_poly(prob.R, Wr, alpha)
         minP = min(minP, np.linalg.eigvalsh(Pa).min())
-        maxQ = max(maxQ, np.linalg.eigvalsh(Aa.T @ Pa + Pa @ Aa).max())
+        maxQ = max(maxQ, np.linalg.eigvalsh(Q).max())
     return dict(minP=float(minP), maxQ=float(maxQ), ok=bool(minP > 0 and maxQ < 0))
 
 

@@ -69,7 +69,13 @@ class Problem:
     """
 
     def __init__(self, A, d_p: int, d1: int, d2: int | None = None, d_a: int = 1,
-                 delta: float = 1.0, delta_L: float = 0.0):
+                 delta: float = 1.0, delta_L: float = 0.0, R=None, d_r: int | None = None, a=None):
+        """R, d_r: the constant term of the generalised inequality of Sec. III-C
+        (Eq. LMI_general with one term, A~ = A(alpha)^T, B~ = I):
+        A(alpha)^T P(alpha) + P(alpha) A(alpha) + R(alpha) < 0 with R(alpha) =
+        sum_rho R_rho alpha^rho homogeneous of degree d_r <= d_p + d_a + d2
+        (coefficients (card W_{d_r}, n, n), symmetric).  a: the dual objective
+        vector (K values), the paper's all-ones vector (Eq. a) by default."""
         A = np.asarray(A, dtype=np.float64)
         self.A = A
         self.n = A.shape[-1]
@@ -84,7 +90,17 @@ class Problem:
         self.beta = polya.beta_table(self.l, d_p, d1)                   # (L0, L)
         self.c = polya.h_coeff_table(self.l, d_p, d_a, self.d2)         # (L0, M, Na)
         self.H = polya.h_matrices(self.c, A)                            # (L0, M, n, n)
-        self.a = np.ones(self.K)                                        # Eq. (a)
+        self.a = np.ones(self.K) if a is None else np.asarray(a, dtype=np.float64)   # Eq. (a)
+        if self.a.shape != (self.K,):
+            raise ValueError("objective vector a must have K entries")
+        self.R, self.d_r = None, None
+        if R is not None:
+            self.d_r = int(d_r)
+            self.R = np.asarray(R, dtype=np.float64)
+            if self.d_r > self.d_p + self.d_a + self.d2 or \
+                    self.R.shape != (polya.f_card(self.l, self.d_r), self.n, self.n):
+                raise ValueError("R must hold card(W_{d_r}) n x n coefficients, d_r <= d_p + d_a + d2")
+        self.CR = self._build_CR()                                      # R's part of the Lyapunov C
         self.C = self._build_C()
 
     @staticmethod
@@ -96,9 +112,30 @@ class Problem:
             raise ValueError("number of A coefficients is not card(W_{d_a}) for any l")
         return l
 
+    def _build_CR(self) -> np.ndarray:
+        """Lyapunov-block coefficients of (sum alpha)^e R(alpha), e = d_p + d_a +
+        d2 - d_r, the degree of the Lyapunov inequality: on the simplex the
+        inequality with R(alpha) and its homogenised form agree, and the dual
+        constraint B^T(y)_gamma - C_gamma >= 0 of block gamma then reads
+        -(coefficient of A^T P + P A) - R_gamma >= 0."""
+        n = self.n
+        CR = np.zeros((self.M, n, n))
+        if self.R is None:
+            return CR
+        e = self.d_p + self.d_a + self.d2 - self.d_r
+        Wr = polya.monomials(self.l, self.d_r)
+        Wpa = polya.monomials(self.l, self.d_p + self.d_a + self.d2)
+        for j, g in enumerate(Wpa):
+            for k, rho in enumerate(Wr):
+                rest = tuple(gi - ri for gi, ri in zip(g, rho))
+                if min(rest) >= 0:
+                    CR[j] += polya.multinomial(e, rest) * self.R[k]
+        return CR
+
     def _build_C(self) -> np.ndarray:
         """Eq. (Cj): delta*I*sum_h beta_{h,j} d_p!/h! on P-side blocks, 0 (or
-        the optional strict margin delta_L*...) on the Lyapunov blocks."""
+        the optional strict margin delta_L*...) on the Lyapunov blocks, plus R's
+        coefficients there (generalised form)."""
         n = self.n
         W0 = polya.monomials(self.l, self.d_p)
         w = np.array([polya.multinomial(self.d_p, h) for h in W0], dtype=np.float64)
@@ -109,6 +146,7 @@ class Problem:
             Wpa = polya.monomials(self.l, self.d_p + self.d_a + self.d2)
             for j, g in enumerate(Wpa):
                 C[self.L + j] = self.delta_L * np.eye(n) * polya.multinomial(sum(g), g)
+        C[self.L:] += self.CR
         return C
 
     # ------------------------------------------------------------ literal B_i
