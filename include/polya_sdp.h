@@ -166,6 +166,25 @@ psdp_status psdp_get_y(psdp_ctx* c, double* y);
  * Errors: EINVAL for non-finite y0, non-positive scalings or theta. */
 psdp_status psdp_set_start(psdp_ctx* c, const double* y0, const double* xscale, double theta);
 
+/* The generalised inequality of Sec. III-C (Eq. LMI_general) with one term,
+ * A~ = A(alpha)^T and B~ = I:  A(alpha)^T P(alpha) + P(alpha) A(alpha) + R(alpha) < 0
+ * on the simplex, with the constant term R(alpha) = sum_rho R_rho alpha^rho
+ * homogeneous of degree d_r, 0 <= d_r <= d_p + d_a + d2 (the Lyapunov
+ * inequality's degree).  R: host, card(W_{d_r}) * n * n doubles, rho in W_{d_r}
+ * in lexicographic order, each n x n coefficient row-major and symmetric
+ * (else EINVAL).  R enters the SDP only through C: on Lyapunov block gamma,
+ * C_gamma = sum_rho multinomial(e; gamma - rho) R_rho, e = d_p + d_a + d2 - d_r
+ * (the coefficients of R(alpha) (sum alpha)^e); the certificate and the
+ * lattice check include R.  Example: R = C^T C with the objective below gives
+ * the robust H2 analysis LMI.  Resets the iterate to the cold start. */
+psdp_status psdp_set_constant_term(psdp_ctx* c, int d_r, const double* R);
+
+/* The dual objective a of min a^T y (Eq. a; the paper's all-ones vector by
+ * default): host, K doubles, finite (else EINVAL).  With y_{q + Ntil h} the
+ * (r, s) entry of P_h, a = the svec weights of a symmetric W (W_rr, 2 W_rs)
+ * minimises sum_h tr(W P_h).  Resets the iterate to the cold start. */
+psdp_status psdp_set_objective(psdp_ctx* c, const double* a);
+
 /* The learned warm-start network (no counterpart in the paper): a three-layer
  * ReLU MLP n_in -> width -> width -> n_out whose products all run on the tensor
  * cores with BF16 operands and FP32 accumulation; Adam on FP32 master weights.

@@ -31,7 +31,8 @@ EXPORTS = ("psdp_default_opts", "psdp_setup", "psdp_sizes", "psdp_step", "psdp_s
            "psdp_destroy", "psdp_strerror", "psdp_tc_gemm_check", "psdp_tc_gemm_persist_check", "psdp_trsv_timeout_check", "psdp_get_schur_mixed",
            "psdp_tc_gemm_noalloc", "psdp_solve_batch", "psdp_autotune", "psdp_set_start", "psdp_mlp_create",
            "psdp_mlp_destroy", "psdp_mlp_params", "psdp_mlp_grads", "psdp_mlp_train", "psdp_mlp_predict",
-           "psdp_fp64_peaks", "psdp_ozaki_gemm_check", "psdp_engines")
+           "psdp_fp64_peaks", "psdp_ozaki_gemm_check", "psdp_engines", "psdp_set_constant_term",
+           "psdp_set_objective")
 
 
 class Opts(C.Structure):
@@ -103,6 +104,8 @@ def _lib():
             "psdp_mlp_predict": (C.c_int, [vp, vp, C.c_int, vp]),
             "psdp_fp64_peaks": (C.c_int, [C.c_int, dp, dp]),
             "psdp_engines": (C.c_int, [vp, ip]),
+            "psdp_set_constant_term": (C.c_int, [vp, C.c_int, dp]),
+            "psdp_set_objective": (C.c_int, [vp, dp]),
             "psdp_ozaki_gemm_check": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_double, C.c_double,
                                                 C.c_int]),
         }
@@ -280,6 +283,16 @@ def psdp_work(h) -> dict:
     _check(_lib().psdp_work(h, _dp(out)), "psdp_work")
     return dict(schur_flops=out[0], chol_flops=out[1], schur_terms=out[2], schur_dense_flops=out[3],
                 kernels_per_step=int(out[4]), nb_chol=int(out[5]), nb_chol32=int(out[6]))
+
+
+def psdp_set_constant_term(h, d_r: int, R: np.ndarray) -> None:
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    _check(_lib().psdp_set_constant_term(h, d_r, _dp(R)), "psdp_set_constant_term")
+
+
+def psdp_set_objective(h, a: np.ndarray) -> None:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    _check(_lib().psdp_set_objective(h, _dp(a)), "psdp_set_objective")
 
 
 def psdp_engines(h) -> dict:

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <new>
 
 #include "psdp_internal.h"
@@ -601,7 +602,7 @@ void free_ctx(psdp_ctx* c) {
                     c->d_opA_hi, c->d_opA_lo, c->d_opB_hi, c->d_opB_lo, c->d_prodA, c->d_prodB, c->d_T32,
                     c->d_Om32, c->d_Linv32, c->d_Pt_hi, c->d_Pt_lo, c->d_z32, c->d_trsv_sync, c->d_Pk_hi, c->d_Pk_lo, c->d_Lt_hi, c->d_Lt_lo, c->d_pcg_x, c->d_pcg_r,
                     c->d_pcg_z, c->d_pcg_p, c->d_pcg_q, c->d_pcg_state, c->d_pcg_done, c->d_M1, c->d_M2,
-                    c->d_oz_sa, c->d_oz_sb, c->d_oz_ea, c->d_oz_eb};
+                    c->d_oz_sa, c->d_oz_sb, c->d_oz_ea, c->d_oz_eb, c->d_R, c->d_Wr, c->d_CR, c->d_avec};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_info) cudaFreeHost(c->h_info);
@@ -1031,6 +1032,18 @@ void invalidate_graph(psdp_ctx* c) {
     c->have_graph32 = false;
 }
 
+// The cold start X = Z = I, y = 0 (Algorithm 2) with the current problem data.
+psdp_status reset_to_cold_start(psdp_ctx* c) {
+    cudaStream_t st = c->stream;
+    launch_identity(st, c->nblk, c->n, c->d_X);
+    launch_identity(st, c->nblk, c->n, c->d_Z);
+    cudaMemsetAsync(c->d_y, 0, (size_t)c->K * sizeof(double), st);
+    cudaMemsetAsync(c->d_flag, 0, sizeof(int), st);
+    c->iters = 0;
+    c->mixed_failed = false;
+    return refresh(c);
+}
+
 }  // namespace
 
 // ======================================================================= ABI
@@ -1268,6 +1281,7 @@ psdp_status psdp_certify(psdp_ctx* c, int* verdict, double* minP, double* maxL) 
     cudaSetDevice(c->device);
     cudaStream_t st = c->stream;
     launch_bt(st, c, c->d_y, c->d_T1);
+    launch_sub_CR(st, c, c->d_T1);    // Lyapunov coefficients -(A^T P + P A + R)
     launch_block_mineig(st, c->nblk, c->n, c->d_T1, 1.0, c->d_tstep);
     launch_certify_finalize(st, c->nblk, c->n, c->d_tstep, c->L, c->d_cert);
     double h[3];
@@ -1304,6 +1318,7 @@ psdp_status psdp_grid_check(psdp_ctx* c, int N, double* minP, double* maxQ) {
         launch_grid_build(st, c, N, first, cnt, P, Aal);
         launch_bgemm(st, c->n, cnt, Aal, nullptr, 1, 1, P, nullptr, 1, 0, Q, nullptr, 1, 0, 1.0, 0.0);
         launch_bgemm(st, c->n, cnt, P, nullptr, 1, 0, Aal, nullptr, 1, 0, Q, nullptr, 1, 0, 1.0, 1.0);
+        launch_grid_addR(st, c, N, first, cnt, Q);
         launch_block_mineig(st, cnt, c->n, P, 1.0, eig);
         launch_block_mineig(st, cnt, c->n, Q, -1.0, eig + 2 * chunk);
         cudaMemcpyAsync(h.data(), eig, (size_t)4 * chunk * sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -1371,11 +1386,104 @@ psdp_status psdp_set_start(psdp_ctx* c, const double* y0, const double* xscale, 
     cudaMemcpyAsync(c->d_y, y0, (size_t)c->K * sizeof(double), cudaMemcpyHostToDevice, st);
     if (xscale) cudaMemcpyAsync(c->d_tstep, xscale, (size_t)c->nblk * sizeof(double), cudaMemcpyHostToDevice, st);
     launch_bt(st, c, c->d_y, c->d_T1);
+    launch_sub_CR(st, c, c->d_T1);    // B^T(y0) - C with the constant term's part of C
     launch_block_mineig(st, c->nblk, c->n, c->d_T1, 1.0, c->d_part);
     launch_start_fix(st, c, c->d_T1, c->d_part, xscale ? c->d_tstep : nullptr, theta);
     c->iters = 0;
     c->mixed_failed = false;
     return refresh(c);
+}
+
+psdp_status psdp_set_constant_term(psdp_ctx* c, int d_r, const double* R) {
+    if (!c || !R || d_r < 0 || d_r > c->d_p + c->d_a + c->d2) return PSDP_EINVAL;
+    const int l = c->l, n = c->n;
+    const int64_t Nr = hcard(l, d_r);
+    const size_t n2 = (size_t)c->n2;
+    for (size_t i = 0; i < (size_t)Nr * n2; ++i)
+        if (!std::isfinite(R[i])) return PSDP_EINVAL;
+    for (int64_t r = 0; r < Nr; ++r)
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < i; ++j)
+                if (R[r * n2 + (size_t)i * n + j] != R[r * n2 + (size_t)j * n + i]) return PSDP_EINVAL;
+    cudaSetDevice(c->device);
+    // exponents of W_{d_r} (lexicographic, (d_r, 0, ..., 0) first) and the
+    // Lyapunov blocks' coefficients sum_rho multinomial(e; gamma - rho) R_rho,
+    // e = d_p + d_a + d2 - d_r, formed on the host once
+    std::vector<std::vector<int>> Wr, Wg;
+    auto enumerate = [&](int d, std::vector<std::vector<int>>& out) {
+        std::vector<int> g(l, 0);
+        std::function<void(int, int)> rec = [&](int pos, int left) {
+            if (pos == l - 1) {
+                g[pos] = left;
+                out.push_back(g);
+                return;
+            }
+            for (int v = left; v >= 0; --v) {
+                g[pos] = v;
+                rec(pos + 1, left - v);
+            }
+        };
+        rec(0, d);
+    };
+    enumerate(d_r, Wr);
+    enumerate(c->d_p + c->d_a + c->d2, Wg);
+    if ((int64_t)Wr.size() != Nr || (int)Wg.size() != c->M) return PSDP_EINVAL;
+    const int e = c->d_p + c->d_a + c->d2 - d_r;
+    std::vector<double> lf(64, 0.0);
+    for (int k = 1; k < 64; ++k) lf[k] = lf[k - 1] + std::log((double)k);
+    std::vector<double> CR((size_t)c->M * n2, 0.0);
+    double c2 = 0.0;
+    for (int gi = 0; gi < c->M; ++gi) {
+        double* Cg = CR.data() + (size_t)gi * n2;
+        for (int64_t r = 0; r < Nr; ++r) {
+            bool ok = true;
+            double lm = lf[e];
+            for (int k = 0; k < l; ++k) {
+                const int dk = Wg[gi][k] - Wr[r][k];
+                if (dk < 0) ok = false;
+                else lm -= lf[dk];
+            }
+            if (!ok) continue;
+            const double m = std::round(std::exp(lm));    // multinomial(e; gamma - rho), an integer
+            for (size_t t = 0; t < n2; ++t) Cg[t] += m * R[r * n2 + t];
+        }
+        const double cd = c->cdiag[c->L + gi];
+        for (size_t t = 0; t < n2; ++t) c2 += Cg[t] * Cg[t];
+        for (int i = 0; i < n; ++i) c2 += 2.0 * cd * Cg[(size_t)i * n + i];
+    }
+    std::vector<int32_t> wr((size_t)Nr * l);
+    for (int64_t r = 0; r < Nr; ++r)
+        for (int k = 0; k < l; ++k) wr[(size_t)r * l + k] = Wr[r][k];
+    if (!c->d_CR) TRY(dalloc(&c->d_CR, (size_t)c->M * n2));
+    if (c->d_R) cudaFree(c->d_R);
+    if (c->d_Wr) cudaFree(c->d_Wr);
+    c->d_R = nullptr;
+    c->d_Wr = nullptr;
+    TRY(dalloc(&c->d_R, (size_t)Nr * n2));
+    TRY(dalloc(&c->d_Wr, (size_t)Nr * l));
+    cudaMemcpy(c->d_CR, CR.data(), CR.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->d_R, R, (size_t)Nr * n2 * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->d_Wr, wr.data(), wr.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    c->d_r = d_r;
+    c->Nr = (int)Nr;
+    c->c2_extra = c2;
+    invalidate_graph(c);
+    return reset_to_cold_start(c);
+}
+
+psdp_status psdp_set_objective(psdp_ctx* c, const double* a) {
+    if (!c || !a) return PSDP_EINVAL;
+    double s = 0.0;
+    for (int k = 0; k < c->K; ++k) {
+        if (!std::isfinite(a[k])) return PSDP_EINVAL;
+        s += a[k] * a[k];
+    }
+    cudaSetDevice(c->device);
+    if (!c->d_avec) TRY(dalloc(&c->d_avec, (size_t)c->K));
+    cudaMemcpy(c->d_avec, a, (size_t)c->K * sizeof(double), cudaMemcpyHostToDevice);
+    c->a_norm = std::sqrt(s);
+    invalidate_graph(c);
+    return reset_to_cold_start(c);
 }
 
 psdp_status psdp_get_iterate(psdp_ctx* c, double* X, double* Z, double* y) {

@@ -217,7 +217,7 @@ k_adj_combine(int n, int L0, int L, int M, int Na, const int32_t* __restrict__ b
 // out[h*Nt + q] = svec_adj(Q_h)_q - 2 sum_lambda svec_adj(A_lambda R_{h,lambda})_q - acoef
 __global__ void k_adj_finish(int n, int Nt, int L0, int Na, const double* __restrict__ adj,
                              const double* __restrict__ adj2, const int32_t* __restrict__ svec, double acoef,
-                             double* out, const int* skip) {
+                             const double* __restrict__ avec, double* out, const int* skip) {
     if (skip && *skip) return;
     const int n2 = n * n;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < L0 * Nt; t += gridDim.x * blockDim.x) {
@@ -230,20 +230,34 @@ __global__ void k_adj_finish(int n, int Nt, int L0, int Na, const double* __rest
             const double* N = adj2 + ((int64_t)h * Na + li) * n2;
             ly += (r == s) ? N[r * n + r] : N[r * n + s] + N[s * n + r];
         }
-        out[t] = val - 2.0 * ly - acoef;
+        out[t] = val - 2.0 * ly - (avec ? acoef * avec[t] : acoef);
     }
 }
 
 // ---------------------------------------------------------------- elementwise
-__global__ void k_ew_G(int nb, int n, const double* __restrict__ cdiag, const double* __restrict__ BTy,
-                       const double* __restrict__ Z, double* G) {
+// G = C - B^T(y) + Z; C = cdiag I on every block plus, when CR is given, the
+// constant term's coefficients on the Lyapunov blocks g >= L (CR[(g - L) n^2 + e])
+__global__ void k_ew_G(int nb, int n, int L, const double* __restrict__ cdiag, const double* __restrict__ CR,
+                       const double* __restrict__ BTy, const double* __restrict__ Z, double* G) {
     const int64_t n2 = (int64_t)n * n, total = n2 * nb;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int g = (int)(t / n2), e = (int)(t % n2);
-        const double c = (e / n == e % n) ? cdiag[g] : 0.0;
+        double c = (e / n == e % n) ? cdiag[g] : 0.0;
+        if (CR && g >= L) c += CR[t - (int64_t)L * n2];
         G[t] = c - BTy[t] + Z[t];
     }
 }
+
+// M[g] -= CR[g - L] on the Lyapunov blocks (the constant term of the generalised form)
+__global__ void k_sub_CR(int nb, int n, int L, const double* __restrict__ CR, double* Mb) {
+    const int64_t n2 = (int64_t)n * n, off = (int64_t)L * n2, total = n2 * (nb - L);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
+        Mb[off + t] -= CR[t];
+}
+
+// Q[pt] += R(alpha_pt) = sum_rho R_rho alpha^rho on the simplex lattice points of k_grid_build
+__global__ void k_grid_addR(int l, int n, int Nr, int N, int64_t first, const int32_t* __restrict__ Wr,
+                            const double* __restrict__ R, double* Q);
 
 __global__ void k_ew_pred(int64_t total, const double* __restrict__ G, const double* __restrict__ D, double* E,
                           double* dZh) {
@@ -325,36 +339,41 @@ __device__ double block_sum(double v, double* red) {
 }
 
 // part[g] = (tr(Z_g X_g), tr(X_g), ||G_g||^2, cdiag_g tr(X_g)); part[nb] = (sum y, ||BX-1||^2, ||BX||^2, 0)
-__global__ void k_partials(int nb, int n, int K, const double* __restrict__ X, const double* __restrict__ Z,
+__global__ void k_partials(int nb, int n, int K, int L, const double* __restrict__ X, const double* __restrict__ Z,
                            const double* __restrict__ G, const double* __restrict__ cdiag,
+                           const double* __restrict__ CR, const double* __restrict__ avec,
                            const double* __restrict__ y, const double* __restrict__ BX, double* part) {
     __shared__ double red[32];
     const int g = blockIdx.x;
     const int64_t n2 = (int64_t)n * n;
     if (g < nb) {
-        double zx = 0.0, tx = 0.0, gg = 0.0;
+        double zx = 0.0, tx = 0.0, gg = 0.0, cx = 0.0;
+        const double* Cg = (CR && g >= L) ? CR + (int64_t)(g - L) * n2 : nullptr;
         for (int e = threadIdx.x; e < n2; e += blockDim.x) {
             const double x = X[g * n2 + e];
             zx = fma(Z[g * n2 + e], x, zx);
             const double gv = G[g * n2 + e];
             gg = fma(gv, gv, gg);
             if (e / n == e % n) tx += x;
+            if (Cg) cx = fma(Cg[e], x, cx);   // tr(C_g X_g), C_g symmetric
         }
         zx = block_sum(zx, red);
         tx = block_sum(tx, red);
         gg = block_sum(gg, red);
+        if (Cg) cx = block_sum(cx, red);
         if (threadIdx.x == 0) {
             part[4 * g + 0] = zx;
             part[4 * g + 1] = tx;
             part[4 * g + 2] = gg;
-            part[4 * g + 3] = cdiag[g] * tx;
+            part[4 * g + 3] = cdiag[g] * tx + cx;
         }
     } else {
         double sy = 0.0, r2 = 0.0, b2 = 0.0;
         for (int k = threadIdx.x; k < K; k += blockDim.x) {
-            sy += y[k];
+            const double ak = avec ? avec[k] : 1.0;
+            sy = fma(ak, y[k], sy);
             const double b = BX[k];
-            r2 = fma(b - 1.0, b - 1.0, r2);
+            r2 = fma(b - ak, b - ak, r2);
             b2 = fma(b, b, b2);
         }
         sy = block_sum(sy, red);
@@ -370,7 +389,8 @@ __global__ void k_partials(int nb, int n, int K, const double* __restrict__ X, c
 }
 
 __global__ void k_finalize(int nb, int n, int K, const double* __restrict__ part, const double* __restrict__ cdiag,
-                           double sigma, int iter, double* scal, double* info, int* flag) {
+                           double c2_extra, double a_norm, double sigma, int iter, double* scal, double* info,
+                           int* flag) {
     // lane t sums blocks g = t (mod 32) in order, then a fixed xor tree: the
     // same bit pattern on every replay, 32 short chains instead of one long one
     double zx = 0, tx = 0, gg = 0, phi = 0, c2 = 0;
@@ -391,8 +411,8 @@ __global__ void k_finalize(int nb, int n, int K, const double* __restrict__ part
     }
     if (threadIdx.x != 0) return;
     const double psi = part[4 * nb + 0];
-    const double pres = sqrt(part[4 * nb + 1]) / (1.0 + sqrt((double)K));
-    const double dres = sqrt(gg) / (1.0 + sqrt(c2));
+    const double pres = sqrt(part[4 * nb + 1]) / (1.0 + a_norm);
+    const double dres = sqrt(gg) / (1.0 + sqrt(c2 + c2_extra));
     const double relgap = fabs(psi - phi) / (1.0 + fabs(psi) + fabs(phi));
     const double mu = sigma * zx / ((double)nb * n);
     scal[SC_TRZX] = zx;
@@ -576,6 +596,26 @@ __global__ void k_grid_build(int l, int n, int Nt, int L0, int Na, int N, int64_
     }
 }
 
+__global__ void k_grid_addR(int l, int n, int Nr, int N, int64_t first, const int32_t* __restrict__ Wr,
+                            const double* __restrict__ R, double* Q) {
+    const int pt = blockIdx.y;
+    int gam[PSDP_MAX_L];
+    unrank(l, N, first + pt, gam);
+    double al[PSDP_MAX_L];
+    for (int i = 0; i < l; ++i) al[i] = (double)gam[i] / N;
+    const int n2 = n * n;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n2; e += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int r = 0; r < Nr; ++r) {
+            double w = 1.0;
+            for (int k = 0; k < l; ++k)
+                for (int c = 0; c < Wr[r * l + k]; ++c) w *= al[k];
+            s = fma(w, R[(int64_t)r * n2 + e], s);
+        }
+        Q[(int64_t)pt * n2 + e] += s;
+    }
+}
+
 // Warm start: Z_g = (B^T(y0) - C)_g + max(0, theta / x_g - lambda_min) I (the
 // block's smallest eigenvalue is eig[2g]), X_g = x_g I.
 __global__ void k_start_fix(int nb, int n, const double* __restrict__ cdiag, const double* __restrict__ BTy,
@@ -640,11 +680,12 @@ void launch_b(cudaStream_t st, psdp_ctx* c, const double* W, double* out, double
     const int np = c->L0 * c->Na;
     launch_bgemm(st, n, np, c->d_A, ix, 0, 0, c->d_adj, ix + np, 0, 0, c->d_adj2, ix + 2 * np, 0, 0, 1.0, 0.0, skip);
     k_adj_finish<<<grid_for((int64_t)c->L0 * c->Nt), kThreads, 0, st>>>(n, c->Nt, c->L0, c->Na, c->d_adj, c->d_adj2,
-                                                                        c->d_svec, acoef, out, skip);
+                                                                        c->d_svec, acoef, c->d_avec, out, skip);
 }
 
 void launch_ew_G(cudaStream_t st, psdp_ctx* c, const double* BTy, const double* Z, double* G) {
-    k_ew_G<<<grid_for((int64_t)c->nblk * c->n2), kThreads, 0, st>>>(c->nblk, c->n, c->d_cdiag, BTy, Z, G);
+    k_ew_G<<<grid_for((int64_t)c->nblk * c->n2), kThreads, 0, st>>>(c->nblk, c->n, c->L, c->d_cdiag, c->d_CR, BTy, Z,
+                                                                    G);
 }
 void launch_ew_pred(cudaStream_t st, psdp_ctx* c, const double* G, const double* D, double* E, double* dZh) {
     const int64_t total = (int64_t)c->nblk * c->n2;
@@ -671,11 +712,12 @@ void launch_identity(cudaStream_t st, int nb, int n, double* X) {
     k_identity<<<grid_for(total), kThreads, 0, st>>>(total, n, X);
 }
 void launch_partials(cudaStream_t st, psdp_ctx* c) {
-    k_partials<<<c->nblk + 1, kThreads, 0, st>>>(c->nblk, c->n, c->K, c->d_X, c->d_Z, c->d_G, c->d_cdiag, c->d_y,
-                                                 c->d_BX, c->d_part);
+    k_partials<<<c->nblk + 1, kThreads, 0, st>>>(c->nblk, c->n, c->K, c->L, c->d_X, c->d_Z, c->d_G, c->d_cdiag,
+                                                 c->d_CR, c->d_avec, c->d_y, c->d_BX, c->d_part);
 }
 void launch_finalize(cudaStream_t st, psdp_ctx* c, int iter) {
-    k_finalize<<<1, 32, 0, st>>>(c->nblk, c->n, c->K, c->d_part, c->d_cdiag, c->opt.sigma, iter, c->d_scal, c->d_info,
+    k_finalize<<<1, 32, 0, st>>>(c->nblk, c->n, c->K, c->d_part, c->d_cdiag, c->c2_extra,
+                                 c->d_avec ? c->a_norm : sqrt((double)c->K), c->opt.sigma, iter, c->d_scal, c->d_info,
                                  c->d_flag);
 }
 void launch_steplen(cudaStream_t st, psdp_ctx* c) {
@@ -720,6 +762,17 @@ void launch_start_fix(cudaStream_t st, psdp_ctx* c, const double* BTy, const dou
                       double theta) {
     k_start_fix<<<grid_for((int64_t)c->nblk * c->n2), kThreads, 0, st>>>(c->nblk, c->n, c->d_cdiag, BTy, eig, xs,
                                                                         theta, c->d_X, c->d_Z);
+}
+
+void launch_sub_CR(cudaStream_t st, psdp_ctx* c, double* blocks) {
+    if (!c->d_CR) return;
+    k_sub_CR<<<grid_for((int64_t)c->M * c->n2), kThreads, 0, st>>>(c->nblk, c->n, c->L, c->d_CR, blocks);
+}
+
+void launch_grid_addR(cudaStream_t st, psdp_ctx* c, int N, int64_t first, int cnt, double* Q) {
+    if (!c->d_R) return;
+    dim3 g((c->n2 + kThreads - 1) / kThreads, cnt);
+    k_grid_addR<<<g, kThreads, 0, st>>>(c->l, c->n, c->Nr, N, first, c->d_Wr, c->d_R, Q);
 }
 
 void launch_certify_finalize(cudaStream_t st, int count, int n, const double* eig, int L, double* out) {

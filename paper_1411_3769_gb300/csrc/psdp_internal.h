@@ -72,6 +72,14 @@ struct psdp_ctx {
     double *d_A = nullptr;                      // [Na][n][n]
     double *d_H = nullptr;                      // [L0][M][n][n]
     double *d_cdiag = nullptr;                  // [nblk]
+    // generalised form (Sec. III-C): constant term R(alpha) and the dual objective a
+    int d_r = -1, Nr = 0;                       // degree of R, card W_{d_r}
+    double *d_R = nullptr;                      // R coefficients [Nr][n][n]
+    int32_t *d_Wr = nullptr;                    // their exponents [Nr][l]
+    double *d_CR = nullptr;                     // R's part of the Lyapunov blocks of C [M][n][n]
+    double *d_avec = nullptr;                   // objective a [K]; null: all ones (Eq. a)
+    double c2_extra = 0.0;                      // ||C||_F^2 beyond the cdiag part
+    double a_norm = 0.0;                        // ||a|| when d_avec is set
 
     // ----- iterate and per-block work arrays, each [nblk][n][n]
     double *d_X = nullptr, *d_Z = nullptr, *d_G = nullptr, *d_Y = nullptr;
@@ -238,6 +246,10 @@ void launch_start_fix(cudaStream_t st, psdp_ctx* c, const double* BTy, const dou
 
 // certificate / grid
 void launch_certify_finalize(cudaStream_t st, int count, int n, const double* eig, int L, double* out);
+// blocks[g] -= CR[g - L] on the Lyapunov blocks (no-op without a constant term)
+void launch_sub_CR(cudaStream_t st, psdp_ctx* c, double* blocks);
+// Q[pt] += R(alpha_pt) on the lattice points of launch_grid_build (no-op without R)
+void launch_grid_addR(cudaStream_t st, psdp_ctx* c, int N, int64_t first, int cnt, double* Q);
 void launch_grid_build(cudaStream_t st, psdp_ctx* c, int N, int64_t first, int cnt, double* P, double* Aal);
 
 // FP64 throughput probe
