@@ -338,10 +338,254 @@ k_ozaki_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUt
     }
 }
 
+
+// Tiles of one Ozaki product in the order every role of the persistent kernel
+// walks them: batch by batch, column tile by column tile (nt), row tiles
+// (mt) inside a column; with lower only the row tiles that reach the diagonal,
+// mt >= nt * 64 / 128.
+struct OzWalk {
+    int MT, NT, batch, lower, b, nt, off;
+    __device__ OzWalk(int M, int N, int batch_, int lower_, int start)
+        : MT((M + OZ_BM - 1) / OZ_BM), NT((N + OZ_BN - 1) / OZ_BN), batch(batch_), lower(lower_), b(0), nt(0),
+          off(start) { settle(); }
+    __device__ int first(int c) const { return lower ? (c * OZ_BN) / OZ_BM : 0; }
+    __device__ int len(int c) const { return MT - first(c); }
+    __device__ void settle() {
+        while (b < batch && off >= len(nt)) {
+            off -= len(nt);
+            if (++nt == NT) {
+                nt = 0;
+                ++b;
+            }
+        }
+    }
+    __device__ bool valid() const { return b < batch; }
+    __device__ int mt() const { return first(nt) + off; }
+    __device__ void advance(int step) {
+        off += step;
+        settle();
+    }
+};
+
+constexpr int OZP_THREADS = 320;   // warp 0 TMA, warp 1 MMA and TMEM, warps 2-9 epilogue
+
+// Persistent form of k_ozaki_gemm: one CTA per SM (or fewer) walks the tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...  The epilogue warps drain a tile's
+// eight level accumulators into registers, combined to one FP64 value per
+// element, and release TMEM at once (barrier tfree), so the MMAs of the next
+// tile run while they read, update and write C; the TMA producer runs ahead
+// into the next tile's stages meanwhile.  Barriers: full/empty per stage,
+// accb (MMA -> epilogue, one phase per tile), tfree (epilogue -> MMA, eight
+// warp arrivals per tile).  Every wait is bounded; after a timeout the roles
+// stop walking and the CTA unwinds with FL_TIMEOUT raised.
+__global__ void __launch_bounds__(OZP_THREADS, 1)
+k_ozaki_gemm_persist(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
+                     const int32_t* __restrict__ eA, const int32_t* __restrict__ eB, int a_rows, int a_row0,
+                     int b_rows, int b_row0, int M, int N, int batch, const int32_t* __restrict__ kd, int kd_uniform,
+                     int k_off, double* C, int64_t ldc, int64_t c_batch, double alpha, double beta, int lower,
+                     int* flag) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t base_raw = smem_u32(smem_raw);
+    const uint32_t base = (base_raw + 1023u) & ~1023u;
+    uint8_t* gbase = smem_raw + (base - base_raw);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + OZ_STAGES * OZ_STAGE);
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * OZ_STAGES + 3);
+    __shared__ int abort_flag;
+    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * OZ_STAGES;
+    const uint32_t accb = full0 + 16 * OZ_STAGES, tfree = accb + 8, drain = accb + 16;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < OZ_STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(accb, 1);
+        mbar_init(tfree, 8);
+        mbar_init(drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(8 * OZ_BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_holder;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer: every slice of both operands for 32 of k per stage, tile after tile
+        int g = 0;
+        for (OzWalk t(M, N, batch, lower, blockIdx.x); t.valid() && !*(volatile int*)&abort_flag;
+             t.advance(gridDim.x)) {
+            const int nk = (oz_depth(kd, kd_uniform, t.b, k_off) + OZ_BK - 1) / OZ_BK;
+            const int m0 = t.mt() * OZ_BM, n0 = t.nt * OZ_BN;
+            for (int kt = 0; kt < nk; ++kt, ++g) {
+                const int s = g % OZ_STAGES;
+                if (g >= OZ_STAGES && !mbar_wait(empty0 + 8 * s, ((g / OZ_STAGES) - 1) & 1, flag)) {
+                    abort_flag = 1;
+                    break;
+                }
+                const uint32_t st = base + s * OZ_STAGE;
+                const uint32_t fb = full0 + 8 * s;
+                mbar_expect_tx(fb, OZ_STAGE);
+#pragma unroll
+                for (int p = 0; p < OZ_S; ++p)
+                    tma_load_3d(st + p * OZ_TA, &mA, fb, kt * OZ_BK, a_row0 + m0, t.b * OZ_S + p);
+#pragma unroll
+                for (int q = 0; q < OZ_S; ++q)
+                    tma_load_3d(st + OZ_S * OZ_TA + q * OZ_TB, &mB, fb, kt * OZ_BK, b_row0 + n0, t.b * OZ_S + q);
+            }
+        }
+        // every issued stage has landed before the CTA may exit
+        for (int q = (g > OZ_STAGES ? g - OZ_STAGES : 0); q < g; ++q)
+            mbar_wait(full0 + 8 * (q % OZ_STAGES), (q / OZ_STAGES) & 1, flag);
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: tile i waits until the epilogue has drained tile i - 1's accumulators
+        constexpr uint32_t idesc = oz_idesc();
+        int g = 0, i = 0;
+        bool issued = false;
+        for (OzWalk t(M, N, batch, lower, blockIdx.x); t.valid() && !*(volatile int*)&abort_flag;
+             t.advance(gridDim.x), ++i) {
+            if (i >= 1 && !mbar_wait(tfree, (i - 1) & 1, flag)) {
+                abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int nk = (oz_depth(kd, kd_uniform, t.b, k_off) + OZ_BK - 1) / OZ_BK;
+            for (int kt = 0; kt < nk; ++kt, ++g) {
+                const int s = g % OZ_STAGES;
+                if (!mbar_wait(full0 + 8 * s, (g / OZ_STAGES) & 1, flag)) {
+                    abort_flag = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t st = base + s * OZ_STAGE;
+#pragma unroll
+                for (int kk = 0; kk < OZ_ROW / 32; ++kk) {
+#pragma unroll
+                    for (int p = 0; p < OZ_S; ++p) {
+#pragma unroll
+                        for (int q = 0; q < OZ_S - p; ++q) {
+                            const uint32_t acc = (kt > 0 || kk > 0 || p > 0) ? 1u : 0u;
+                            mma_bf16(tmem + (uint32_t)(OZ_BN * (p + q)), sdesc64(st + p * OZ_TA + kk * 32),
+                                     sdesc64(st + OZ_S * OZ_TA + q * OZ_TB + kk * 32), idesc, acc);
+                        }
+                    }
+                }
+                issued = true;
+                mma_commit(empty0 + 8 * s);
+            }
+            if (*(volatile int*)&abort_flag) break;
+            mma_commit(accb);        // a tile of depth 0 commits too: its epilogue reads zeros
+        }
+        // all MMAs complete before TMEM is released
+        if (issued) {
+            mma_commit(drain);
+            mbar_wait(drain, 0, flag);
+        }
+    } else if (warp >= 2) {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 and columns 32 h .. +31, h = (w - 2) / 4
+        const int quad = warp & 3, half = (warp - 2) >> 2;
+        const int amode = (alpha == 1.0) ? 0 : (alpha == -1.0 ? 1 : 2);
+        const int bmode = (beta == 0.0) ? 0 : (beta == 1.0 ? 1 : 2);
+        int i = 0;
+        for (OzWalk t(M, N, batch, lower, blockIdx.x); t.valid(); t.advance(gridDim.x), ++i) {
+            const int Kd = oz_depth(kd, kd_uniform, t.b, k_off);
+            const int m0 = t.mt() * OZ_BM, n0 = t.nt * OZ_BN;
+            const int row = m0 + 32 * quad + lane;
+            const int jc = n0 + 32 * half;
+            // warp-uniform decision: the TMEM loads below are warp-collective
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(accb, i & 1, flag));
+            if (!ok) {
+                abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // drain: the eight levels of 32 columns, combined exactly to (Va 2^28 + Vb)
+            // in FP64 (one rounding); the 2^(e_i + f_j - 63) scale is applied below
+            double w[32];
+#pragma unroll
+            for (int c0 = 0; c0 < 32; c0 += 8) {
+                uint32_t r[OZ_S][8];
+                if (Kd > 0) {
+#pragma unroll
+                    for (int tl = 0; tl < OZ_S; ++tl)
+                        tmem_ld8_nw(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(OZ_BN * tl + 32 * half + c0),
+                                    r[tl]);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                } else {
+#pragma unroll
+                    for (int tl = 0; tl < OZ_S; ++tl)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) r[tl][j] = 0u;
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    long long T[OZ_S];
+#pragma unroll
+                    for (int tl = 0; tl < OZ_S; ++tl) T[tl] = (long long)__float2int_rn(__uint_as_float(r[tl][j]));
+                    const long long Va = ((T[0] * 128 + T[1]) * 128 + T[2]) * 128 + T[3];
+                    const long long Vb = ((T[4] * 128 + T[5]) * 128 + T[6]) * 128 + T[7];
+                    w[c0 + j] = fma(oz_i2d(Va), 268435456.0, oz_i2d(Vb));
+                }
+            }
+            // TMEM free for the next tile's MMAs
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tfree);
+            // C update under the next tile's MMAs
+            if (row < M) {
+                const int ei = eA[(int64_t)t.b * a_rows + a_row0 + row];
+                const int32_t* eBb = eB + (int64_t)t.b * b_rows + b_row0;
+                double* Cb = C + (int64_t)t.b * c_batch;
+#pragma unroll
+                for (int c0 = 0; c0 < 32; c0 += 8) {
+                    double cold[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int col = jc + c0 + j;
+                        cold[j] =
+                            (bmode != 0 && col < N && !(lower && row < col)) ? Cb[(int64_t)col * ldc + row] : 0.0;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int col = jc + c0 + j;
+                        if (col >= N || (lower && row < col)) continue;
+                        double v = w[c0 + j];
+                        const int E = ei + eBb[col] - 63;
+                        if (v != 0.0) {
+                            const long long bits = __double_as_longlong(v);
+                            const int be = (int)((bits >> 52) & 0x7FF) + E;
+                            v = (be <= 0 || be >= 2047) ? ldexp(v, E)
+                                                        : __longlong_as_double(bits + ((long long)E << 52));
+                        }
+                        if (amode) v = (amode == 1) ? -v : alpha * v;
+                        Cb[(int64_t)col * ldc + row] =
+                            (bmode == 0) ? v : (bmode == 1 ? cold[j] + v : fma(beta, cold[j], v));
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(8 * OZ_BN));
+    }
+}
+
+constexpr size_t ozp_smem_bytes() { return (size_t)OZ_STAGES * OZ_STAGE + 1024 + 8 * (2 * OZ_STAGES + 3) + 16; }
+
 }  // namespace
 
 void init_attrs_ozaki(int smem_optin) {
     set_max_dynamic_smem((const void*)k_ozaki_gemm, smem_optin);
+    set_max_dynamic_smem((const void*)k_ozaki_gemm_persist, smem_optin);
     set_max_dynamic_smem((const void*)k_ozaki_split, smem_optin);
 }
 
@@ -360,7 +604,7 @@ void launch_ozaki_split(cudaStream_t st, const double* src, int64_t ld, int64_t 
 bool launch_ozaki_gemm(cudaStream_t st, const uint16_t* As, int a_rows, int a_row0, const int32_t* eA,
                        const uint16_t* Bs, int b_rows, int b_row0, const int32_t* eB, int M, int N, int dpad,
                        int batch, const int32_t* kd, int kd_uniform, int k_off, double* C, int64_t ldc,
-                       int64_t c_batch, double alpha, double beta, int lower, int* flag) {
+                       int64_t c_batch, double alpha, double beta, int lower, int* flag, int ctas) {
     if (M <= 0 || N <= 0 || batch <= 0) return true;
     if (dpad % OZ_BK != 0 || dpad > kOzakiMaxDepth || a_row0 + M > a_rows || b_row0 + N > b_rows || a_row0 < 0 ||
         b_row0 < 0)
@@ -371,10 +615,22 @@ bool launch_ozaki_gemm(cudaStream_t st, const uint16_t* As, int a_rows, int a_ro
         !tc_make_map_swz(&mB, Bs, true, dpad, b_rows, (int64_t)batch * OZ_S, dpad, (int64_t)b_rows * dpad, OZ_BK,
                          OZ_BN, 64))
         return false;
-    dim3 grid((N + OZ_BN - 1) / OZ_BN, (M + OZ_BM - 1) / OZ_BM, batch);
-    k_ozaki_gemm<<<grid, OZ_THREADS, oz_smem_bytes(), st>>>(mA, mB, eA, eB, a_rows, a_row0, b_rows, b_row0, M, N, kd,
-                                                             kd_uniform, k_off, C, ldc, c_batch, alpha, beta, lower,
-                                                             flag);
+    // persistent: one CTA per SM (at most one per tile) walks the tiles
+    const int64_t MT = (M + OZ_BM - 1) / OZ_BM, NT = (N + OZ_BN - 1) / OZ_BN;
+    int64_t tiles = 0;
+    for (int64_t c = 0; c < NT; ++c) tiles += lower ? MT - (c * OZ_BN) / OZ_BM : MT;
+    tiles *= batch;
+    if (tiles <= 0) return true;
+    if (ctas <= 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        ctas = sms > 0 ? sms : 1;
+    }
+    const int grid = (int)std::min<int64_t>(tiles, ctas);
+    k_ozaki_gemm_persist<<<grid, OZP_THREADS, ozp_smem_bytes(), st>>>(mA, mB, eA, eB, a_rows, a_row0, b_rows, b_row0,
+                                                                      M, N, batch, kd, kd_uniform, k_off, C, ldc,
+                                                                      c_batch, alpha, beta, lower, flag);
     return true;
 }
 

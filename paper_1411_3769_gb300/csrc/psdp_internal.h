@@ -288,11 +288,12 @@ void launch_ozaki_split(cudaStream_t st, const double* src, int64_t ld, int64_t 
                         int rows, const int32_t* kdv, int kd_uniform, int k_off, int dpad, int batch, uint16_t* out,
                         int32_t* ex);
 // C_b[j * ldc + i] = alpha sum_k A_b[i][k] B_b[j][k] + beta C_b[...] (i >= j only when lower),
-// A_b's rows a_row0 + i (i < M) of slice arrays of a_rows rows (exponents eA[b][a_rows]), B_b likewise
+// A_b's rows a_row0 + i (i < M) of slice arrays of a_rows rows (exponents eA[b][a_rows]), B_b likewise;
+// a persistent launch of min(tiles, ctas) CTAs (ctas <= 0: one per SM)
 bool launch_ozaki_gemm(cudaStream_t st, const uint16_t* As, int a_rows, int a_row0, const int32_t* eA,
                        const uint16_t* Bs, int b_rows, int b_row0, const int32_t* eB, int M, int N, int dpad,
                        int batch, const int32_t* kd, int kd_uniform, int k_off, double* C, int64_t ldc,
-                       int64_t c_batch, double alpha, double beta, int lower, int* flag);
+                       int64_t c_batch, double alpha, double beta, int lower, int* flag, int ctas = 0);
 
 // mixed precision (k_mixed.cu)
 void launch_schur_pack32(cudaStream_t st, psdp_ctx* c);
