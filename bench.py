@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--dfma", type=int, default=1, help="time one FP64-FMA-only step of the headline workload")
     ap.add_argument("--mid", type=int, default=1, help="also measure the mid workload in FP64")
     ap.add_argument("--mid-steps", type=int, default=30)
+    ap.add_argument("--batch", type=int, default=64, help="instances of the batched-vs-sequential record (0: skip)")
     ap.add_argument("--mixed-workloads", default="mid,large")
     ap.add_argument("--extra-items", default="err,ex2,syrk,batch,warm")
     ap.add_argument("--err-large", type=int, default=1, help="also solve the large workload in plain FP64")
@@ -423,6 +424,48 @@ def measure_batch(bd, synth, count, device, n_range=(8, 48), precision=1):
             "setup_s": t1 - t0, "solve_s": t2 - t1, "certify_s": t3 - t2, "time_to_all_certificates_s": t3 - t0,
             "certified": int(sum(verdicts)), "status_counts": {s: status.count(s) for s in sorted(set(status))},
             "K_max": max(Ks), "K_mean": float(np.mean(Ks))}
+
+
+def measure_batch_vs_sequential(bd, synth, count, device, precision=0):
+    """The same uneven instances (the batch workload's draw: n ~ U{8..48}, l ~
+    U{2,3,4}, d_p ~ U{1,2}, d1 ~ U{1..4}, s ~ U[0.05, 3]) solved together
+    (psdp_solve_batch: one graph launch per interior-point iteration over every
+    unfinished instance) and one after another (psdp_solve each), set-up and
+    certificates included on both sides; statuses and iteration counts must agree."""
+    inst = synth.batch_instances(count, base_seed=1000)
+
+    def setup_all():
+        return [bd.psdp_setup(d["n"], d["l"], d["d_p"], d["d1"], d["A"],
+                              bd.psdp_default_opts(precision=precision, device=device)) for d in inst]
+
+    t0 = time.perf_counter()
+    hs = setup_all()
+    try:
+        st_b, it_b = bd.psdp_solve_batch(hs)
+        v_b = [bd.psdp_certify(h)[0] for h in hs]
+    finally:
+        for h in hs:
+            bd.psdp_destroy(h)
+    t1 = time.perf_counter()
+    st_s, it_s, v_s = [], [], []
+    for d in inst:
+        h = bd.psdp_setup(d["n"], d["l"], d["d_p"], d["d1"], d["A"],
+                          bd.psdp_default_opts(precision=precision, device=device))
+        try:
+            s, it, _ = bd.psdp_solve(h)
+            st_s.append(bd.STATUS[s])
+            it_s.append(it)
+            v_s.append(bd.psdp_certify(h)[0])
+        finally:
+            bd.psdp_destroy(h)
+    t2 = time.perf_counter()
+    steps = int(sum(it_b))
+    return {"instances": count, "precision": "mixed" if precision else "fp64",
+            "K_max": max(polya_K(d) for d in inst), "newton_steps": steps,
+            "batched_s": t1 - t0, "sequential_s": t2 - t1, "batched_steps_per_s": steps / (t1 - t0),
+            "sequential_steps_per_s": int(sum(it_s)) / (t2 - t1), "speedup": (t2 - t1) / (t1 - t0),
+            "same_outcomes": list(st_b) == st_s and list(it_b) == it_s and v_b == v_s,
+            "certified": int(sum(v_b)), "status_counts": {s: list(st_b).count(s) for s in sorted(set(st_b))}}
 
 
 def polya_K(d):
@@ -795,6 +838,14 @@ def run_ours(args):
                "kernels": km, "clocks": clk_m.summary(),
                "time_to_certificate_eps_1e-8": {k: v for k, v in tm.items() if k != "y"}}
 
+    # ---- many uneven instances: batched against one after another
+    batch = {}
+    if args.batch > 0:
+        try:
+            batch = measure_batch_vs_sequential(bd, synth, args.batch, local)
+        except Exception as exc:
+            batch = {"error": str(exc)[:200]}
+
     # ---- the oracle on a bounded sample of the headline workload
     est = [oracle_sample(A, w)[0] for _ in range(max(1, args.cpu_samples))]
     cpu = {"value": len(est) / sum(est), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -815,7 +866,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": (ttc["P_bytes"] + 16 * 8 * iters + 4 * iters) / max(iters, 1),
                     "time_to_certificate_s": ttc["seconds"], "newton_steps": iters, "status": ttc["status"],
                     "verdict": ttc["verdict"], "relgap": ttc["relgap"]},
-            "fp64_dfma_step": dfma, "mixed": mixed, "mid_fp64": mid,
+            "fp64_dfma_step": dfma, "mixed": mixed, "mid_fp64": mid, "batch": batch,
             "fp64_peaks_tflops": {"dfma": dfma_peak, "dmma": dmma_peak},
             "gpu_launches": int(work["kernels_per_step"]) * args.steps,
             "clocks": clk.summary(),

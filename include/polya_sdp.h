@@ -141,6 +141,22 @@ psdp_status psdp_solve_batch(psdp_ctx** ctx, int count, psdp_status* status, int
  * may be NULL. */
 psdp_status psdp_autotune(psdp_ctx* c, const char* cache_path, int* choice, double* ms3);
 
+/* The same over a chosen set of step configurations (no counterpart in the
+ * paper): bit k of mask enables candidate k,
+ *   0 FP64 with the automatic engines (psdp_opts.fp64_gemm),
+ *   1 mixed precision, 64-column FP32 Cholesky panels,
+ *   2 mixed precision, 128-column FP32 Cholesky panels,
+ *   3 FP64 with FP64-FMA contractions (Schur tiles 80 x 80 or 64 x 64 by n^2,
+ *     32 x 32 Cholesky bulk tiles, one-shot or persistent by the tile waves),
+ *   4 FP64 with Ozaki-scheme contractions (128 x 64 tensor-core tiles, 256-column
+ *     outer Cholesky panels),
+ *   5 FP64 with the Ozaki Schur contraction and the FP64-FMA Cholesky.
+ * The cache key is (n, l, d_p, d1, d2, d_a, mask); ms (may be NULL) receives
+ * PSDP_TUNE_CANDIDATES per-candidate step times in ms (-1 if not timed).  The
+ * fastest candidate is applied to the context.  psdp_autotune is mask 7. */
+#define PSDP_TUNE_CANDIDATES 6
+psdp_status psdp_autotune_ex(psdp_ctx* c, const char* cache_path, unsigned mask, int* choice, double* ms);
+
 /* Certificate of Theorems 1-2 from the current y: P_h = smat(y_h) (Root step 4);
  * every P-side coefficient sum_h beta_{h,gamma} P_h (Eq. LMI_3) and every negated
  * Lyapunov coefficient -sum_h (H^T P_h + P_h H) (Eq. LMI_4) must have its smallest

@@ -32,7 +32,7 @@ EXPORTS = ("psdp_default_opts", "psdp_setup", "psdp_sizes", "psdp_step", "psdp_s
            "psdp_tc_gemm_noalloc", "psdp_solve_batch", "psdp_autotune", "psdp_set_start", "psdp_mlp_create",
            "psdp_mlp_destroy", "psdp_mlp_params", "psdp_mlp_grads", "psdp_mlp_train", "psdp_mlp_predict",
            "psdp_fp64_peaks", "psdp_ozaki_gemm_check", "psdp_engines", "psdp_set_constant_term",
-           "psdp_set_objective")
+           "psdp_set_objective", "psdp_autotune_ex")
 
 
 class Opts(C.Structure):
@@ -106,6 +106,7 @@ def _lib():
             "psdp_engines": (C.c_int, [vp, ip]),
             "psdp_set_constant_term": (C.c_int, [vp, C.c_int, dp]),
             "psdp_set_objective": (C.c_int, [vp, dp]),
+            "psdp_autotune_ex": (C.c_int, [vp, C.c_char_p, C.c_uint, C.POINTER(C.c_int), dp]),
             "psdp_ozaki_gemm_check": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_double, C.c_double,
                                                 C.c_int]),
         }
@@ -386,6 +387,17 @@ def psdp_autotune(h, cache_path: str | None = None) -> tuple[int, np.ndarray]:
     ms = np.zeros(3)
     _check(_lib().psdp_autotune(h, cache_path.encode() if cache_path else None, C.byref(ch), _dp(ms)),
            "psdp_autotune")
+    return ch.value, ms
+
+
+TUNE_CANDIDATES = ("fp64-auto", "mixed-64", "mixed-128", "fp64-fma", "fp64-ozaki", "fp64-ozaki-schur")
+
+
+def psdp_autotune_ex(h, mask: int, cache_path: str | None = None) -> tuple[int, np.ndarray]:
+    ch = C.c_int(-1)
+    ms = np.zeros(len(TUNE_CANDIDATES))
+    _check(_lib().psdp_autotune_ex(h, cache_path.encode() if cache_path else None, mask, C.byref(ch), _dp(ms)),
+           "psdp_autotune_ex")
     return ch.value, ms
 
 

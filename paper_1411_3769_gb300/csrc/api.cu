@@ -165,10 +165,10 @@ constexpr int kCritSms64 = 8;
 constexpr int kOneShotWaves = 64;
 
 // Omega = L L^T with the trailing updates by the Ozaki scheme: outer panels of
-// kOzakiMaxDepth (256) columns, each factored as 32-column inner panels by the
-// FP64 kernels (diagonal factor and inverse, panel solve, update of the outer
-// panel's remaining columns), then FP64-accurate updates of depth 256 from the
-// outer panel's slices.  Look-ahead of depth one at the outer level:
+// kOzakiMaxDepth (256) columns, each factored as 32-column inner panels (FP64
+// diagonal factor and inverse, FP64 panel solve, update of the outer panel's
+// remaining columns), then FP64-accurate updates of depth 256 from the outer
+// panel's slices.  Look-ahead of depth one at the outer level:
 //   crit: inner(P), split(P) | wait bulk(P-1) | next(P): the next outer panel's columns
 //   main: wait split(P) | bulk(P): every column right of the next outer panel
 // so outer panel P+1 is factored while bulk(P) runs.  bulk(P-1) and next(P)
@@ -176,6 +176,7 @@ constexpr int kOneShotWaves = 64;
 // slice buffer bulk(P-1) read, after the same wait.  Every element receives its
 // updates in panel order, and the 32 x 32 diagonal inverses are those the
 // triangular solves use.
+constexpr int kOzakiInnerMinRows = 8192;
 void enqueue_cholesky_ozaki(psdp_ctx* c) {
     cudaStream_t st = c->stream, cs = c->crit;
     const int K = c->K, nb = c->nb_chol, OB = kOzakiMaxDepth;
@@ -201,9 +202,20 @@ void enqueue_cholesky_ozaki(psdp_ctx* c) {
             }
             const int nrem = J0 + wo - (j0 + w);      // outer-panel columns right of this inner panel
             if (nrem > 0) {
+                // the outer panel's remaining columns, all rows below (lower part): by the
+                // Ozaki scheme from the inner panel's own slices (depth w = 32) where the
+                // rows are many (large workload: 99 -> 55 ms a step), by FP64 FMA below
+                // (mid workload: 1.05 vs 1.84 ms)
                 ProfScope q(c, "chol_inner_update", cs);
-                launch_gemm_tn(cs, nrem, rest, 1, panel, K, nullptr, 0, panel, K, nullptr, 0, nullptr, w,
-                               A + (int64_t)(j0 + w) * K + j0 + w, K, 0, -1.0, 1.0, 1);
+                if (rest >= kOzakiInnerMinRows) {
+                    launch_ozaki_split(cs, panel, K, 0, nullptr, rest, nullptr, w, 0, 32, 1, c->d_oz_si, c->d_oz_ei);
+                    launch_ozaki_gemm(cs, c->d_oz_si, rest, 0, c->d_oz_ei, c->d_oz_si, rest, 0, c->d_oz_ei, rest, nrem,
+                                      32, 1, nullptr, w, 0, A + (int64_t)(j0 + w) * K + j0 + w, K, 0, -1.0, 1.0, 1,
+                                      c->d_flag);
+                } else {
+                    launch_gemm_tn(cs, nrem, rest, 1, panel, K, nullptr, 0, panel, K, nullptr, 0, nullptr, w,
+                                   A + (int64_t)(j0 + w) * K + j0 + w, K, 0, -1.0, 1.0, 1);
+                }
             }
         }
         const int rest = K - (J0 + wo);
@@ -602,7 +614,8 @@ void free_ctx(psdp_ctx* c) {
                     c->d_opA_hi, c->d_opA_lo, c->d_opB_hi, c->d_opB_lo, c->d_prodA, c->d_prodB, c->d_T32,
                     c->d_Om32, c->d_Linv32, c->d_Pt_hi, c->d_Pt_lo, c->d_z32, c->d_trsv_sync, c->d_Pk_hi, c->d_Pk_lo, c->d_Lt_hi, c->d_Lt_lo, c->d_pcg_x, c->d_pcg_r,
                     c->d_pcg_z, c->d_pcg_p, c->d_pcg_q, c->d_pcg_state, c->d_pcg_done, c->d_M1, c->d_M2,
-                    c->d_oz_sa, c->d_oz_sb, c->d_oz_ea, c->d_oz_eb, c->d_R, c->d_Wr, c->d_CR, c->d_avec};
+                    c->d_oz_sa, c->d_oz_sb, c->d_oz_ea, c->d_oz_eb, c->d_R, c->d_Wr, c->d_CR, c->d_avec,
+                    c->d_oz_si, c->d_oz_ei};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_info) cudaFreeHost(c->h_info);
@@ -709,6 +722,8 @@ psdp_status build_schur_lists(psdp_ctx* c) {
     return PSDP_OK;
 }
 
+psdp_status alloc_ozaki(psdp_ctx* c);
+
 // Buffers of the FP64 Schur contraction and Cholesky (allocated at set-up in
 // FP64 mode, on first need in mixed mode).
 psdp_status alloc_fp64(psdp_ctx* c) {
@@ -726,6 +741,13 @@ psdp_status alloc_fp64(psdp_ctx* c) {
     TRY(dalloc(&c->d_Linv, (size_t)npanel * nbc * nbc));
     TRY(dalloc(&c->d_Linv64, (size_t)((c->K + 63) / 64) * 64 * 64));
     TRY(dalloc(&c->d_chol_ctr, (size_t)npanel));
+    TRY(alloc_ozaki(c));
+    c->have_fp64 = true;
+    return PSDP_OK;
+}
+
+// The Ozaki slice buffers for the engines chosen now.
+psdp_status alloc_ozaki(psdp_ctx* c) {
     // Ozaki slices: the Schur operands of one chunk of pairs (both sides), or one
     // outer Cholesky panel's rows, whichever is larger
     size_t sa = 0, sb = 0, ea = 0;
@@ -735,9 +757,12 @@ psdp_status alloc_fp64(psdp_ctx* c) {
         ea = (size_t)c->pairs_per_chunk * c->n2;
     }
     if (c->oz_chol) {
-        // one outer panel's rows, double-buffered by panel parity (look-ahead)
+        // one outer panel's rows, double-buffered by panel parity (look-ahead),
+        // and one inner panel's rows (depth 32) for the inner updates
         sa = std::max(sa, 2 * ozaki_slice_elems(c->K, kOzakiMaxDepth, 1));
         ea = std::max(ea, 2 * (size_t)c->K);
+        if (!c->d_oz_si) TRY(dalloc(&c->d_oz_si, ozaki_slice_elems(c->K, 32, 1)));
+        if (!c->d_oz_ei) TRY(dalloc(&c->d_oz_ei, (size_t)c->K));
     }
     if (sa) {
         TRY(dalloc(&c->d_oz_sa, sa));
@@ -747,8 +772,17 @@ psdp_status alloc_fp64(psdp_ctx* c) {
         TRY(dalloc(&c->d_oz_sb, sb));
         TRY(dalloc(&c->d_oz_eb, ea));
     }
-    c->have_fp64 = true;
     return PSDP_OK;
+}
+
+psdp_status realloc_ozaki(psdp_ctx* c) {
+    if (!c->have_fp64) return PSDP_OK;     // alloc_fp64 sizes them when it runs
+    cudaStreamSynchronize(c->stream);
+    for (void* p : {(void*)c->d_oz_sa, (void*)c->d_oz_sb, (void*)c->d_oz_ea, (void*)c->d_oz_eb})
+        if (p) cudaFree(p);
+    c->d_oz_sa = c->d_oz_sb = nullptr;
+    c->d_oz_ea = c->d_oz_eb = nullptr;
+    return alloc_ozaki(c);
 }
 
 // Buffers of the mixed-precision step and the Schur operand tensor maps.
@@ -795,10 +829,17 @@ psdp_status alloc_mixed(psdp_ctx* c) {
 // workload, K = 2100: 4.45 vs 6.64 ms a step), the Schur contraction from
 // n >= 16 (n^2 >= 256 rows); DFMA below, where the step is latency-bound.
 constexpr int kOzakiCholMinK = 1024;
-void choose_fp64_engines(psdp_ctx* c) {
+bool choose_engine_chol(const psdp_ctx* c) {
     const int e = c->opt.fp64_gemm;
-    c->oz_chol = e == PSDP_GEMM_OZAKI || (e == PSDP_GEMM_AUTO && c->K >= kOzakiCholMinK);
-    c->oz_schur = e == PSDP_GEMM_OZAKI || (e == PSDP_GEMM_AUTO && c->n2 >= 256);
+    return e == PSDP_GEMM_OZAKI || (e == PSDP_GEMM_AUTO && c->K >= kOzakiCholMinK);
+}
+bool choose_engine_schur(const psdp_ctx* c) {
+    const int e = c->opt.fp64_gemm;
+    return e == PSDP_GEMM_OZAKI || (e == PSDP_GEMM_AUTO && c->n2 >= 256);
+}
+void choose_fp64_engines(psdp_ctx* c) {
+    c->oz_chol = choose_engine_chol(c);
+    c->oz_schur = choose_engine_schur(c);
 }
 
 psdp_status setup_impl(int n, int l, int d_p, int d1, const double* A, const psdp_opts* o, psdp_ctx** out) {
@@ -1203,23 +1244,54 @@ psdp_status psdp_solve_batch(psdp_ctx** v, int count, psdp_status* status, int* 
     }
 }
 
-psdp_status psdp_autotune(psdp_ctx* c, const char* cache_path, int* choice, double* ms_out) {
-    if (!c) return PSDP_EINVAL;
+// Apply candidate `cand` of psdp_autotune_ex to the context (buffers allocated on first need).
+psdp_status apply_tune_candidate(psdp_ctx* c, int cand) {
+    const bool mixed = cand == 1 || cand == 2;
+    if (mixed && !c->d_Om32) TRY(alloc_mixed(c));
+    if (!mixed) {
+        const bool oz_s = cand == 4 || cand == 5 || (cand == 0 && choose_engine_schur(c));
+        const bool oz_c = cand == 4 || (cand == 0 && choose_engine_chol(c));
+        if ((oz_s && !c->oz_schur) || (oz_c && !c->oz_chol)) {
+            // the Ozaki slice buffers are sized at allocation: redo them for the new engines
+            c->oz_schur = oz_s;
+            c->oz_chol = oz_c;
+            TRY(realloc_ozaki(c));
+        }
+        c->oz_schur = oz_s;
+        c->oz_chol = oz_c;
+        TRY(alloc_fp64(c));
+    }
+    c->mixed = mixed;
+    c->mixed_failed = false;
+    if (mixed) c->nb32 = (cand == 1) ? 64 : 128;
+    invalidate_graph(c);
+    return PSDP_OK;
+}
+
+psdp_status psdp_autotune_ex(psdp_ctx* c, const char* cache_path, unsigned mask, int* choice, double* ms_out) {
+    if (!c || (mask & ((1u << PSDP_TUNE_CANDIDATES) - 1)) == 0) return PSDP_EINVAL;
     cudaSetDevice(c->device);
-    // candidates: 0 = FP64, 1 = mixed with 64-column FP32 panels, 2 = mixed with 128-column panels
-    char key[128];
-    snprintf(key, sizeof key, "n=%d l=%d d_p=%d d1=%d d2=%d d_a=%d", c->n, c->l, c->d_p, c->d1, c->d2, c->d_a);
+    mask &= (1u << PSDP_TUNE_CANDIDATES) - 1;
+    char key[160];
+    snprintf(key, sizeof key, "n=%d l=%d d_p=%d d1=%d d2=%d d_a=%d mask=%u", c->n, c->l, c->d_p, c->d1, c->d2, c->d_a,
+             mask);
     int best = -1;
-    double ms[3] = {-1.0, -1.0, -1.0};
+    double ms[PSDP_TUNE_CANDIDATES];
+    for (double& m : ms) m = -1.0;
     if (cache_path) {
         if (FILE* f = fopen(cache_path, "r")) {
-            char line[256];
+            char line[512];
             while (fgets(line, sizeof line, f)) {
                 int ch = -1;
+                double t[PSDP_TUNE_CANDIDATES];
                 char* bar = strchr(line, '|');
                 if (bar && (size_t)(bar - line) == strlen(key) && strncmp(line, key, strlen(key)) == 0 &&
-                    sscanf(bar + 1, "%d %lf %lf %lf", &ch, &ms[0], &ms[1], &ms[2]) >= 1)
+                    sscanf(bar + 1, "%d %lf %lf %lf %lf %lf %lf", &ch, &t[0], &t[1], &t[2], &t[3], &t[4], &t[5]) ==
+                        1 + PSDP_TUNE_CANDIDATES &&
+                    ch >= 0 && ch < PSDP_TUNE_CANDIDATES && ((mask >> ch) & 1u)) {
                     best = ch;
+                    memcpy(ms, t, sizeof ms);
+                }
             }
             fclose(f);
         }
@@ -1229,20 +1301,17 @@ psdp_status psdp_autotune(psdp_ctx* c, const char* cache_path, int* choice, doub
         const size_t nb = (size_t)c->nblk * c->n2;
         std::vector<double> X(nb), Z(nb), y(c->K);
         TRY(psdp_get_iterate(c, X.data(), Z.data(), y.data()));
-        const bool was_mixed = c->mixed;
         cudaEvent_t a, b;
         cudaEventCreate(&a);
         cudaEventCreate(&b);
-        for (int cand = 0; cand < 3; ++cand) {
-            const bool mixed = cand > 0;
-            if (mixed && !c->d_Om32) TRY(alloc_mixed(c));
-            c->nb32 = (cand == 1) ? 64 : 128;
-            invalidate_graph(c);
+        for (int cand = 0; cand < PSDP_TUNE_CANDIDATES; ++cand) {
+            if (!((mask >> cand) & 1u)) continue;
+            TRY(apply_tune_candidate(c, cand));
             float total = 0.f;
             for (int rep = 0; rep < 2; ++rep) {
                 TRY(psdp_load_iterate(c, X.data(), Z.data(), y.data()));
                 cudaEventRecord(a, c->stream);
-                TRY(launch_step(c, mixed));
+                TRY(launch_step(c, c->mixed));
                 cudaEventRecord(b, c->stream);
                 TRY(sync_check(c));
                 cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream);
@@ -1251,29 +1320,31 @@ psdp_status psdp_autotune(psdp_ctx* c, const char* cache_path, int* choice, doub
                 if (rep == 1) total = t;   // the first repetition captures the graph
             }
             ms[cand] = total;
+            if (best < 0 || ms[cand] < ms[best]) best = cand;
         }
         cudaEventDestroy(a);
         cudaEventDestroy(b);
-        best = 0;
-        for (int cand = 1; cand < 3; ++cand)
-            if (ms[cand] < ms[best]) best = cand;
-        c->mixed = was_mixed;
         TRY(psdp_load_iterate(c, X.data(), Z.data(), y.data()));
         if (cache_path) {
             if (FILE* f = fopen(cache_path, "a")) {
-                fprintf(f, "%s|%d %.4f %.4f %.4f\n", key, best, ms[0], ms[1], ms[2]);
+                fprintf(f, "%s|%d", key, best);
+                for (double m : ms) fprintf(f, " %.4f", m);
+                fprintf(f, "\n");
                 fclose(f);
             }
         }
     }
-    if (best > 0 && !c->d_Om32) TRY(alloc_mixed(c));
-    c->mixed = best > 0;
-    c->mixed_failed = false;
-    c->nb32 = (best == 1) ? 64 : 128;
-    invalidate_graph(c);
+    TRY(apply_tune_candidate(c, best));
     if (choice) *choice = best;
     if (ms_out) memcpy(ms_out, ms, sizeof ms);
     return PSDP_OK;
+}
+
+psdp_status psdp_autotune(psdp_ctx* c, const char* cache_path, int* choice, double* ms_out) {
+    double ms[PSDP_TUNE_CANDIDATES];
+    const psdp_status s = psdp_autotune_ex(c, cache_path, 7u, choice, ms);
+    if (s == PSDP_OK && ms_out) memcpy(ms_out, ms, 3 * sizeof(double));
+    return s;
 }
 
 psdp_status psdp_certify(psdp_ctx* c, int* verdict, double* minP, double* maxL) {

@@ -120,6 +120,8 @@ struct psdp_ctx {
     bool oz_chol = false, oz_schur = false;   // engines chosen at set-up
     uint16_t *d_oz_sa = nullptr, *d_oz_sb = nullptr;   // slices [batch][8][rows][dpad]
     int32_t *d_oz_ea = nullptr, *d_oz_eb = nullptr;    // row exponents [batch][rows]
+    uint16_t *d_oz_si = nullptr;                        // an inner Cholesky panel's slices [8][K][32]
+    int32_t *d_oz_ei = nullptr;                         // and row exponents [K]
     double flops_schur = 0, flops_chol = 0, flops_schur_dense = 0;
 
     // ----- misc

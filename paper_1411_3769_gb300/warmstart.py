@@ -3,11 +3,17 @@ runs in the library: solves, training, inference, start repair).
 
 Family: fixed (n, l, d_p, d1), systems drawn by ``synth.system`` with the
 uncertainty scale s uniform in a range.  Features are the flattened
-A_1..A_l; targets are the optimal dual y* (K values) and log(tr(X*_g) / n) per
-block (L + M values).  A prediction becomes a start through ``psdp_set_start``
-(y0, X_g = exp(pred_g) I, Z lifted to lambda_min >= theta / x_g); the plain
-cold start is the fallback whenever the warm-started solve does not end in the
-same kind of outcome, and every verdict is checked against the cold solve.
+A_1..A_l.  Targets describe one iterate of the plain cold-start solve: the
+dual y (K values), log(tr(X_g) / n) per block (L + M values) and log mu,
+mu = tr(ZX) / n_X.  With ``stop_iter`` = k the iterate is the one after k
+interior-point steps from the cold start: a unique, continuous function of A
+(the method is deterministic), unlike the optimal dual y*, which is not unique
+on the optimal face and so is mostly not a function of A at all.  Without it
+the targets come from the final iterate (the optimum).  A prediction becomes a
+start through ``psdp_set_start`` (y0, X_g = exp(pred_g) I, Z lifted to
+lambda_min >= theta / x_g with theta = the predicted mu); the plain cold start
+is the fallback whenever the warm-started solve does not end in the same kind of
+outcome, and every verdict is checked against the cold solve.
 """
 
 from __future__ import annotations
@@ -34,17 +40,21 @@ def draw(count: int, n: int, l: int, s_range, base_seed: int):
 CHUNK = 256   # instances per batched solve (bounds the device memory of the contexts)
 
 
-def solve_family(systems, d_p: int, d1: int, precision: int = 1, eps: float = 1e-7):
+def solve_family(systems, d_p: int, d1: int, precision: int = 1, eps: float = 1e-7, stop_iter: int | None = None):
     """Solve every system (one batched launch per iteration, CHUNK instances at
-    a time); returns features, targets, statuses, iteration counts and verdicts."""
+    a time), to the stopping rule or for stop_iter steps; returns features,
+    targets (y, log(tr X_g / n), log mu of the last iterate), statuses,
+    iteration counts and verdicts."""
     feats, targs, verdicts, status, iters = [], [], [], [], []
     for c0 in range(0, len(systems), CHUNK):
         part = systems[c0:c0 + CHUNK]
         handles = []
         try:
             for A, _ in part:
-                handles.append(bd.psdp_setup(A.shape[-1], A.shape[0], d_p, d1, A,
-                                             bd.psdp_default_opts(precision=precision, eps=eps)))
+                opts = bd.psdp_default_opts(precision=precision, eps=eps)
+                if stop_iter:
+                    opts.max_iter = stop_iter
+                handles.append(bd.psdp_setup(A.shape[-1], A.shape[0], d_p, d1, A, opts))
             st, it = bd.psdp_solve_batch(handles)
             status += list(st)
             iters += list(it)
@@ -52,14 +62,24 @@ def solve_family(systems, d_p: int, d1: int, precision: int = 1, eps: float = 1e
                 X, Z, y = bd.psdp_get_iterate(h)
                 n = A.shape[-1]
                 xs = np.log(np.maximum(np.einsum("gii->g", X) / n, 1e-30))
+                mu = float(np.einsum("gij,gji->", Z, X)) / (X.shape[0] * n)
                 feats.append(A.reshape(-1))
-                targs.append(np.concatenate([y, xs]))
+                targs.append(np.concatenate([y, xs, [np.log(max(mu, 1e-30))]]))
                 verdicts.append(bd.psdp_certify(h)[0])
         finally:
             for h in handles:
                 bd.psdp_destroy(h)
     return (np.array(feats, np.float32), np.array(targs, np.float32), status, np.array(iters),
             np.array(verdicts))
+
+
+def start_from(pred, K: int, nblk: int):
+    """(y0, x-scales, theta) of a start from one predicted target row."""
+    pred = np.asarray(pred, dtype=np.float64)
+    y0 = pred[:K]
+    xs = np.exp(np.clip(pred[K:K + nblk], -30, 30))
+    theta = float(np.exp(np.clip(pred[K + nblk], np.log(1e-8), 0.0))) if pred.shape[0] > K + nblk else THETA
+    return y0, xs, theta
 
 
 def train(feats, targs, width: int = 1024, epochs: int = 200, batch: int = 64, lr: float = 1e-3, seed: int = 0):
@@ -71,9 +91,10 @@ def train(feats, targs, width: int = 1024, epochs: int = 200, batch: int = 64, l
 
 def solve_warm(m, A, d_p: int, d1: int, K: int, nblk: int, precision: int = 1, eps: float = 1e-7):
     """Warm-started solve; falls back to the cold start if the warm run fails."""
-    pred = bd.psdp_mlp_predict(m, A.reshape(1, -1).astype(np.float32), K + nblk)[0].astype(np.float64)
+    pred = bd.psdp_mlp_predict(m, A.reshape(1, -1).astype(np.float32), K + nblk + 1)[0]
+    y0, xs, theta = start_from(pred, K, nblk)
     with bd.Solver(A, d_p, d1, precision=precision, eps=eps) as s:
-        bd.psdp_set_start(s.h, pred[:K], np.exp(np.clip(pred[K:], -30, 30)), THETA)
+        bd.psdp_set_start(s.h, y0, xs, theta)
         status, iters, info = s.solve()
         verdict = s.certify()[0]
         fallback = False
@@ -96,9 +117,9 @@ def _batch_solve(part, d_p, d1, precision, eps, starts=None):
             h = bd.psdp_setup(A.shape[-1], A.shape[0], d_p, d1, A, bd.psdp_default_opts(precision=precision, eps=eps))
             handles.append(h)
             if starts is not None:
-                K = bd.psdp_sizes(h)["K"]
-                pred = starts[k]
-                bd.psdp_set_start(h, pred[:K], np.exp(np.clip(pred[K:], -30, 30)), THETA)
+                sz = bd.psdp_sizes(h)
+                y0, xs, theta = start_from(starts[k], sz["K"], sz["nblk"])
+                bd.psdp_set_start(h, y0, xs, theta)
         st, it = bd.psdp_solve_batch(handles)
         return list(st), list(it), [bd.psdp_certify(h)[0] for h in handles]
     finally:
@@ -123,7 +144,7 @@ def evaluate(m, systems, d_p: int, d1: int, precision: int = 1, eps: float = 1e-
         first = bd.psdp_setup(part[0][0].shape[-1], part[0][0].shape[0], d_p, d1, part[0][0])
         sz = bd.psdp_sizes(first)
         bd.psdp_destroy(first)
-        n_out = sz["K"] + sz["nblk"]
+        n_out = sz["K"] + sz["nblk"] + 1
         preds = (predict(feats, n_out) if predict is not None else bd.psdp_mlp_predict(m, feats, n_out)).astype(np.float64)
         st_w, it_w, v_w = _batch_solve(part, d_p, d1, precision, eps, starts=preds)
         for k, (A, _) in enumerate(part):

@@ -85,3 +85,36 @@ def test_autotune_choice_and_cache(bd, tmp_path):
         bd.psdp_destroy(h)
     with open(cache) as fh:
         assert len(fh.read().strip().splitlines()) == 1
+
+
+def test_autotune_over_engines_and_tiles(bd, tmp_path):
+    """psdp_autotune_ex over all six step configurations (FP64 automatic, the two
+    mixed panel widths, FP64-FMA, Ozaki, Ozaki Schur with FP64-FMA Cholesky):
+    the applied choice is the fastest timed one and the tuned context solves to
+    the oracle's verdict; the cache answers the same shape and mask."""
+    w = synth.WORKLOADS["mid"]
+    A = synth.system(w["n"], w["l"], w["s"], 0)
+    cache = os.path.join(tmp_path, "tune_ex.txt")
+    h = bd.psdp_setup(w["n"], w["l"], w["d_p"], w["d1"], A)
+    try:
+        choice, ms = bd.psdp_autotune_ex(h, 0b111111, cache)
+        assert 0 <= choice < 6 and np.all(ms > 0) and ms[choice] == ms.min()
+        status, iters, info = bd.psdp_solve(h)
+        assert bd.STATUS[status] == "OK" and bd.psdp_certify(h)[0] == 1
+    finally:
+        bd.psdp_destroy(h)
+    h = bd.psdp_setup(w["n"], w["l"], w["d_p"], w["d1"], A)
+    try:
+        choice2, ms2 = bd.psdp_autotune_ex(h, 0b111111, cache)
+        assert choice2 == choice and np.allclose(ms2, ms, rtol=1e-3)
+    finally:
+        bd.psdp_destroy(h)
+    # each FP64 engine configuration on its own solves to the same verdict
+    for cand in (3, 4, 5):
+        h = bd.psdp_setup(w["n"], w["l"], w["d_p"], w["d1"], A)
+        try:
+            assert bd.psdp_autotune_ex(h, 1 << cand)[0] == cand
+            status, iters, info = bd.psdp_solve(h)
+            assert bd.STATUS[status] == "OK" and bd.psdp_certify(h)[0] == 1, cand
+        finally:
+            bd.psdp_destroy(h)
