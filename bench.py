@@ -480,9 +480,9 @@ def measure_warm(bd, n_train, n_test, device):
     t0 = time.perf_counter()
     train_sys = ws.draw(n_train, n, l, (0.1, 1.5), base_seed=5000)
     test_sys = ws.draw(n_test, n, l, (0.1, 1.5), base_seed=9000)
-    F, T, status, iters, verdicts = ws.solve_family(train_sys, d_p, d1)
+    F, T, status, iters, verdicts = ws.solve_family(train_sys, d_p, d1, stop_iter=ws.K_TARGET)
     t1 = time.perf_counter()
-    ok = np.array([s == "OK" for s in status])
+    ok = np.array([s in ("OK", "EMAXITER") for s in status])
     m, loss = ws.train(F[ok], T[ok], width=1024, epochs=200, batch=64, lr=1e-3)
     t2 = time.perf_counter()
     try:
@@ -491,8 +491,8 @@ def measure_warm(bd, n_train, n_test, device):
         # network and of the training-target mean
         mean = T[ok].mean(axis=0)
         sd = np.maximum(T[ok].std(axis=0), 1e-6)
-        Fte, Tte, st_te, _, _ = ws.solve_family(test_sys, d_p, d1)
-        okt = np.array([s == "OK" for s in st_te])
+        Fte, Tte, st_te, _, _ = ws.solve_family(test_sys, d_p, d1, stop_iter=ws.K_TARGET)
+        okt = np.array([s in ("OK", "EMAXITER") for s in st_te])
         P = bd.psdp_mlp_predict(m, Fte[okt], T.shape[1])
         res["heldout_std_mse"] = {"network": float((((P - Tte[okt]) / sd) ** 2).mean()),
                                   "mean_predictor": float((((mean - Tte[okt]) / sd) ** 2).mean())}

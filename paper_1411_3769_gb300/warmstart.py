@@ -26,6 +26,10 @@ from . import binding as bd
 from . import synth
 
 THETA = 0.1
+# the cold-start iterate the network learns to propose: after this many steps,
+# roughly a third of a cold solve on the n=32 family (4096 training systems are
+# not enough to learn the optimum, which is not unique, nor a later iterate)
+K_TARGET = 10
 
 
 def draw(count: int, n: int, l: int, s_range, base_seed: int):
