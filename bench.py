@@ -49,8 +49,15 @@ NOMINAL_TF32_TFLOPS = 1100.0
 # BF16 slice products per FP64 multiply-add in the Ozaki scheme (8 slices, levels <= 9)
 OZ_PAIRS = 36
 OZ_DEPTH = 256
-KERNEL_OF = {"schur_gemm": "k_gemm_tn", "chol_syrk_gemm": "k_syrk_tri_persist", "oz_chol": "k_ozaki_gemm",
-             "oz_schur": "k_ozaki_gemm", "chol32_syrk_tc": "k_tc_gemm_persist"}
+OZ_KERNEL = "k_ozaki_gemm_persist<64, 16>"
+# DRAM bytes per updated element of OZ_KERNEL's lower trailing update at depth 256:
+# dram__bytes_read.sum + dram__bytes_write.sum = 559.4 MB of one ncu capture of the
+# 8192 x 8192 update (33.56 M elements; profiles/ozaki_gemm_persist_8192.md).  The C
+# read-modify-write (16 B an element) dominates, so the traffic of a launch grows
+# with the elements it updates; re-capture when the kernel changes.
+OZ_DRAM_BYTES_PER_ELEMENT = 559.4e6 / (8192 * 8193 / 2)
+KERNEL_OF = {"schur_gemm": "k_gemm_tn", "chol_syrk_gemm": "k_syrk_tri_persist", "oz_chol": OZ_KERNEL,
+             "oz_schur": OZ_KERNEL, "chol32_syrk_tc": "k_tc_gemm_persist"}
 
 
 def parse():
@@ -717,7 +724,7 @@ def fp64_roofline(kern, prof, prof_ms, steps, K, work, engines, fp64_peak, pk, p
     if ozaki:
         peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
         ach = OZ_PAIRS * rate if rate else None
-        roof = {"kernel": "k_ozaki_gemm (" + dom + ", FP64 by the Ozaki scheme)", "bound": "tensor", "achieved": ach,
+        roof = {"kernel": OZ_KERNEL + " (" + dom + ", FP64 by the Ozaki scheme)", "bound": "tensor", "achieved": ach,
                 "peak": peak, "unit": "TFLOP/s", "frac": (ach / peak) if ach else None,
                 "peak_source": f"{pk_kind} bf16 sustained (kernel timed inside a seconds-long step)",
                 "counted": f"{OZ_PAIRS} BF16 slice products per FP64 multiply-add of the algorithmic work",
@@ -728,6 +735,15 @@ def fp64_roofline(kern, prof, prof_ms, steps, K, work, engines, fp64_peak, pk, p
                 "unit": "TFLOP/s", "frac": (rate / fp64_peak) if rate else None,
                 "peak_source": "measured: the larger of the DFMA and DMMA probes (psdp_fp64_peaks)"}
     roof["traffic"] = None
+    if ozaki and dom == "chol_syrk_gemm" and dom in kern:
+        # elements one bulk launch updates: its flops / (2 x depth), on average
+        elems = cf["bulk"] / (2.0 * OZ_DEPTH) / kern[dom]["launches_per_step"]
+        roof["traffic"] = OZ_DRAM_BYTES_PER_ELEMENT * elems
+        roof["traffic_unit"] = "bytes per launch"
+        roof["traffic_source"] = (f"ncu capture of {OZ_KERNEL} on the 8192 x 8192 lower update at depth 256: "
+                                  f"{OZ_DRAM_BYTES_PER_ELEMENT:.2f} B per updated element, times the elements of "
+                                  "an average bulk launch")
+        roof["algorithmic_bytes"] = 16.0 * elems      # C read and written once
     return roof
 
 

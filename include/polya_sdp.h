@@ -71,7 +71,8 @@ typedef struct {
     int    device;      /* CUDA device ordinal; default 0 */
     int    crit_sms;    /* SMs the persistent Cholesky trailing update leaves to the
                            critical path (panel factor, panel solve, next-rows
-                           update); 0 = the default (8 in FP64, 16 in the mixed form) */
+                           update); 0 = the default (8 with FP64 FMA, 16 with the
+                           Ozaki scheme and in the mixed form) */
     int    fp64_gemm;   /* engine of the FP64 form's two large contractions, the Schur
                            complement and the Cholesky trailing updates:
                            PSDP_GEMM_AUTO (default: by size), PSDP_GEMM_DFMA (FP64 FMA),

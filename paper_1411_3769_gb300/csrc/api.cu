@@ -177,9 +177,15 @@ constexpr int kOneShotWaves = 64;
 // updates in panel order, and the 32 x 32 diagonal inverses are those the
 // triangular solves use.
 constexpr int kOzakiInnerMinRows = 8192;
+// SMs the persistent bulk update leaves to the look-ahead chain: its CTAs fill
+// an SM (197 KB of shared memory, all of TMEM), so the chain's kernels run only
+// on SMs it does not hold (large workload: 476.5 ms a step with all 152 SMs,
+// 473.3 with 8 left, 469.2 with 16, 483.5 with 32).
+constexpr int kCritSmsOzaki = 16;
 void enqueue_cholesky_ozaki(psdp_ctx* c) {
     cudaStream_t st = c->stream, cs = c->crit;
     const int K = c->K, nb = c->nb_chol, OB = kOzakiMaxDepth;
+    const int crit = c->opt.crit_sms > 0 ? c->opt.crit_sms : kCritSmsOzaki;
     double* A = c->d_Om;
     const size_t slice_elems = ozaki_slice_elems(K, OB, 1);
     stream_dep(st, cs, c->ev_fork);
@@ -243,7 +249,8 @@ void enqueue_cholesky_ozaki(psdp_ctx* c) {
             // columns [wo2, rest) of T, rows from wo2 (lower part)
             ProfScope q(c, "chol_syrk_gemm", st);
             launch_ozaki_gemm(st, sl, rest, wo2, ex, sl, rest, wo2, ex, rest - wo2, rest - wo2, dpad, 1, nullptr,
-                              wo, 0, T + (int64_t)wo2 * K + wo2, K, 0, -1.0, 1.0, 1, c->d_flag);
+                              wo, 0, T + (int64_t)wo2 * K + wo2, K, 0, -1.0, 1.0, 1, c->d_flag,
+                              std::max(1, c->num_sms - crit));
         }
     }
     stream_dep(cs, st, c->ev_join);

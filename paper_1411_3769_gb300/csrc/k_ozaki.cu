@@ -30,14 +30,17 @@
 // of D_ij is at most about Kd 2^(e_i + f_j - 56) + 2^-53 |D_ij|, the accuracy of
 // an FP64 GEMM.
 //
-// Tiles: 128 rows (TMEM lanes) x 64 columns; per stage 32 of k for all 8
-// slices of both operands (64-byte swizzled rows, 96 KB), two stages.  Warp 0
-// lane 0 issues the TMA loads, warp 1 lane 0 the 36 slice-pair MMAs per
-// 16-deep k step, and all eight warps drain TMEM, warp w taking lanes
-// 32 (w % 4) .. +31 and columns 32 (w / 4) .. +31.  Every thread loads the 32
-// old C values of its row (and the column exponents go to shared memory)
-// before the main loop, so their latency is hidden under the MMAs.  Waits are
-// bounded as in the other tcgen05 kernels.
+// Kernel: persistent, one CTA per SM walking 128 x 64 tiles (128 TMEM lanes;
+// 8 levels x 64 columns fill the 512 TMEM columns); per stage 32 of k for all
+// 8 slices of both operands (64-byte swizzled rows, 96 KB), two stages.  Warp
+// 0 lane 0 issues the TMA loads, warp 1 lane 0 the 36 slice-pair MMAs per
+// 16-deep k step, and sixteen epilogue warps drain TMEM, release it to the
+// next tile's MMAs and then update C.  Measured rates that set this shape
+// (GB300, one issuing thread, operands in shared memory): an M = 128, K = 16
+// BF16 MMA takes about 44.5 cycles at N = 32 or 48, 48 at N = 64, 56 at N = 96
+// and 64 at N = 128 (the tensor-core rate), so 64 columns keep 67 % of the
+// tensor rate while the eight accumulators still fit in TMEM; more issuing
+// threads make it slower.  Waits are bounded as in the other tcgen05 kernels.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -49,16 +52,12 @@
 namespace {
 
 constexpr int OZ_S = 8;                         // slices per operand
-constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 32;
+constexpr int OZ_BM = 128, OZ_BK = 32;
 constexpr int OZ_ROW = OZ_BK * 2;               // bytes of one slice row in a stage (64-byte swizzle)
 constexpr int OZ_TA = OZ_BM * OZ_ROW;           // 8 KB
-constexpr int OZ_TB = OZ_BN * OZ_ROW;           // 4 KB
-constexpr int OZ_STAGE = OZ_S * (OZ_TA + OZ_TB);  // 96 KB
 constexpr int OZ_STAGES = 2;
-constexpr int OZ_THREADS = 256;   // 8 warps: two per TMEM lane quadrant in the epilogue
 constexpr int OZ_SPLIT_THREADS = 256;
 
-constexpr size_t oz_smem_bytes() { return (size_t)OZ_STAGES * OZ_STAGE + 1024 + 8 * (2 * OZ_STAGES + 1) + 16; }
 constexpr size_t oz_split_smem_bytes() { return (size_t)kOzakiMaxDepth * 33 * sizeof(double); }
 
 // shared-memory matrix descriptor: K-major, SWIZZLE_64B (8-row groups of 64-byte rows, 512 B apart)
@@ -70,11 +69,6 @@ __device__ __forceinline__ uint64_t sdesc64(uint32_t saddr) {
     d |= (uint64_t)1 << 46;               // descriptor version
     d |= (uint64_t)4 << 61;               // SWIZZLE_64B
     return d;
-}
-
-// instruction descriptor: F32 accumulate, BF16 A and B, both K-major, N = 64, M = 128
-constexpr uint32_t oz_idesc() {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) | ((uint32_t)(OZ_BM >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -107,19 +101,6 @@ __device__ __forceinline__ double oz_i2d(long long x) {
     const int msb = 63 - __clzll((long long)u);                      // <= 52
     const unsigned long long m = u << (52 - msb);
     return __longlong_as_double((long long)(sgn | ((unsigned long long)(msb + 1023) << 52) | (m & 0xFFFFFFFFFFFFFull)));
-}
-
-// D = (Va 2^28 + Vb) 2^E in FP64 with one rounding: Va, Vb are exact in FP64
-// (|Va|, |Vb| < 2^47), the FMA rounds once, and the power-of-two scale goes
-// into the exponent field by an integer add (ldexp only outside the normal
-// range).  One FP64 instruction: GB300's FP64 pipe is this epilogue's scarce unit.
-__device__ __forceinline__ double oz_combine(long long Va, long long Vb, int E) {
-    const double v = fma(oz_i2d(Va), 268435456.0, oz_i2d(Vb));
-    if (v == 0.0) return 0.0;
-    const long long bits = __double_as_longlong(v);
-    const int be = (int)((bits >> 52) & 0x7FF) + E;
-    if (be <= 0 || be >= 2047) return ldexp(v, E);
-    return __longlong_as_double(bits + ((long long)E << 52));
 }
 
 // Slices of one batch of operands.  Element (r, k) of batch b is
@@ -182,173 +163,17 @@ k_ozaki_split(const double* __restrict__ src, int64_t ld, int64_t src_batch, con
     }
 }
 
-// C_b = alpha * D_b + beta * C_b with D_b[i][j] = sum_k A_b[i][k] B_b[j][k] from
-// the slices of A_b (rows a_row0 + i, i < M, of slice arrays of a_rows rows) and
-// B_b (rows b_row0 + j, j < N, of b_rows) over the depth window
-// oz_depth(kd, kd_uniform, b, k_off); C_b[j * ldc + i] (column-major in i).
-// lower: only elements with i >= j, tiles wholly above the diagonal are skipped.
-__global__ void __launch_bounds__(OZ_THREADS, 1)
-k_ozaki_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
-             const int32_t* __restrict__ eA, const int32_t* __restrict__ eB, int a_rows, int a_row0, int b_rows,
-             int b_row0, int M, int N,
-             const int32_t* __restrict__ kd, int kd_uniform, int k_off, double* C, int64_t ldc, int64_t c_batch,
-             double alpha, double beta, int lower, int* flag) {
-    extern __shared__ uint8_t smem_raw[];
-    const int nt = blockIdx.x, mt = blockIdx.y, b = blockIdx.z;
-    const int m0 = mt * OZ_BM, n0 = nt * OZ_BN;
-    if (lower && m0 + OZ_BM - 1 < n0) return;
-    const uint32_t base_raw = smem_u32(smem_raw);
-    const uint32_t base = (base_raw + 1023u) & ~1023u;
-    uint8_t* gbase = smem_raw + (base - base_raw);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + OZ_STAGES * OZ_STAGE);
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * OZ_STAGES + 1);
-    __shared__ int ecol[OZ_BN];
-    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * OZ_STAGES, accb = full0 + 16 * OZ_STAGES;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int Kd = oz_depth(kd, kd_uniform, b, k_off);
-    const int nk = (Kd + OZ_BK - 1) / OZ_BK;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < OZ_STAGES; ++s) {
-            mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);
-        }
-        mbar_init(accb, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
-                     "r"(8 * OZ_BN));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    // epilogue operands, fetched now: row i, columns jc .. jc + 31 of this thread
-    const int quad = warp & 3, half = warp >> 2;
-    const int i = m0 + 32 * quad + lane;
-    const int jc = n0 + 32 * half;
-    const int ei = (i < M) ? eA[(int64_t)b * a_rows + a_row0 + i] : 0;
-    double* Cb = C + (int64_t)b * c_batch;
-    // alpha, beta classified once (FP64 compares issue on the FP64 pipe)
-    const int amode = (alpha == 1.0) ? 0 : (alpha == -1.0 ? 1 : 2);
-    const int bmode = (beta == 0.0) ? 0 : (beta == 1.0 ? 1 : 2);
-    double cold[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        const int col = jc + j;
-        cold[j] = (bmode != 0 && i < M && col < N && !(lower && i < col)) ? Cb[(int64_t)col * ldc + i] : 0.0;
-    }
-    if (threadIdx.x < OZ_BN)
-        ecol[threadIdx.x] = (n0 + (int)threadIdx.x < N) ? eB[(int64_t)b * b_rows + b_row0 + n0 + threadIdx.x] : 0;
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tmem_holder;
-
-    if (nk > 0) {
-        if (warp == 0 && lane == 0) {
-            // TMA producer: every slice of both operands for 32 of k per stage
-            int kt = 0;
-            for (; kt < nk; ++kt) {
-                const int s = kt & 1;
-                if (kt >= OZ_STAGES && !mbar_wait(empty0 + 8 * s, ((kt >> 1) - 1) & 1, flag)) break;
-                const uint32_t st = base + s * OZ_STAGE;
-                const uint32_t fb = full0 + 8 * s;
-                mbar_expect_tx(fb, OZ_STAGE);
-#pragma unroll
-                for (int p = 0; p < OZ_S; ++p)
-                    tma_load_3d(st + p * OZ_TA, &mA, fb, kt * OZ_BK, a_row0 + m0, b * OZ_S + p);
-#pragma unroll
-                for (int q = 0; q < OZ_S; ++q)
-                    tma_load_3d(st + OZ_S * OZ_TA + q * OZ_TB, &mB, fb, kt * OZ_BK, b_row0 + n0, b * OZ_S + q);
-            }
-            // every issued stage has landed before the CTA may exit
-            for (int q = (kt > OZ_STAGES ? kt - OZ_STAGES : 0); q < kt; ++q)
-                mbar_wait(full0 + 8 * (q & 1), (q >> 1) & 1, flag);
-        } else if (warp == 1 && lane == 0) {
-            // MMA issuer: level t = p + q + 2 (0-based slices) accumulates in TMEM columns [64 (t-2), 64 (t-1))
-            constexpr uint32_t idesc = oz_idesc();
-            int kt = 0;
-            for (; kt < nk; ++kt) {
-                const int s = kt & 1;
-                if (!mbar_wait(full0 + 8 * s, (kt >> 1) & 1, flag)) break;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t st = base + s * OZ_STAGE;
-#pragma unroll
-                for (int kk = 0; kk < OZ_ROW / 32; ++kk) {
-#pragma unroll
-                    for (int p = 0; p < OZ_S; ++p) {
-#pragma unroll
-                        for (int q = 0; q < OZ_S - p; ++q) {
-                            const uint32_t acc = (kt > 0 || kk > 0 || p > 0) ? 1u : 0u;
-                            mma_bf16(tmem + (uint32_t)(OZ_BN * (p + q)), sdesc64(st + p * OZ_TA + kk * 32),
-                                     sdesc64(st + OZ_S * OZ_TA + q * OZ_TB + kk * 32), idesc, acc);
-                        }
-                    }
-                }
-                mma_commit(empty0 + 8 * s);
-            }
-            mma_commit(accb);
-        }
-    }
-    __syncwarp();
-    bool ok = true;
-    if (nk > 0) ok = mbar_wait(accb, 0, flag);
-    // warp-uniform decision: the TMEM loads below are warp-collective; after a
-    // timeout (FL_TIMEOUT raised) C is left as it is
-    ok = __all_sync(0xffffffffu, ok);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
-#pragma unroll
-        for (int c0 = 0; c0 < 32; c0 += 8) {
-            uint32_t r[OZ_S][8];
-            if (nk > 0) {
-#pragma unroll
-                for (int t = 0; t < OZ_S; ++t)
-                    tmem_ld8_nw(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(OZ_BN * t + 32 * half + c0), r[t]);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            } else {
-#pragma unroll
-                for (int t = 0; t < OZ_S; ++t)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) r[t][j] = 0u;
-            }
-            if (i < M) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int col = jc + c0 + j;
-                    if (col >= N || (lower && i < col)) continue;
-                    long long T[OZ_S];
-#pragma unroll
-                    for (int t = 0; t < OZ_S; ++t) T[t] = (long long)__float2int_rn(__uint_as_float(r[t][j]));
-                    const long long Va = ((T[0] * 128 + T[1]) * 128 + T[2]) * 128 + T[3];
-                    const long long Vb = ((T[4] * 128 + T[5]) * 128 + T[6]) * 128 + T[7];
-                    // D_ij = 2^(e_i + f_j - 63) (Va 2^28 + Vb), one rounding
-                    double w = oz_combine(Va, Vb, ei + ecol[col - n0] - 63);
-                    if (amode) w = (amode == 1) ? -w : alpha * w;
-                    const double c_old = cold[c0 + j];
-                    Cb[(int64_t)col * ldc + i] = (bmode == 0) ? w : (bmode == 1 ? c_old + w : fma(beta, c_old, w));
-                }
-            }
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(8 * OZ_BN));
-    }
-}
-
-
 // Tiles of one Ozaki product in the order every role of the persistent kernel
-// walks them: batch by batch, column tile by column tile (nt), row tiles
-// (mt) inside a column; with lower only the row tiles that reach the diagonal,
-// mt >= nt * 64 / 128.
+// walks them: batch by batch, column tile by column tile (nt), row tiles (mt)
+// inside a column; with lower only the row tiles that reach the diagonal,
+// mt >= nt * BN / 128.
+template <int BN>
 struct OzWalk {
     int MT, NT, batch, lower, b, nt, off;
     __device__ OzWalk(int M, int N, int batch_, int lower_, int start)
-        : MT((M + OZ_BM - 1) / OZ_BM), NT((N + OZ_BN - 1) / OZ_BN), batch(batch_), lower(lower_), b(0), nt(0),
+        : MT((M + OZ_BM - 1) / OZ_BM), NT((N + BN - 1) / BN), batch(batch_), lower(lower_), b(0), nt(0),
           off(start) { settle(); }
-    __device__ int first(int c) const { return lower ? (c * OZ_BN) / OZ_BM : 0; }
+    __device__ int first(int c) const { return lower ? (c * BN) / OZ_BM : 0; }
     __device__ int len(int c) const { return MT - first(c); }
     __device__ void settle() {
         while (b < batch && off >= len(nt)) {
@@ -367,32 +192,63 @@ struct OzWalk {
     }
 };
 
-constexpr int OZP_THREADS = 320;   // warp 0 TMA, warp 1 MMA and TMEM, warps 2-9 epilogue
+// Shape of the persistent kernel: tiles of 128 x BN, EPI epilogue warps.  A
+// tile's eight level accumulators take 8 BN of the 512 TMEM columns, so NBUF =
+// 512 / (8 BN) tiles fit at once (BN = 32: the MMAs fill one buffer while the
+// epilogue drains the other; measured slower than BN = 64 with one buffer, as
+// the MMAs cost as much at N = 32 as at 64).  EPI = 16 drains a 128 x 64 tile
+// in about 9.7k cycles against 13.8k with 8 warps.
+template <int BN, int EPI>
+struct OzCfg {
+    static constexpr int NBUF = 512 / (8 * BN);
+    static constexpr int THREADS = 64 + 32 * EPI;     // warp 0 TMA, warp 1 MMA and TMEM, then the epilogue
+    static constexpr int CW = BN * 4 / EPI;           // columns of one epilogue warp
+    static constexpr int TB = BN * OZ_ROW;            // one B slice of a stage
+    static constexpr int STAGE = OZ_S * (OZ_TA + TB);
+    static constexpr int NBAR = 2 * OZ_STAGES + 2 * NBUF + 1;
+    static constexpr size_t SMEM = (size_t)OZ_STAGES * STAGE + 1024 + 8 * NBAR + 16;
+    // instruction descriptor: F32 accumulate, BF16 A and B, both K-major, N = BN, M = 128
+    static constexpr uint32_t IDESC =
+        (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(OZ_BM >> 4) << 24);
+    static_assert(NBUF >= 1 && 8 * BN * NBUF == 512 && CW % 8 == 0 && EPI % 4 == 0, "tile shape");
+};
 
-// Persistent form of k_ozaki_gemm: one CTA per SM (or fewer) walks the tiles
-// blockIdx.x, blockIdx.x + gridDim.x, ...  The epilogue warps drain a tile's
-// eight level accumulators into registers, combined to one FP64 value per
-// element, and release TMEM at once (barrier tfree), so the MMAs of the next
-// tile run while they read, update and write C; the TMA producer runs ahead
-// into the next tile's stages meanwhile.  Barriers: full/empty per stage,
-// accb (MMA -> epilogue, one phase per tile), tfree (epilogue -> MMA, eight
-// warp arrivals per tile).  Every wait is bounded; after a timeout the roles
-// stop walking and the CTA unwinds with FL_TIMEOUT raised.
-__global__ void __launch_bounds__(OZP_THREADS, 1)
+// C_b = alpha * D_b + beta * C_b with D_b[i][j] = sum_k A_b[i][k] B_b[j][k] from
+// the slices of A_b (rows a_row0 + i, i < M, of slice arrays of a_rows rows) and
+// B_b (rows b_row0 + j, j < N, of b_rows) over the depth window
+// oz_depth(kd, kd_uniform, b, k_off); C_b[j * ldc + i] (column-major in i).
+// lower: only elements with i >= j, tiles wholly above the diagonal are skipped.
+//
+// Persistent: one CTA per SM (or fewer) walks the tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...  Warp 0 lane 0 issues the TMA loads of every
+// stage (running up to two stages ahead, across tiles), warp 1 lane 0 the 36
+// slice-pair MMAs per 16-deep k step into the tile's TMEM buffer, and the
+// epilogue warps drain a tile's eight level accumulators into registers,
+// combined to one FP64 value per element, release the buffer (barrier tfree)
+// and then read, update and write C while the MMAs run on.  Epilogue warp w
+// takes TMEM lanes 32 (w % 4) .. +31 and CW columns.  Barriers: full/empty per
+// stage, accb per buffer (MMA -> epilogue, one phase per tile), tfree per buffer
+// (epilogue -> MMA, EPI arrivals per tile).  Every wait is bounded; after a
+// timeout the roles stop walking and the CTA unwinds with FL_TIMEOUT raised.
+template <int BN, int EPI>
+__global__ void __launch_bounds__(OzCfg<BN, EPI>::THREADS, 1)
 k_ozaki_gemm_persist(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
                      const int32_t* __restrict__ eA, const int32_t* __restrict__ eB, int a_rows, int a_row0,
                      int b_rows, int b_row0, int M, int N, int batch, const int32_t* __restrict__ kd, int kd_uniform,
                      int k_off, double* C, int64_t ldc, int64_t c_batch, double alpha, double beta, int lower,
                      int* flag) {
+    using Cfg = OzCfg<BN, EPI>;
+    using Walk = OzWalk<BN>;
+    constexpr int NBUF = Cfg::NBUF, CW = Cfg::CW;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t base_raw = smem_u32(smem_raw);
     const uint32_t base = (base_raw + 1023u) & ~1023u;
     uint8_t* gbase = smem_raw + (base - base_raw);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + OZ_STAGES * OZ_STAGE);
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * OZ_STAGES + 3);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + OZ_STAGES * Cfg::STAGE);
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + Cfg::NBAR);
     __shared__ int abort_flag;
     const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * OZ_STAGES;
-    const uint32_t accb = full0 + 16 * OZ_STAGES, tfree = accb + 8, drain = accb + 16;
+    const uint32_t accb0 = full0 + 16 * OZ_STAGES, tfree0 = accb0 + 8 * NBUF, drain = tfree0 + 8 * NBUF;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -401,15 +257,17 @@ k_ozaki_gemm_persist(const __grid_constant__ CUtensorMap mA, const __grid_consta
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
-        mbar_init(accb, 1);
-        mbar_init(tfree, 8);
+        for (int u = 0; u < NBUF; ++u) {
+            mbar_init(accb0 + 8 * u, 1);
+            mbar_init(tfree0 + 8 * u, EPI);
+        }
         mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
-                     "r"(8 * OZ_BN));
+                     "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -420,42 +278,43 @@ k_ozaki_gemm_persist(const __grid_constant__ CUtensorMap mA, const __grid_consta
     if (warp == 0 && lane == 0) {
         // TMA producer: every slice of both operands for 32 of k per stage, tile after tile
         int g = 0;
-        for (OzWalk t(M, N, batch, lower, blockIdx.x); t.valid() && !*(volatile int*)&abort_flag;
+        for (Walk t(M, N, batch, lower, blockIdx.x); t.valid() && !*(volatile int*)&abort_flag;
              t.advance(gridDim.x)) {
             const int nk = (oz_depth(kd, kd_uniform, t.b, k_off) + OZ_BK - 1) / OZ_BK;
-            const int m0 = t.mt() * OZ_BM, n0 = t.nt * OZ_BN;
+            const int m0 = t.mt() * OZ_BM, n0 = t.nt * BN;
             for (int kt = 0; kt < nk; ++kt, ++g) {
                 const int s = g % OZ_STAGES;
                 if (g >= OZ_STAGES && !mbar_wait(empty0 + 8 * s, ((g / OZ_STAGES) - 1) & 1, flag)) {
                     abort_flag = 1;
                     break;
                 }
-                const uint32_t st = base + s * OZ_STAGE;
+                const uint32_t st = base + s * Cfg::STAGE;
                 const uint32_t fb = full0 + 8 * s;
-                mbar_expect_tx(fb, OZ_STAGE);
+                mbar_expect_tx(fb, Cfg::STAGE);
 #pragma unroll
                 for (int p = 0; p < OZ_S; ++p)
                     tma_load_3d(st + p * OZ_TA, &mA, fb, kt * OZ_BK, a_row0 + m0, t.b * OZ_S + p);
 #pragma unroll
                 for (int q = 0; q < OZ_S; ++q)
-                    tma_load_3d(st + OZ_S * OZ_TA + q * OZ_TB, &mB, fb, kt * OZ_BK, b_row0 + n0, t.b * OZ_S + q);
+                    tma_load_3d(st + OZ_S * OZ_TA + q * Cfg::TB, &mB, fb, kt * OZ_BK, b_row0 + n0, t.b * OZ_S + q);
             }
         }
         // every issued stage has landed before the CTA may exit
         for (int q = (g > OZ_STAGES ? g - OZ_STAGES : 0); q < g; ++q)
             mbar_wait(full0 + 8 * (q % OZ_STAGES), (q / OZ_STAGES) & 1, flag);
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer: tile i waits until the epilogue has drained tile i - 1's accumulators
-        constexpr uint32_t idesc = oz_idesc();
+        // MMA issuer: tile i goes to buffer i % NBUF once tile i - NBUF has been drained from it
         int g = 0, i = 0;
         bool issued = false;
-        for (OzWalk t(M, N, batch, lower, blockIdx.x); t.valid() && !*(volatile int*)&abort_flag;
+        for (Walk t(M, N, batch, lower, blockIdx.x); t.valid() && !*(volatile int*)&abort_flag;
              t.advance(gridDim.x), ++i) {
-            if (i >= 1 && !mbar_wait(tfree, (i - 1) & 1, flag)) {
+            const int u = i % NBUF;
+            if (i >= NBUF && !mbar_wait(tfree0 + 8 * u, ((i / NBUF) - 1) & 1, flag)) {
                 abort_flag = 1;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t tbuf = tmem + (uint32_t)(u * 8 * BN);
             const int nk = (oz_depth(kd, kd_uniform, t.b, k_off) + OZ_BK - 1) / OZ_BK;
             for (int kt = 0; kt < nk; ++kt, ++g) {
                 const int s = g % OZ_STAGES;
@@ -464,7 +323,7 @@ k_ozaki_gemm_persist(const __grid_constant__ CUtensorMap mA, const __grid_consta
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t st = base + s * OZ_STAGE;
+                const uint32_t st = base + s * Cfg::STAGE;
 #pragma unroll
                 for (int kk = 0; kk < OZ_ROW / 32; ++kk) {
 #pragma unroll
@@ -472,8 +331,8 @@ k_ozaki_gemm_persist(const __grid_constant__ CUtensorMap mA, const __grid_consta
 #pragma unroll
                         for (int q = 0; q < OZ_S - p; ++q) {
                             const uint32_t acc = (kt > 0 || kk > 0 || p > 0) ? 1u : 0u;
-                            mma_bf16(tmem + (uint32_t)(OZ_BN * (p + q)), sdesc64(st + p * OZ_TA + kk * 32),
-                                     sdesc64(st + OZ_S * OZ_TA + q * OZ_TB + kk * 32), idesc, acc);
+                            mma_bf16(tbuf + (uint32_t)(BN * (p + q)), sdesc64(st + p * OZ_TA + kk * 32),
+                                     sdesc64(st + OZ_S * OZ_TA + q * Cfg::TB + kk * 32), Cfg::IDESC, acc);
                         }
                     }
                 }
@@ -481,7 +340,7 @@ k_ozaki_gemm_persist(const __grid_constant__ CUtensorMap mA, const __grid_consta
                 mma_commit(empty0 + 8 * s);
             }
             if (*(volatile int*)&abort_flag) break;
-            mma_commit(accb);        // a tile of depth 0 commits too: its epilogue reads zeros
+            mma_commit(accb0 + 8 * u);   // a tile of depth 0 commits too: its epilogue reads zeros
         }
         // all MMAs complete before TMEM is released
         if (issued) {
@@ -489,34 +348,33 @@ k_ozaki_gemm_persist(const __grid_constant__ CUtensorMap mA, const __grid_consta
             mbar_wait(drain, 0, flag);
         }
     } else if (warp >= 2) {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 and columns 32 h .. +31, h = (w - 2) / 4
-        const int quad = warp & 3, half = (warp - 2) >> 2;
+        const int quad = warp & 3, grp = (warp - 2) >> 2;
         const int amode = (alpha == 1.0) ? 0 : (alpha == -1.0 ? 1 : 2);
         const int bmode = (beta == 0.0) ? 0 : (beta == 1.0 ? 1 : 2);
         int i = 0;
-        for (OzWalk t(M, N, batch, lower, blockIdx.x); t.valid(); t.advance(gridDim.x), ++i) {
+        for (Walk t(M, N, batch, lower, blockIdx.x); t.valid(); t.advance(gridDim.x), ++i) {
+            const int u = i % NBUF;
             const int Kd = oz_depth(kd, kd_uniform, t.b, k_off);
-            const int m0 = t.mt() * OZ_BM, n0 = t.nt * OZ_BN;
+            const int m0 = t.mt() * OZ_BM, n0 = t.nt * BN;
             const int row = m0 + 32 * quad + lane;
-            const int jc = n0 + 32 * half;
+            const int jc = n0 + CW * grp;
             // warp-uniform decision: the TMEM loads below are warp-collective
-            const bool ok = __all_sync(0xffffffffu, mbar_wait(accb, i & 1, flag));
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(accb0 + 8 * u, (i / NBUF) & 1, flag));
             if (!ok) {
                 abort_flag = 1;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // drain: the eight levels of 32 columns, combined exactly to (Va 2^28 + Vb)
+            // drain: the eight levels of CW columns, combined exactly to (Va 2^28 + Vb)
             // in FP64 (one rounding); the 2^(e_i + f_j - 63) scale is applied below
-            double w[32];
+            const uint32_t tl0 = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(u * 8 * BN + CW * grp);
+            double w[CW];
 #pragma unroll
-            for (int c0 = 0; c0 < 32; c0 += 8) {
+            for (int c0 = 0; c0 < CW; c0 += 8) {
                 uint32_t r[OZ_S][8];
                 if (Kd > 0) {
 #pragma unroll
-                    for (int tl = 0; tl < OZ_S; ++tl)
-                        tmem_ld8_nw(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(OZ_BN * tl + 32 * half + c0),
-                                    r[tl]);
+                    for (int tl = 0; tl < OZ_S; ++tl) tmem_ld8_nw(tl0 + (uint32_t)(BN * tl + c0), r[tl]);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 } else {
 #pragma unroll
@@ -534,17 +392,17 @@ k_ozaki_gemm_persist(const __grid_constant__ CUtensorMap mA, const __grid_consta
                     w[c0 + j] = fma(oz_i2d(Va), 268435456.0, oz_i2d(Vb));
                 }
             }
-            // TMEM free for the next tile's MMAs
+            // the buffer is free for tile i + NBUF's MMAs
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(tfree);
-            // C update under the next tile's MMAs
+            if (lane == 0) mbar_arrive(tfree0 + 8 * u);
+            // C update under the next tiles' MMAs
             if (row < M) {
                 const int ei = eA[(int64_t)t.b * a_rows + a_row0 + row];
                 const int32_t* eBb = eB + (int64_t)t.b * b_rows + b_row0;
                 double* Cb = C + (int64_t)t.b * c_batch;
 #pragma unroll
-                for (int c0 = 0; c0 < 32; c0 += 8) {
+                for (int c0 = 0; c0 < CW; c0 += 8) {
                     double cold[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
@@ -575,17 +433,14 @@ k_ozaki_gemm_persist(const __grid_constant__ CUtensorMap mA, const __grid_consta
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 1) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(8 * OZ_BN));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
     }
 }
-
-constexpr size_t ozp_smem_bytes() { return (size_t)OZ_STAGES * OZ_STAGE + 1024 + 8 * (2 * OZ_STAGES + 3) + 16; }
 
 }  // namespace
 
 void init_attrs_ozaki(int smem_optin) {
-    set_max_dynamic_smem((const void*)k_ozaki_gemm, smem_optin);
-    set_max_dynamic_smem((const void*)k_ozaki_gemm_persist, smem_optin);
+    set_max_dynamic_smem((const void*)k_ozaki_gemm_persist<64, 16>, smem_optin);
     set_max_dynamic_smem((const void*)k_ozaki_split, smem_optin);
 }
 
@@ -601,6 +456,42 @@ void launch_ozaki_split(cudaStream_t st, const double* src, int64_t ld, int64_t 
                                                                          kd_uniform, k_off, dpad, out, ex);
 }
 
+// Persistent grid: one CTA per SM (ctas <= 0) or ctas, and at most one per tile.
+int persist_grid(int M, int N, int batch, int lower, int bn, int ctas) {
+    const int64_t MT = (M + OZ_BM - 1) / OZ_BM, NT = (N + bn - 1) / bn;
+    int64_t tiles = 0;
+    for (int64_t c = 0; c < NT; ++c) tiles += lower ? MT - (c * bn) / OZ_BM : MT;
+    tiles *= batch;
+    if (tiles <= 0) return 0;
+    if (ctas <= 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        ctas = sms > 0 ? sms : 1;
+    }
+    return (int)std::min<int64_t>(tiles, ctas);
+}
+
+template <int BN, int EPI>
+bool launch_persist(cudaStream_t st, const uint16_t* As, int a_rows, int a_row0, const int32_t* eA,
+                    const uint16_t* Bs, int b_rows, int b_row0, const int32_t* eB, int M, int N, int dpad, int batch,
+                    const int32_t* kd, int kd_uniform, int k_off, double* C, int64_t ldc, int64_t c_batch,
+                    double alpha, double beta, int lower, int* flag, int ctas) {
+    using Cfg = OzCfg<BN, EPI>;
+    CUtensorMap mA, mB;
+    if (!tc_make_map_swz(&mA, As, true, dpad, a_rows, (int64_t)batch * OZ_S, dpad, (int64_t)a_rows * dpad, OZ_BK,
+                         OZ_BM, 64) ||
+        !tc_make_map_swz(&mB, Bs, true, dpad, b_rows, (int64_t)batch * OZ_S, dpad, (int64_t)b_rows * dpad, OZ_BK,
+                         BN, 64))
+        return false;
+    const int grid = persist_grid(M, N, batch, lower, BN, ctas);
+    if (grid <= 0) return true;
+    k_ozaki_gemm_persist<BN, EPI><<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(mA, mB, eA, eB, a_rows, a_row0, b_rows,
+                                                                         b_row0, M, N, batch, kd, kd_uniform, k_off,
+                                                                         C, ldc, c_batch, alpha, beta, lower, flag);
+    return true;
+}
+
 bool launch_ozaki_gemm(cudaStream_t st, const uint16_t* As, int a_rows, int a_row0, const int32_t* eA,
                        const uint16_t* Bs, int b_rows, int b_row0, const int32_t* eB, int M, int N, int dpad,
                        int batch, const int32_t* kd, int kd_uniform, int k_off, double* C, int64_t ldc,
@@ -609,29 +500,8 @@ bool launch_ozaki_gemm(cudaStream_t st, const uint16_t* As, int a_rows, int a_ro
     if (dpad % OZ_BK != 0 || dpad > kOzakiMaxDepth || a_row0 + M > a_rows || b_row0 + N > b_rows || a_row0 < 0 ||
         b_row0 < 0)
         return false;
-    CUtensorMap mA, mB;
-    if (!tc_make_map_swz(&mA, As, true, dpad, a_rows, (int64_t)batch * OZ_S, dpad, (int64_t)a_rows * dpad, OZ_BK,
-                         OZ_BM, 64) ||
-        !tc_make_map_swz(&mB, Bs, true, dpad, b_rows, (int64_t)batch * OZ_S, dpad, (int64_t)b_rows * dpad, OZ_BK,
-                         OZ_BN, 64))
-        return false;
-    // persistent: one CTA per SM (at most one per tile) walks the tiles
-    const int64_t MT = (M + OZ_BM - 1) / OZ_BM, NT = (N + OZ_BN - 1) / OZ_BN;
-    int64_t tiles = 0;
-    for (int64_t c = 0; c < NT; ++c) tiles += lower ? MT - (c * OZ_BN) / OZ_BM : MT;
-    tiles *= batch;
-    if (tiles <= 0) return true;
-    if (ctas <= 0) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        ctas = sms > 0 ? sms : 1;
-    }
-    const int grid = (int)std::min<int64_t>(tiles, ctas);
-    k_ozaki_gemm_persist<<<grid, OZP_THREADS, ozp_smem_bytes(), st>>>(mA, mB, eA, eB, a_rows, a_row0, b_rows, b_row0,
-                                                                      M, N, batch, kd, kd_uniform, k_off, C, ldc,
-                                                                      c_batch, alpha, beta, lower, flag);
-    return true;
+    return launch_persist<64, 16>(st, As, a_rows, a_row0, eA, Bs, b_rows, b_row0, eB, M, N, dpad, batch, kd,
+                                  kd_uniform, k_off, C, ldc, c_batch, alpha, beta, lower, flag, ctas);
 }
 
 // Self-test on host data: C (N x M column-major, C[j*M + i]) = alpha A B^T + beta C
