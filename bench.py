@@ -507,6 +507,15 @@ def measure_warm(bd, n_train, n_test, device):
         abl = ws.evaluate(None, test_sys, d_p, d1, predict=lambda f, k: np.tile(mean, (f.shape[0], 1)))
         res["mean_predictor"] = {"warm_iters": abl["warm_iters"], "iterations_saved": abl["iterations_saved"],
                                  "verdicts_agree": abl["verdicts_agree"], "fallbacks": abl["fallbacks"]}
+        # the same held-out systems solved in plain FP64 from the cold start: the
+        # mixed + learned-warm-start form against the plain GPU path, same stopping rule
+        f64 = ws.cold_solves(test_sys, d_p, d1, precision=0)
+        res["fp64_cold"] = {"seconds": f64["seconds"], "iters": f64["iters"]}
+        res["mixed_warm_vs_fp64_cold"] = {
+            "speedup_time_to_certificate": f64["seconds"] / res["warm_s"],
+            "mixed_cold_speedup": f64["seconds"] / res["cold_s"],
+            "verdicts_agree": bool(all(a == b for a, b in zip(f64["verdicts"], res["warm_verdicts"])))}
+        res.pop("warm_verdicts", None)
     finally:
         bd.psdp_mlp_destroy(m)
     res.update(train_instances=int(ok.sum()), train_generate_s=t1 - t0, train_s=t2 - t1, final_train_loss=loss,

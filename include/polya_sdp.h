@@ -267,6 +267,17 @@ psdp_status psdp_profile_reset(psdp_ctx* c);
 psdp_status psdp_profile_get(psdp_ctx* c, int max_entries, char* names, int64_t* launches,
                              double* ms, int* count);
 
+/* Timeline of the last profiled step (the paper has no counterpart: this is
+ * instrumentation).  Entry i is one timed launch in issue order: name_ids[i]
+ * indexes the names of psdp_profile_get, t0_ms[i] / t1_ms[i] are the times its
+ * start and end events completed, in ms after the step's first timed launch
+ * started, and on_crit[i] is 1 for launches on the look-ahead's critical stream.
+ * Writes up to max_entries entries (any output pointer may be NULL) and the
+ * count to *count; an empty trace when profiling is off.  Host arrays, owned by
+ * the caller. */
+psdp_status psdp_profile_trace(psdp_ctx* c, int max_entries, int* name_ids, double* t0_ms, double* t1_ms,
+                               int* on_crit, int* count);
+
 /* Algorithmic floating-point work of one Newton step: out[0] = Schur assembly
  * flops over the non-zero (pair, block) terms, out[1] = Cholesky flops K^3/3,
  * out[2] = Schur terms in the contraction (sum over block pairs), out[3] = dense

@@ -27,7 +27,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ECHOL_BLOCK", 5: "E
 EXPORTS = ("psdp_default_opts", "psdp_setup", "psdp_sizes", "psdp_step", "psdp_solve", "psdp_certify",
            "psdp_grid_check", "psdp_get_P", "psdp_get_y", "psdp_get_tables", "psdp_load_iterate",
            "psdp_get_iterate", "psdp_get_schur", "psdp_get_schur_cols", "psdp_apply_BT", "psdp_apply_B", "psdp_profile_enable",
-           "psdp_profile_reset", "psdp_profile_get", "psdp_work", "psdp_stream", "psdp_fp64_peak",
+           "psdp_profile_reset", "psdp_profile_get", "psdp_profile_trace", "psdp_work", "psdp_stream", "psdp_fp64_peak",
            "psdp_destroy", "psdp_strerror", "psdp_tc_gemm_check", "psdp_tc_gemm_persist_check", "psdp_trsv_timeout_check", "psdp_get_schur_mixed",
            "psdp_tc_gemm_noalloc", "psdp_solve_batch", "psdp_autotune", "psdp_set_start", "psdp_mlp_create",
            "psdp_mlp_destroy", "psdp_mlp_params", "psdp_mlp_grads", "psdp_mlp_train", "psdp_mlp_predict",
@@ -81,6 +81,8 @@ def _lib():
             "psdp_profile_enable": (C.c_int, [vp, C.c_int]),
             "psdp_profile_reset": (C.c_int, [vp]),
             "psdp_profile_get": (C.c_int, [vp, C.c_int, C.c_char_p, C.POINTER(C.c_int64), dp, C.POINTER(C.c_int)]),
+            "psdp_profile_trace": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), dp, dp, C.POINTER(C.c_int),
+                                             C.POINTER(C.c_int)]),
             "psdp_work": (C.c_int, [vp, dp]),
             "psdp_stream": (vp, [vp]),
             "psdp_fp64_peak": (C.c_int, [C.c_int, dp]),
@@ -277,6 +279,20 @@ def psdp_profile_get(h, max_entries: int = 64) -> dict:
         nm = raw[32 * i:32 * (i + 1)].split(b"\0", 1)[0].decode()
         out[nm] = (int(launches[i]), float(ms[i]))
     return out
+
+
+def psdp_profile_trace(h, max_entries: int = 20000) -> list:
+    """[(name, t0_ms, t1_ms, on_crit)] of the last profiled step, in issue order."""
+    names = list(psdp_profile_get(h, 256).keys())
+    ids = np.zeros(max_entries, dtype=np.int32)
+    t0 = np.zeros(max_entries)
+    t1 = np.zeros(max_entries)
+    crit = np.zeros(max_entries, dtype=np.int32)
+    cnt = C.c_int(0)
+    ip = C.POINTER(C.c_int)
+    _check(_lib().psdp_profile_trace(h, max_entries, ids.ctypes.data_as(ip), _dp(t0), _dp(t1), crit.ctypes.data_as(ip),
+                                     C.byref(cnt)), "psdp_profile_trace")
+    return [(names[ids[i]], float(t0[i]), float(t1[i]), bool(crit[i])) for i in range(cnt.value)]
 
 
 def psdp_work(h) -> dict:

@@ -81,11 +81,23 @@ void prof_end(psdp_ctx* c, int site) {
 
 void prof_collect(psdp_ctx* c, bool mixed) {
     if (!c->prof_on) return;
-    for (const ProfSite& s : (mixed ? c->prof_sites32 : c->prof_sites)) {
-        float ms = 0.f;
+    const std::vector<ProfSite>& sites = mixed ? c->prof_sites32 : c->prof_sites;
+    c->prof_tr_id.clear();
+    c->prof_tr_crit.clear();
+    c->prof_tr_t0.clear();
+    c->prof_tr_t1.clear();
+    for (const ProfSite& s : sites) {
+        float ms = 0.f, t0 = 0.f, t1 = 0.f;
         if (cudaEventElapsedTime(&ms, s.a, s.b) == cudaSuccess) {
             c->prof_ms[s.name_id] += ms;
             c->prof_launches[s.name_id] += 1;
+        }
+        if (cudaEventElapsedTime(&t0, sites[0].a, s.a) == cudaSuccess &&
+            cudaEventElapsedTime(&t1, sites[0].a, s.b) == cudaSuccess) {
+            c->prof_tr_id.push_back(s.name_id);
+            c->prof_tr_crit.push_back(s.st == c->crit ? 1 : 0);
+            c->prof_tr_t0.push_back(t0);
+            c->prof_tr_t1.push_back(t1);
         }
     }
     cudaGetLastError();
@@ -182,10 +194,20 @@ constexpr int kOzakiInnerMinRows = 8192;
 // on SMs it does not hold (large workload: 476.5 ms a step with all 152 SMs,
 // 473.3 with 8 left, 469.2 with 16, 483.5 with 32).
 constexpr int kCritSmsOzaki = 16;
+// ... at least, and kCritSmsOzaki * kCritOzakiRows / rest for a trailing matrix
+// of rest rows, at most kCritSmsOzakiMax (large step: 468 ms fixed at 16, 463 /
+// 459 / 482 / 528 ms with 25000 / 35000 / 45000 / 60000 rows)
+constexpr int kCritOzakiRows = 35000, kCritSmsOzakiMax = 64;
 void enqueue_cholesky_ozaki(psdp_ctx* c) {
     cudaStream_t st = c->stream, cs = c->crit;
     const int K = c->K, nb = c->nb_chol, OB = kOzakiMaxDepth;
     const int crit = c->opt.crit_sms > 0 ? c->opt.crit_sms : kCritSmsOzaki;
+    // SMs left to the chain beside bulk(P): the bulk's work falls as rest^2 and the
+    // chain's as rest, so the share grows as 1/rest (psdp_opts.crit_sms fixes it)
+    auto crit_for = [&](int rest) {
+        if (c->opt.crit_sms > 0) return crit;
+        return std::min(kCritSmsOzakiMax, std::max(crit, (int)((int64_t)crit * kCritOzakiRows / std::max(rest, 1))));
+    };
     double* A = c->d_Om;
     const size_t slice_elems = ozaki_slice_elems(K, OB, 1);
     stream_dep(st, cs, c->ev_fork);
@@ -203,8 +225,22 @@ void enqueue_cholesky_ozaki(psdp_ctx* c) {
             double* panel = A + (int64_t)j0 * K + j0 + w;
             {
                 ProfScope q(c, "chol_trsm_gemm", cs);
-                launch_gemm_tn(cs, w, rest, 1, Lp, nb, nullptr, 0, panel, K, nullptr, 0, nullptr, w, panel, K, 0, 1.0,
-                               0.0, 0);
+                if (rest >= kOzakiInnerMinRows) {
+                    // P <- P L_jj^{-T} by the Ozaki scheme (depth 32): the panel and L_jj^{-1}
+                    // are split first, so the product may overwrite the panel.  On the FP64
+                    // pipe the solve of a 25000-row panel is ~8 SM-ms of DFMAs, which the
+                    // chain's SMs cannot finish under the bulk update (470 us against 55 on
+                    // the whole GPU)
+                    uint16_t* sl_l = c->d_oz_si + ozaki_slice_elems(K, 32, 1);
+                    int32_t* ex_l = c->d_oz_ei + K;
+                    launch_ozaki_split(cs, panel, K, 0, nullptr, rest, nullptr, w, 0, 32, 1, c->d_oz_si, c->d_oz_ei);
+                    launch_ozaki_split(cs, Lp, nb, 0, nullptr, w, nullptr, w, 0, 32, 1, sl_l, ex_l);
+                    launch_ozaki_gemm(cs, c->d_oz_si, rest, 0, c->d_oz_ei, sl_l, w, 0, ex_l, rest, w, 32, 1, nullptr,
+                                      w, 0, panel, K, 0, 1.0, 0.0, 0, c->d_flag);
+                } else {
+                    launch_gemm_tn(cs, w, rest, 1, Lp, nb, nullptr, 0, panel, K, nullptr, 0, nullptr, w, panel, K, 0,
+                                   1.0, 0.0, 0);
+                }
             }
             const int nrem = J0 + wo - (j0 + w);      // outer-panel columns right of this inner panel
             if (nrem > 0) {
@@ -250,7 +286,7 @@ void enqueue_cholesky_ozaki(psdp_ctx* c) {
             ProfScope q(c, "chol_syrk_gemm", st);
             launch_ozaki_gemm(st, sl, rest, wo2, ex, sl, rest, wo2, ex, rest - wo2, rest - wo2, dpad, 1, nullptr,
                               wo, 0, T + (int64_t)wo2 * K + wo2, K, 0, -1.0, 1.0, 1, c->d_flag,
-                              std::max(1, c->num_sms - crit));
+                              std::max(1, c->num_sms - crit_for(rest)));
         }
     }
     stream_dep(cs, st, c->ev_join);
@@ -768,8 +804,9 @@ psdp_status alloc_ozaki(psdp_ctx* c) {
         // and one inner panel's rows (depth 32) for the inner updates
         sa = std::max(sa, 2 * ozaki_slice_elems(c->K, kOzakiMaxDepth, 1));
         ea = std::max(ea, 2 * (size_t)c->K);
-        if (!c->d_oz_si) TRY(dalloc(&c->d_oz_si, ozaki_slice_elems(c->K, 32, 1)));
-        if (!c->d_oz_ei) TRY(dalloc(&c->d_oz_ei, (size_t)c->K));
+        // (and 32 more rows: L_jj^{-1} of the panel solve)
+        if (!c->d_oz_si) TRY(dalloc(&c->d_oz_si, ozaki_slice_elems(c->K + 32, 32, 1)));
+        if (!c->d_oz_ei) TRY(dalloc(&c->d_oz_ei, (size_t)c->K + 32));
     }
     if (sa) {
         TRY(dalloc(&c->d_oz_sa, sa));
@@ -1714,6 +1751,20 @@ psdp_status psdp_profile_get(psdp_ctx* c, int max_entries, char* names, int64_t*
         }
         if (launches) launches[i] = c->prof_launches[i];
         if (ms) ms[i] = c->prof_ms[i];
+    }
+    *count = nn;
+    return PSDP_OK;
+}
+
+psdp_status psdp_profile_trace(psdp_ctx* c, int max_entries, int* name_ids, double* t0_ms, double* t1_ms,
+                               int* on_crit, int* count) {
+    if (!c || !count || max_entries < 0) return PSDP_EINVAL;
+    const int nn = std::min<int>(max_entries, (int)c->prof_tr_id.size());
+    for (int i = 0; i < nn; ++i) {
+        if (name_ids) name_ids[i] = c->prof_tr_id[i];
+        if (t0_ms) t0_ms[i] = c->prof_tr_t0[i];
+        if (t1_ms) t1_ms[i] = c->prof_tr_t1[i];
+        if (on_crit) on_crit[i] = c->prof_tr_crit[i];
     }
     *count = nn;
     return PSDP_OK;

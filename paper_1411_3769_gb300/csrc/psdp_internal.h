@@ -120,8 +120,8 @@ struct psdp_ctx {
     bool oz_chol = false, oz_schur = false;   // engines chosen at set-up
     uint16_t *d_oz_sa = nullptr, *d_oz_sb = nullptr;   // slices [batch][8][rows][dpad]
     int32_t *d_oz_ea = nullptr, *d_oz_eb = nullptr;    // row exponents [batch][rows]
-    uint16_t *d_oz_si = nullptr;                        // an inner Cholesky panel's slices [8][K][32]
-    int32_t *d_oz_ei = nullptr;                         // and row exponents [K]
+    uint16_t *d_oz_si = nullptr;                        // an inner Cholesky panel's slices [8][K][32], then L_jj^{-1}'s [8][32][32]
+    int32_t *d_oz_ei = nullptr;                         // and row exponents [K + 32]
     double flops_schur = 0, flops_chol = 0, flops_schur_dense = 0;
 
     // ----- misc
@@ -166,6 +166,10 @@ struct psdp_ctx {
     std::vector<ProfSite> prof_sites32;   // sites of the mixed-precision step
     std::vector<ProfSite>* prof_cur = nullptr;
     std::vector<cudaEvent_t> prof_pool;   // reusable events
+    // trace of the last profiled step: per site, its name, start and end (ms
+    // after the step's first site started) and whether it ran on the critical stream
+    std::vector<int> prof_tr_id, prof_tr_crit;
+    std::vector<double> prof_tr_t0, prof_tr_t1;
     size_t prof_pool_used = 0, prof_pool_limit = 0;
 };
 

@@ -131,6 +131,22 @@ def _batch_solve(part, d_p, d1, precision, eps, starts=None):
             bd.psdp_destroy(h)
 
 
+def cold_solves(systems, d_p: int, d1: int, precision: int = 0, eps: float = 1e-7):
+    """Plain cold-start solves of the systems (batched, CHUNK at a time): wall
+    seconds, iterations and verdicts; with precision 0 (FP64) the reference
+    the mixed and warm-started solves are compared with."""
+    t, it, verdicts, status = 0.0, [], [], []
+    for c0 in range(0, len(systems), CHUNK):
+        part = systems[c0:c0 + CHUNK]
+        t0 = time.perf_counter()
+        st, its, v = _batch_solve(part, d_p, d1, precision, eps)
+        t += time.perf_counter() - t0
+        it += its
+        verdicts += v
+        status += st
+    return dict(seconds=t, iters=float(np.mean(it)), verdicts=verdicts, status=status)
+
+
 def evaluate(m, systems, d_p: int, d1: int, precision: int = 1, eps: float = 1e-7, predict=None):
     """Cold vs warm solves of held-out systems (each side batched, CHUNK at a
     time): iterations, verdicts, fallbacks, wall time.  A warm solve that ends
@@ -138,7 +154,7 @@ def evaluate(m, systems, d_p: int, d1: int, precision: int = 1, eps: float = 1e-
     its iterations count on the warm side.  predict(features, n_out) replaces
     the network's prediction when given (e.g. the training-set mean, the
     ablation without learning)."""
-    cold_it, warm_it, agree, fallbacks, t_cold, t_warm = [], [], [], 0, 0.0, 0.0
+    cold_it, warm_it, agree, fallbacks, t_cold, t_warm, warm_v = [], [], [], 0, 0.0, 0.0, []
     for c0 in range(0, len(systems), CHUNK):
         part = systems[c0:c0 + CHUNK]
         t0 = time.perf_counter()
@@ -164,6 +180,7 @@ def evaluate(m, systems, d_p: int, d1: int, precision: int = 1, eps: float = 1e-
         cold_it += it_c
         warm_it += it_w
         agree += [a == b for a, b in zip(v_c, v_w)]
+        warm_v += list(v_w)
     return dict(cold_iters=float(np.mean(cold_it)), warm_iters=float(np.mean(warm_it)),
                 iterations_saved=float(np.mean(cold_it) - np.mean(warm_it)), verdicts_agree=bool(all(agree)),
-                fallbacks=fallbacks, cold_s=t_cold, warm_s=t_warm, count=len(systems))
+                fallbacks=fallbacks, cold_s=t_cold, warm_s=t_warm, count=len(systems), warm_verdicts=warm_v)

@@ -11,6 +11,8 @@ full-size code paths, and batched solves of instances shaped like the
   have more than 64 waves of 32 x 32 tiles, so the bulk update takes the
   one-shot tiled kernel there and the persistent one later; and the same step
   by the Ozaki scheme (twenty outer panels, 1600-row Schur operands).
+* n=60, l=3, d_p=2, d1=1 (K = 10980): panels with 8192 rows or more below them
+  (Ozaki panel solves and inner updates), against the FP64-FMA engine's step.
 From the same iterate (the oracle's k-th, loaded through the C ABI) one step of
 the library must match one step of the oracle (Sec. IV-A, Algorithm 2) to the
 1e-8 relative bound of the small-size step test: the step solves Omega dy = r
@@ -96,6 +98,32 @@ def test_ozaki_engine_newton_step_matches_oracle(bd):
     Schur contraction on 1600-row operands."""
     A = synth.system(40, 3, 0.3, 3)
     _step_parity(bd, A, 2, 1, ks=(1,), engine=2)
+
+
+def test_ozaki_panels_of_8192_rows_match_the_fma_engine(bd):
+    """n=60, l=3, d_p=2, d1=1 (K = 10980): the first outer panels have 8192 rows
+    or more below them, so their panel solves and inner updates also take the
+    Ozaki product (depth 32).  One step from the same interior iterate must
+    agree with the FP64-FMA engine's step (pinned to the oracle above) to 1e-9
+    relative: both are FP64-accurate, and the step solves Omega dy = r."""
+    A = synth.system(60, 3, 0.3, 3)
+    hs = [bd.psdp_setup(60, 3, 2, 1, A, bd.psdp_default_opts(fp64_gemm=e)) for e in (1, 2)]
+    try:
+        assert bd.psdp_sizes(hs[0])["K"] == 10980
+        assert bd.psdp_engines(hs[1]) == {"schur": "ozaki", "cholesky": "ozaki"}
+        for _ in range(3):
+            assert bd.psdp_step(hs[0])[0] == 0
+        X0, Z0, y0 = bd.psdp_get_iterate(hs[0])
+        out = []
+        for h in hs:
+            bd.psdp_load_iterate(h, X0, Z0, y0)
+            assert bd.psdp_step(h)[0] == 0
+            out.append(bd.psdp_get_iterate(h))
+        for got, ref in zip(out[1], out[0]):
+            assert _rel(got, ref) <= 1e-9
+    finally:
+        for h in hs:
+            bd.psdp_destroy(h)
 
 
 def _oracle_solve_verdict(args):
