@@ -1,6 +1,7 @@
 // C ABI of the Polya/SDP library: context set-up, the Newton-step orchestration
 // (one CUDA graph per step), solve / certify and the inspection hooks.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -1216,8 +1217,14 @@ psdp_status psdp_solve_batch(psdp_ctx** v, int count, psdp_status* status, int* 
         psdp_status err = PSDP_OK;
         int remaining = count;
         bool rebuild = true;
+        // a finished instance's branch keeps running (frozen) until the graph is
+        // rebuilt: rebuild once the step work of the frozen branches, at the measured
+        // time of an iteration, costs more than half a measured rebuild
+        auto work = [&](int i) { return v[i]->flops_chol + v[i]->flops_schur + 1.0; };
+        double t_build = 0.0, t_iter = 0.0;
         while (remaining > 0 && err == PSDP_OK) {
             if (rebuild) {
+                const auto b0 = std::chrono::steady_clock::now();
                 // one graph whose branches are the step graphs of all unfinished instances
                 if (exec) cudaGraphExecDestroy(exec);
                 exec = nullptr;
@@ -1240,17 +1247,16 @@ psdp_status psdp_solve_batch(psdp_ctx** v, int count, psdp_status* status, int* 
                 if (err != PSDP_OK) break;
                 for (int i : built) frozen[i] = 0;
                 rebuild = false;
+                t_build = std::chrono::duration<double>(std::chrono::steady_clock::now() - b0).count();
             }
+            const auto l0 = std::chrono::steady_clock::now();
             if (cudaGraphLaunch(exec, bs) != cudaSuccess || cudaStreamSynchronize(bs) != cudaSuccess) {
                 err = PSDP_ECUDA;
                 break;
             }
-            int newly = 0, in_graph_frozen = 0;
+            t_iter = std::chrono::duration<double>(std::chrono::steady_clock::now() - l0).count();
             for (int i : built) {
-                if (frozen[i]) {
-                    ++in_graph_frozen;
-                    continue;
-                }
+                if (frozen[i]) continue;
                 psdp_ctx* c = v[i];
                 const bool mixed = c->mixed && !c->mixed_failed;
                 double inf[PSDP_INFO_LEN];
@@ -1264,14 +1270,18 @@ psdp_status psdp_solve_batch(psdp_ctx** v, int count, psdp_status* status, int* 
                     done[i] = 1;
                     frozen[i] = 1;
                     --remaining;
-                    ++newly;
                     // a frozen instance keeps running inside the graph until the next
                     // rebuild, but its update kernel sees the flag and leaves the iterate
                     cudaMemcpyAsync(c->d_flag, &frozen_flag, sizeof(int), cudaMemcpyHostToDevice, c->stream);
                     cudaStreamSynchronize(c->stream);
                 }
             }
-            if ((newly + in_graph_frozen) * 4 >= (int)built.size()) rebuild = true;
+            double w_all = 0.0, w_frozen = 0.0;
+            for (int i : built) {
+                w_all += work(i);
+                if (frozen[i]) w_frozen += work(i);
+            }
+            if (w_frozen / w_all * t_iter >= 0.5 * t_build) rebuild = true;
         }
         if (exec) cudaGraphExecDestroy(exec);
         for (int i = 0; i < count; ++i) {

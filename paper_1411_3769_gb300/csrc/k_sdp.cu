@@ -7,6 +7,7 @@
 #include <type_traits>
 
 #include "psdp_internal.h"
+#include "tc_ptx.cuh"
 
 namespace {
 
@@ -500,8 +501,9 @@ __global__ void k_schur_copy(int n, int nterms, const int32_t* __restrict__ desc
 template <class F>
 __global__ void __launch_bounds__(kThreads)
 k_schur_gather(int n, int Nt, int K, int p0, const int32_t* __restrict__ pa, const int32_t* __restrict__ pb,
-               const int32_t* __restrict__ svec, const F* __restrict__ T, F* Om) {
+               const int32_t* __restrict__ svec, const F* __restrict__ T, F* Om, int* flag) {
     extern __shared__ double smd[];
+    __shared__ uint64_t bar;
     F* sm = reinterpret_cast<F*>(smd);
     const int n2 = n * n;
     const int p = blockIdx.x, pl = blockIdx.y, pair = p0 + pl;
@@ -510,21 +512,35 @@ k_schur_gather(int n, int Nt, int K, int p0, const int32_t* __restrict__ pa, con
     const F* Tp = T + (int64_t)pl * n2 * n2;
     F* F1 = sm;                   // F_rs
     F* F2 = sm + n2;              // F_sr (only if r != s)
-    // 16-byte loads, unrolled, so each thread has several loads in flight (the
-    // staging is latency-bound: two CTAs per SM at n = 100)
     constexpr int V = 16 / sizeof(F);
     if (n % V == 0) {
-        using VT = typename std::conditional<sizeof(F) == 4, float4, double2>::type;
-        const int nv = n / V;
-#pragma unroll 4
-        for (int e = threadIdx.x; e < n * nv; e += blockDim.x) {
-            const int j = e / nv, u = (e - j * nv) * V;
-            *reinterpret_cast<VT*>(F1 + j * n + u) =
-                *reinterpret_cast<const VT*>(Tp + ((int64_t)r * n + j) * n2 + s * n + u);
-            if (r != s)
-                *reinterpret_cast<VT*>(F2 + j * n + u) =
-                    *reinterpret_cast<const VT*>(Tp + ((int64_t)s * n + j) * n2 + r * n + u);
+        // rows of 16-byte multiples: every row of both sub-blocks is an asynchronous
+        // bulk copy issued at once, completing on one mbarrier, so the whole 2 n^2
+        // staging is in flight together (one CTA an SM at n = 100 has nothing else
+        // to overlap it with)
+        const uint32_t mb = smem_u32(&bar);
+        const int nrow = (r != s) ? 2 * n : n;
+        const uint32_t rowb = (uint32_t)(n * sizeof(F));
+        if (threadIdx.x == 0) {
+            mbar_init(mb, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(mb, (uint32_t)nrow * rowb);
         }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            for (int j = threadIdx.x; j < nrow; j += 32) {
+                const bool second = j >= n;
+                const int jj = second ? j - n : j;
+                const F* src = Tp + ((int64_t)(second ? s : r) * n + jj) * n2 + (int64_t)(second ? r : s) * n;
+                const uint32_t dst = smem_u32((second ? F2 : F1) + jj * n);
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                    "l"(src), "r"(rowb), "r"(mb)
+                    : "memory");
+            }
+        }
+        if (!__syncthreads_and(mbar_wait(mb, 0, flag) ? 1 : 0)) return;
     } else {
 #pragma unroll 4
         for (int e = threadIdx.x; e < n2; e += blockDim.x) {
@@ -748,14 +764,14 @@ void launch_schur_gather(cudaStream_t st, psdp_ctx* c, int p0, int np) {
     const size_t sm = (size_t)2 * c->n2 * sizeof(double);
     dim3 g(c->Nt, np);
     k_schur_gather<double><<<g, kThreads, sm, st>>>(c->n, c->Nt, c->K, p0, c->d_pair_a, c->d_pair_b, c->d_svec,
-                                                    c->d_Tbuf, c->d_Om);
+                                                    c->d_Tbuf, c->d_Om, c->d_flag);
 }
 
 void launch_schur_gather32(cudaStream_t st, psdp_ctx* c, int p0, int np, const float* T, float* Om) {
     const size_t sm = (size_t)2 * c->n2 * sizeof(float);
     dim3 g(c->Nt, np);
     k_schur_gather<float><<<g, kThreads, sm, st>>>(c->n, c->Nt, c->K, p0, c->d_pair_a, c->d_pair_b, c->d_svec, T,
-                                                   Om);
+                                                   Om, c->d_flag);
 }
 
 void launch_start_fix(cudaStream_t st, psdp_ctx* c, const double* BTy, const double* eig, const double* xs,
