@@ -48,7 +48,7 @@ NOMINAL_BF16_TFLOPS = 2250.0
 NOMINAL_TF32_TFLOPS = 1100.0
 # BF16 slice products per FP64 multiply-add in the Ozaki scheme (8 slices, levels <= 9)
 OZ_PAIRS = 36
-OZ_DEPTH = 256
+OZ_DEPTH = 384
 OZ_KERNEL = "k_ozaki_gemm_persist<64, 16>"
 # DRAM bytes per updated element of OZ_KERNEL's lower trailing update at depth 256:
 # dram__bytes_read.sum + dram__bytes_write.sum = 559.4 MB of one ncu capture of the
@@ -232,11 +232,18 @@ def chol_flops(K, nb):
     return out
 
 
-def chol_flops_ozaki(K, nb=32, ob=OZ_DEPTH):
+def oz_outer(K):
+    """Outer panel width of the Ozaki Cholesky: one 384-deep exact window from
+    K = 8192 on, 256 below."""
+    return OZ_DEPTH if K >= 8192 else 256
+
+
+def chol_flops_ozaki(K, nb=32, ob=None):
     """Algorithmic flops of one FP64 Cholesky with Ozaki-scheme trailing updates, by
     kernel: 32-column panel solves (trsm), updates of the outer panel's remaining
-    columns (inner, FP64 FMA), the depth-256 update of the next outer panel's
+    columns (inner), the outer-panel-deep update of the next outer panel's
     columns (next) and of the rest of the trailing matrix (bulk), lower parts."""
+    ob = ob or oz_outer(K)
     out = {"trsm": 0.0, "inner": 0.0, "next": 0.0, "bulk": 0.0}
     for J0 in range(0, K, ob):
         wo = min(ob, K - J0)
@@ -746,7 +753,7 @@ def fp64_roofline(kern, prof, prof_ms, steps, K, work, engines, fp64_peak, pk, p
     roof["traffic"] = None
     if ozaki and dom == "chol_syrk_gemm" and dom in kern:
         # elements one bulk launch updates: its flops / (2 x depth), on average
-        elems = cf["bulk"] / (2.0 * OZ_DEPTH) / kern[dom]["launches_per_step"]
+        elems = cf["bulk"] / (2.0 * oz_outer(K)) / kern[dom]["launches_per_step"]
         roof["traffic"] = OZ_DRAM_BYTES_PER_ELEMENT * elems
         roof["traffic_unit"] = "bytes per launch"
         roof["traffic_source"] = (f"ncu capture of {OZ_KERNEL} on the 8192 x 8192 lower update at depth 256: "

@@ -178,7 +178,7 @@ constexpr int kCritSms64 = 8;
 constexpr int kOneShotWaves = 64;
 
 // Omega = L L^T with the trailing updates by the Ozaki scheme: outer panels of
-// kOzakiMaxDepth (256) columns, each factored as 32-column inner panels (FP64
+// kOzakiMaxDepth (384) columns (256 below K = 8192), each factored as 32-column inner panels (FP64
 // diagonal factor and inverse, FP64 panel solve, update of the outer panel's
 // remaining columns), then FP64-accurate updates of depth 256 from the outer
 // panel's slices.  Look-ahead of depth one at the outer level:
@@ -201,7 +201,11 @@ constexpr int kCritSmsOzaki = 16;
 constexpr int kCritOzakiRows = 35000, kCritSmsOzakiMax = 64;
 void enqueue_cholesky_ozaki(psdp_ctx* c) {
     cudaStream_t st = c->stream, cs = c->crit;
-    const int K = c->K, nb = c->nb_chol, OB = kOzakiMaxDepth;
+    // outer panels as deep as one exact Ozaki window where the factor is large: each
+    // bulk tile drains its TMEM levels once per window (large step: 445 ms with
+    // 384 columns, 455 with 256); 256 below, where the longer chain costs more
+    // (mid step: 4.56 vs 4.34-4.51 ms)
+    const int K = c->K, nb = c->nb_chol, OB = c->K >= kOzakiInnerMinRows ? kOzakiMaxDepth : 256;
     const int crit = c->opt.crit_sms > 0 ? c->opt.crit_sms : kCritSmsOzaki;
     // SMs left to the chain beside bulk(P): the bulk's work falls as rest^2 and the
     // chain's as rest, so the share grows as 1/rest (psdp_opts.crit_sms fixes it)

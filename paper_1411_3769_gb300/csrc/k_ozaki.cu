@@ -8,7 +8,7 @@
 // step (the Schur complement and the trailing updates of its Cholesky factor)
 // run here at FP64 accuracy.
 //
-// Split.  Row i of an operand (depth Kd <= 256) is scaled by 2^-e_i, where
+// Split.  Row i of an operand (depth Kd <= 384) is scaled by 2^-e_i, where
 // e_i is the exponent with max_k |a_ik| < 2^e_i, and rounded to the integer
 // X = round(a_ik 2^(56 - e_i)), |X| < 2^56.  X is written in balanced base-128
 // digits, X = sum_{p=1..8} s_p 128^(8-p): s_2..s_8 in [-64, 63] and s_1 in
@@ -18,8 +18,8 @@
 // Product.  sum_k a_ik b_jk = 2^(e_i + f_j) sum_{t=2..9} 2^(-7t) T_t with the
 // level sums T_t = sum_{p+q=t} sum_k s_p(a_ik) s_q(b_jk); the levels t > 9
 // carry less than 2^-63 of the scale and are left out.  Per k a level adds at
-// most 2 * 2^13 + (t - 3) * 2^12 <= 10 * 2^12 in magnitude, so over Kd <= 256
-// every partial sum is an integer below 2^24: the FP32 accumulation of the
+// most 2 * 2^13 + (t - 3) * 2^12 <= 10 * 2^12 in magnitude, so over Kd <= 384
+// every partial sum is an integer of at most 15,728,640 < 2^24 in magnitude: the FP32 accumulation of the
 // tensor cores is exact.  Each level has its own TMEM accumulator (8 levels x
 // 64 columns fill the 512 columns of TMEM).
 //
@@ -539,7 +539,7 @@ extern "C" psdp_status psdp_ozaki_gemm_check(int M, int N, int K, const double* 
         cudaMemcpy(dB, Bt.data(), Bt.size() * 8, cudaMemcpyHostToDevice);
         cudaMemcpy(dC, C, (size_t)M * N * 8, cudaMemcpyHostToDevice);
         cudaMemset(dflag, 0, 4);
-        // depth windows of 256: each window's product is exact, the windows are summed in FP64
+        // depth windows of kOzakiMaxDepth: each window's product is exact, the windows are summed in FP64
         for (int k0 = 0; k0 < K && s == PSDP_OK; k0 += kOzakiMaxDepth) {
             launch_ozaki_split(0, dA, M, 0, nullptr, M, nullptr, K, k0, dpad, 1, sA, eA);
             launch_ozaki_split(0, dB, N, 0, nullptr, N, nullptr, K, k0, dpad, 1, sB, eB);

@@ -283,7 +283,7 @@ cudaError_t set_attrs_tc_gemm_fp32(int smem_optin);
 // Slices: 8 BF16 digits per element, [batch][8][rows][dpad] (uint16 bit
 // patterns), row exponents [batch][rows]; depth <= kOzakiMaxDepth, dpad a
 // multiple of 32.
-constexpr int kOzakiMaxDepth = 256;
+constexpr int kOzakiMaxDepth = 384;
 void init_attrs_ozaki(int smem_optin);
 size_t ozaki_slice_elems(int rows, int dpad, int batch);
 // Each call covers the depth window [k_off, k_off + kOzakiMaxDepth) of every batch

@@ -7,7 +7,8 @@ products by Veltkamp splitting and error-free sums, accurate to about one
 rounding of the result for these well-conditioned data.  The bound the Ozaki
 product must meet follows from its construction: each row is represented to
 2^-57 of its own power-of-two scale 2^e (max |row| < 2^e <= 2 max |row|), the
-slice products are exact, and the combination rounds twice, so
+slice products are exact (every level sum an integer below 2^24 over a depth
+window of 384), and the combination rounds twice, so
 |D_oz - D| <= K 2^-56 2^(e_i + f_j) + 2^-52 |D|  <=  K 2^-54 max|A_i| max|B_j| + 2^-52 |D|.
 """
 
@@ -55,18 +56,18 @@ def dot2(A, B):
 
 
 def _bound(A, B, D):
-    """Deeper than 256 the product is formed in windows of 256, each within the
+    """Deeper than 384 the product is formed in windows of 384, each within the
     bound above, and the windows are summed in FP64 (one rounding each)."""
     K = A.shape[1]
     ra = np.abs(A).max(axis=1)[:, None]
     rb = np.abs(B).max(axis=1)[None, :]
-    windows = -(-K // 256)
+    windows = -(-K // 384)
     extra = (windows - 1) * 2.0 ** -52 * (np.abs(A) @ np.abs(B).T) if windows > 1 else 0.0
     return K * 2.0 ** -54 * ra * rb + 2.0 ** -52 * np.abs(D) + extra
 
 
 @pytest.mark.parametrize("M,N,K", [(300, 200, 256), (129, 65, 70), (128, 64, 32), (40, 300, 1), (257, 130, 200),
-                                   (100, 90, 600)])
+                                   (100, 90, 600), (200, 140, 384), (130, 70, 800)])
 def test_ozaki_product_is_fp64_accurate(bd, M, N, K):
     rng = np.random.default_rng(M + N + K)
     A = rng.normal(size=(M, K))
@@ -89,6 +90,23 @@ def test_ozaki_wide_dynamic_range(bd):
     got = bd.psdp_ozaki_gemm_check(A, B)
     ref = dot2(A, B)
     assert np.all(np.abs(got - ref) <= _bound(A, B, ref))
+
+
+def test_ozaki_level_sums_near_the_exactness_limit(bd):
+    """Every entry x = -64 (128^7 + ... + 1) 2^-56 (row scale 2^0), whose eight
+    balanced digits are all -64: every slice product is 4096 with one sign, so
+    the level sums reach (t - 1) 4096 K, 12.6 M < 2^24 at the full depth 384.
+    A tensor-core accumulation that rounded near 2^24 would miss the bound by
+    far (a level-2 unit is 2^-14 of the scale)."""
+    X = -64 * sum(128 ** j for j in range(8))
+    x = X / 2.0 ** 56
+    assert x * 2.0 ** 56 == X
+    for K in (384, 383, 768):
+        A = np.full((130, K), x)
+        B = np.full((70, K), x)
+        got = bd.psdp_ozaki_gemm_check(A, B)
+        ref = dot2(A, B)
+        assert np.all(np.abs(got - ref) <= _bound(A, B, ref))
 
 
 def test_ozaki_integer_products_are_exact(bd):
