@@ -58,7 +58,6 @@ constexpr int OZ_TA = OZ_BM * OZ_ROW;           // 8 KB
 constexpr int OZ_STAGES = 2;
 constexpr int OZ_SPLIT_THREADS = 256;
 
-constexpr size_t oz_split_smem_bytes() { return (size_t)kOzakiMaxDepth * 33 * sizeof(double); }
 
 // shared-memory matrix descriptor: K-major, SWIZZLE_64B (8-row groups of 64-byte rows, 512 B apart)
 __device__ __forceinline__ uint64_t sdesc64(uint32_t saddr) {
@@ -103,6 +102,38 @@ __device__ __forceinline__ double oz_i2d(long long x) {
     return __longlong_as_double((long long)(sgn | ((unsigned long long)(msb + 1023) << 52) | (m & 0xFFFFFFFFFFFFFull)));
 }
 
+// round-to-nearest-even of x 2^s for |x 2^s| < 2^62 by integer operations on
+// x's bits: the same integer as __double2ll_rn(ldexp(x, s)), whose conversion and
+// scaling issue on GB300's scarce FP64 pipe
+__device__ __forceinline__ long long oz_round_scaled(double x, int s) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    if (ex) m |= 1ull << 52;
+    const int sh = (ex ? ex : 1) - 1075 + s;      // |x| 2^s = m 2^sh
+    unsigned long long q;
+    if (sh >= 0) {
+        q = m << sh;
+    } else if (sh < -63) {
+        q = 0;
+    } else {
+        const int r = -sh;
+        q = m >> r;
+        const unsigned long long rem = m & ((1ull << r) - 1), half = 1ull << (r - 1);
+        if (rem > half || (rem == half && (q & 1))) ++q;
+    }
+    return (b >> 63) ? -(long long)q : (long long)q;
+}
+
+// BF16 bits of an integer d with |d| <= 256 (exact: at most 8 significant bits)
+__device__ __forceinline__ uint16_t oz_bf16_of_int(int d) {
+    if (d == 0) return 0;
+    const unsigned a = (unsigned)(d < 0 ? -d : d);
+    const int msb = 31 - __clz((int)a);
+    const unsigned bits = ((unsigned)(msb + 127) << 7) | ((a << (7 - msb)) & 0x7Fu);
+    return (uint16_t)(bits | (d < 0 ? 0x8000u : 0u));
+}
+
 // Slices of one batch of operands.  Element (r, k) of batch b is
 // src[off_b + (k_off + k) * ld + r], off_b = src_off[b] if given, else
 // b * src_batch (rows contiguous: a column-major block, or the stacked n x n
@@ -120,7 +151,7 @@ k_ozaki_split(const double* __restrict__ src, int64_t ld, int64_t src_batch, con
     __shared__ int es[32];
     const int b = blockIdx.y;
     const int r0 = blockIdx.x * 32;
-    const int kd = oz_depth(kdv, kd_uniform, b, k_off);
+    const int kd = min(oz_depth(kdv, kd_uniform, b, k_off), dpad);   // the staging holds dpad columns
     src += (src_off ? (int64_t)src_off[b] : (int64_t)b * src_batch) + (int64_t)k_off * ld;
     out += (int64_t)b * OZ_S * rows * dpad;
     ex += (int64_t)b * rows;
@@ -148,7 +179,7 @@ k_ozaki_split(const double* __restrict__ src, int64_t ld, int64_t src_batch, con
         const int rr = idx / dpad, k = idx - rr * dpad, r = r0 + rr;
         if (r >= rows) continue;
         const double x = (k < kd) ? tile[k * 33 + rr] : 0.0;
-        long long X = __double2ll_rn(ldexp(x, 56 - es[rr]));
+        long long X = oz_round_scaled(x, 56 - es[rr]);
         int dig[OZ_S];
 #pragma unroll
         for (int p = OZ_S - 1; p >= 1; --p) {
@@ -157,9 +188,9 @@ k_ozaki_split(const double* __restrict__ src, int64_t ld, int64_t src_batch, con
             X = (X - d) >> 7;
         }
         dig[0] = (int)X;
-        __nv_bfloat16* o = out + (int64_t)r * dpad + k;
+        uint16_t* o = reinterpret_cast<uint16_t*>(out) + (int64_t)r * dpad + k;
 #pragma unroll
-        for (int p = 0; p < OZ_S; ++p) o[p * slice] = __float2bfloat16_rn((float)dig[p]);
+        for (int p = 0; p < OZ_S; ++p) o[p * slice] = oz_bf16_of_int(dig[p]);
     }
 }
 
@@ -450,9 +481,10 @@ void launch_ozaki_split(cudaStream_t st, const double* src, int64_t ld, int64_t 
                         int rows, const int32_t* kdv, int kd_uniform, int k_off, int dpad, int batch, uint16_t* out_bits,
                         int32_t* ex) {
     __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(out_bits);
-    if (rows <= 0 || batch <= 0) return;
+    if (rows <= 0 || batch <= 0 || dpad <= 0 || dpad > kOzakiMaxDepth) return;
     dim3 grid((rows + 31) / 32, batch);
-    k_ozaki_split<<<grid, OZ_SPLIT_THREADS, oz_split_smem_bytes(), st>>>(src, ld, src_batch, src_off, rows, kdv,
+    // staging for the launch's own depth (at most dpad columns), not the largest window
+    k_ozaki_split<<<grid, OZ_SPLIT_THREADS, (size_t)dpad * 33 * sizeof(double), st>>>(src, ld, src_batch, src_off, rows, kdv,
                                                                          kd_uniform, k_off, dpad, out, ex);
 }
 
