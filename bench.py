@@ -646,13 +646,15 @@ def run_reference(args):
     from paper_1411_3769_gb300 import synth
     w = WORKLOAD
     A = synth.system(w["n"], w["l"], w["s"], w["seed"])
-    oracle_sample(A, w)                               # one untimed warm-up sample
+    warm = max(1, args.warmup)
+    for _ in range(warm):                             # untimed warm-up samples (~6 s each)
+        oracle_sample(A, w)
     est = [oracle_sample(A, w)[0] for _ in range(args.steps)]
     tot = sum(est)
     v = args.steps / tot
     cores = os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": 1, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "warmup": warm, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(w),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
