@@ -240,27 +240,36 @@ def oz_outer(K):
 
 def chol_flops_ozaki(K, nb=32, ob=None):
     """Algorithmic flops of one FP64 Cholesky with Ozaki-scheme trailing updates, by
-    kernel: 32-column panel solves (trsm), updates of the outer panel's remaining
-    columns (inner), the outer-panel-deep update of the next outer panel's
-    columns (next) and of the rest of the trailing matrix (bulk), lower parts."""
+    kernel: 32-column panel solves (trsm), updates of the remaining columns of the
+    inner panel's 128-column block (inner; of the whole outer panel below K = 8192),
+    the block's update of the outer panel's columns right of it (block), the
+    outer-panel-deep update of the next outer panel's columns (next) and of the
+    rest of the trailing matrix (bulk), lower parts."""
     ob = ob or oz_outer(K)
-    out = {"trsm": 0.0, "inner": 0.0, "next": 0.0, "bulk": 0.0}
+    out = {"trsm": 0.0, "inner": 0.0, "block": 0.0, "next": 0.0, "bulk": 0.0}
+    tri = lambda rows, cols: cols * rows - cols * (cols - 1) / 2      # lower part of a rows x cols block
     for J0 in range(0, K, ob):
         wo = min(ob, K - J0)
-        for j0 in range(J0, J0 + wo, nb):
-            w = min(nb, K - j0)
-            rest = K - j0 - w
-            if rest <= 0:
-                break
-            out["trsm"] += 2.0 * rest * w * w
-            nrem = J0 + wo - (j0 + w)
-            if nrem > 0:
-                out["inner"] += 2.0 * w * (nrem * rest - nrem * (nrem - 1) / 2)
+        bw = 128 if K >= 8192 else wo
+        for b0 in range(J0, J0 + wo, bw):
+            wb = min(bw, J0 + wo - b0)
+            for j0 in range(b0, b0 + wb, nb):
+                w = min(nb, K - j0)
+                rest = K - j0 - w
+                if rest <= 0:
+                    break
+                out["trsm"] += 2.0 * rest * w * w
+                nrem = b0 + wb - (j0 + w)
+                if nrem > 0:
+                    out["inner"] += 2.0 * w * tri(rest, nrem)
+            nrem_o, rest_b = J0 + wo - (b0 + wb), K - (b0 + wb)
+            if nrem_o > 0 and rest_b > 0:
+                out["block"] += 2.0 * wb * tri(rest_b, nrem_o)
         r = K - (J0 + wo)
         if r <= 0:
             break
         w2 = min(ob, r)
-        out["next"] += 2.0 * wo * (w2 * r - w2 * (w2 - 1) / 2)
+        out["next"] += 2.0 * wo * tri(r, w2)
         m = r - w2
         out["bulk"] += float(m) * (m + 1) * wo
     return out
@@ -724,7 +733,7 @@ def fp64_roofline(kern, prof, prof_ms, steps, K, work, engines, fp64_peak, pk, p
     cf = chol_flops_ozaki(K) if oz_c else chol_flops(K, work["nb_chol"])
     for name, fl in (("schur_gemm", work["schur_flops"]), ("chol_syrk_gemm", cf["bulk"]),
                      ("chol_syrk_next", cf["next"]), ("chol_trsm_gemm", cf["trsm"]),
-                     ("chol_inner_update", cf.get("inner", 0.0))):
+                     ("chol_inner_update", cf.get("inner", 0.0)), ("chol_block_update", cf.get("block", 0.0))):
         if name in prof and prof[name][0] > 0:
             launches, tms = prof[name]
             per_step = launches / steps

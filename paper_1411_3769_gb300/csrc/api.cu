@@ -218,50 +218,75 @@ void enqueue_cholesky_ozaki(psdp_ctx* c) {
     stream_dep(st, cs, c->ev_fork);
     for (int J0 = 0, P = 0; J0 < K; J0 += OB, ++P) {
         const int wo = std::min(OB, K - J0);
-        for (int j0 = J0; j0 < J0 + wo; j0 += nb) {
-            const int w = std::min(nb, K - j0);
-            double* Lp = c->d_Linv + (size_t)(j0 / nb) * nb * nb;
-            {
-                ProfScope q(c, "chol_potrf_diag", cs);
-                launch_potrf_diag(cs, A, K, j0, nb, Lp, c->d_flag);
-            }
-            const int rest = K - j0 - w;
-            if (rest <= 0) break;
-            double* panel = A + (int64_t)j0 * K + j0 + w;
-            {
-                ProfScope q(c, "chol_trsm_gemm", cs);
-                if (rest >= kOzakiInnerMinRows) {
-                    // P <- P L_jj^{-T} by the Ozaki scheme (depth 32): the panel and L_jj^{-1}
-                    // are split first, so the product may overwrite the panel.  On the FP64
-                    // pipe the solve of a 25000-row panel is ~8 SM-ms of DFMAs, which the
-                    // chain's SMs cannot finish under the bulk update (470 us against 55 on
-                    // the whole GPU)
-                    uint16_t* sl_l = c->d_oz_si + ozaki_slice_elems(K, 32, 1);
-                    int32_t* ex_l = c->d_oz_ei + K;
-                    launch_ozaki_split(cs, panel, K, 0, nullptr, rest, nullptr, w, 0, 32, 1, c->d_oz_si, c->d_oz_ei);
-                    launch_ozaki_split(cs, Lp, nb, 0, nullptr, w, nullptr, w, 0, 32, 1, sl_l, ex_l);
-                    launch_ozaki_gemm(cs, c->d_oz_si, rest, 0, c->d_oz_ei, sl_l, w, 0, ex_l, rest, w, 32, 1, nullptr,
-                                      w, 0, panel, K, 0, 1.0, 0.0, 0, c->d_flag);
-                } else {
-                    launch_gemm_tn(cs, w, rest, 1, Lp, nb, nullptr, 0, panel, K, nullptr, 0, nullptr, w, panel, K, 0,
-                                   1.0, 0.0, 0);
+        // blocks of 128 columns inside a large outer panel: an inner panel updates only
+        // its own block's columns (depth 32), and each block then updates the outer
+        // panel's columns right of it at depth 128, which drains rest x 1344 instead of
+        // rest x 2496 Ozaki elements per outer panel (large step: 432 -> 420 ms; the mid
+        // workload keeps the single block: 4.36 vs 4.41 ms)
+        const int BW = K >= kOzakiInnerMinRows ? 128 : wo;
+        for (int b0 = J0; b0 < J0 + wo; b0 += BW) {
+            const int wb = std::min(BW, J0 + wo - b0);
+            for (int j0 = b0; j0 < b0 + wb; j0 += nb) {
+                const int w = std::min(nb, K - j0);
+                double* Lp = c->d_Linv + (size_t)(j0 / nb) * nb * nb;
+                {
+                    ProfScope q(c, "chol_potrf_diag", cs);
+                    launch_potrf_diag(cs, A, K, j0, nb, Lp, c->d_flag);
+                }
+                const int rest = K - j0 - w;
+                if (rest <= 0) break;
+                double* panel = A + (int64_t)j0 * K + j0 + w;
+                {
+                    ProfScope q(c, "chol_trsm_gemm", cs);
+                    if (rest >= kOzakiInnerMinRows) {
+                        // P <- P L_jj^{-T} by the Ozaki scheme (depth 32): the panel and L_jj^{-1}
+                        // are split first, so the product may overwrite the panel.  On the FP64
+                        // pipe the solve of a 25000-row panel is ~8 SM-ms of DFMAs, which the
+                        // chain's SMs cannot finish under the bulk update (470 us against 55 on
+                        // the whole GPU)
+                        uint16_t* sl_l = c->d_oz_si + ozaki_slice_elems(K, 32, 1);
+                        int32_t* ex_l = c->d_oz_ei + K;
+                        launch_ozaki_split(cs, panel, K, 0, nullptr, rest, nullptr, w, 0, 32, 1, c->d_oz_si, c->d_oz_ei);
+                        launch_ozaki_split(cs, Lp, nb, 0, nullptr, w, nullptr, w, 0, 32, 1, sl_l, ex_l);
+                        launch_ozaki_gemm(cs, c->d_oz_si, rest, 0, c->d_oz_ei, sl_l, w, 0, ex_l, rest, w, 32, 1, nullptr,
+                                          w, 0, panel, K, 0, 1.0, 0.0, 0, c->d_flag);
+                    } else {
+                        launch_gemm_tn(cs, w, rest, 1, Lp, nb, nullptr, 0, panel, K, nullptr, 0, nullptr, w, panel, K, 0,
+                                       1.0, 0.0, 0);
+                    }
+                }
+                const int nrem = b0 + wb - (j0 + w);      // block columns right of this inner panel
+                if (nrem > 0) {
+                    // the outer panel's remaining columns, all rows below (lower part): by the
+                    // Ozaki scheme from the inner panel's own slices (depth w = 32) where the
+                    // rows are many (large workload: 99 -> 55 ms a step), by FP64 FMA below
+                    // (mid workload: 1.05 vs 1.84 ms)
+                    ProfScope q(c, "chol_inner_update", cs);
+                    if (rest >= kOzakiInnerMinRows) {
+                        launch_ozaki_split(cs, panel, K, 0, nullptr, rest, nullptr, w, 0, 32, 1, c->d_oz_si, c->d_oz_ei);
+                        launch_ozaki_gemm(cs, c->d_oz_si, rest, 0, c->d_oz_ei, c->d_oz_si, rest, 0, c->d_oz_ei, rest, nrem,
+                                          32, 1, nullptr, w, 0, A + (int64_t)(j0 + w) * K + j0 + w, K, 0, -1.0, 1.0, 1,
+                                          c->d_flag);
+                    } else {
+                        launch_gemm_tn(cs, nrem, rest, 1, panel, K, nullptr, 0, panel, K, nullptr, 0, nullptr, w,
+                                       A + (int64_t)(j0 + w) * K + j0 + w, K, 0, -1.0, 1.0, 1);
+                    }
                 }
             }
-            const int nrem = J0 + wo - (j0 + w);      // outer-panel columns right of this inner panel
-            if (nrem > 0) {
-                // the outer panel's remaining columns, all rows below (lower part): by the
-                // Ozaki scheme from the inner panel's own slices (depth w = 32) where the
-                // rows are many (large workload: 99 -> 55 ms a step), by FP64 FMA below
-                // (mid workload: 1.05 vs 1.84 ms)
-                ProfScope q(c, "chol_inner_update", cs);
-                if (rest >= kOzakiInnerMinRows) {
-                    launch_ozaki_split(cs, panel, K, 0, nullptr, rest, nullptr, w, 0, 32, 1, c->d_oz_si, c->d_oz_ei);
-                    launch_ozaki_gemm(cs, c->d_oz_si, rest, 0, c->d_oz_ei, c->d_oz_si, rest, 0, c->d_oz_ei, rest, nrem,
-                                      32, 1, nullptr, w, 0, A + (int64_t)(j0 + w) * K + j0 + w, K, 0, -1.0, 1.0, 1,
-                                      c->d_flag);
+            // the outer panel's columns right of this block, with the whole block (depth wb)
+            const int nrem_o = J0 + wo - (b0 + wb), rest_b = K - (b0 + wb);
+            if (nrem_o > 0 && rest_b > 0) {
+                ProfScope q(c, "chol_block_update", cs);
+                const double* Pb = A + (int64_t)b0 * K + b0 + wb;
+                double* Cb = A + (int64_t)(b0 + wb) * K + b0 + wb;
+                if (rest_b >= kOzakiInnerMinRows) {
+                    const int dpb = (wb + 31) / 32 * 32;
+                    launch_ozaki_split(cs, Pb, K, 0, nullptr, rest_b, nullptr, wb, 0, dpb, 1, c->d_oz_sm, c->d_oz_em);
+                    launch_ozaki_gemm(cs, c->d_oz_sm, rest_b, 0, c->d_oz_em, c->d_oz_sm, rest_b, 0, c->d_oz_em, rest_b,
+                                      nrem_o, dpb, 1, nullptr, wb, 0, Cb, K, 0, -1.0, 1.0, 1, c->d_flag);
                 } else {
-                    launch_gemm_tn(cs, nrem, rest, 1, panel, K, nullptr, 0, panel, K, nullptr, 0, nullptr, w,
-                                   A + (int64_t)(j0 + w) * K + j0 + w, K, 0, -1.0, 1.0, 1);
+                    launch_gemm_tn(cs, nrem_o, rest_b, 1, Pb, K, nullptr, 0, Pb, K, nullptr, 0, nullptr, wb, Cb, K, 0,
+                                   -1.0, 1.0, 1);
                 }
             }
         }
@@ -663,7 +688,7 @@ void free_ctx(psdp_ctx* c) {
                     c->d_Om32, c->d_Linv32, c->d_Pt_hi, c->d_Pt_lo, c->d_z32, c->d_trsv_sync, c->d_Pk_hi, c->d_Pk_lo, c->d_Lt_hi, c->d_Lt_lo, c->d_pcg_x, c->d_pcg_r,
                     c->d_pcg_z, c->d_pcg_p, c->d_pcg_q, c->d_pcg_state, c->d_pcg_done, c->d_M1, c->d_M2,
                     c->d_oz_sa, c->d_oz_sb, c->d_oz_ea, c->d_oz_eb, c->d_R, c->d_Wr, c->d_CR, c->d_avec,
-                    c->d_oz_si, c->d_oz_ei};
+                    c->d_oz_si, c->d_oz_ei, c->d_oz_sm, c->d_oz_em};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_info) cudaFreeHost(c->h_info);
@@ -812,6 +837,9 @@ psdp_status alloc_ozaki(psdp_ctx* c) {
         // (and 32 more rows: L_jj^{-1} of the panel solve)
         if (!c->d_oz_si) TRY(dalloc(&c->d_oz_si, ozaki_slice_elems(c->K + 32, 32, 1)));
         if (!c->d_oz_ei) TRY(dalloc(&c->d_oz_ei, (size_t)c->K + 32));
+        // and one 128-column block's rows (the block updates inside an outer panel)
+        if (!c->d_oz_sm) TRY(dalloc(&c->d_oz_sm, ozaki_slice_elems(c->K, 128, 1)));
+        if (!c->d_oz_em) TRY(dalloc(&c->d_oz_em, (size_t)c->K));
     }
     if (sa) {
         TRY(dalloc(&c->d_oz_sa, sa));

@@ -122,6 +122,8 @@ struct psdp_ctx {
     int32_t *d_oz_ea = nullptr, *d_oz_eb = nullptr;    // row exponents [batch][rows]
     uint16_t *d_oz_si = nullptr;                        // an inner Cholesky panel's slices [8][K][32], then L_jj^{-1}'s [8][32][32]
     int32_t *d_oz_ei = nullptr;                         // and row exponents [K + 32]
+    uint16_t *d_oz_sm = nullptr;                        // a 128-column block's rows [8][K][128]
+    int32_t *d_oz_em = nullptr;                         // and row exponents [K]
     double flops_schur = 0, flops_chol = 0, flops_schur_dense = 0;
 
     // ----- misc
