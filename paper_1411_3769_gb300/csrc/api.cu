@@ -190,6 +190,9 @@ constexpr int kOneShotWaves = 64;
 // updates in panel order, and the 32 x 32 diagonal inverses are those the
 // triangular solves use.
 constexpr int kOzakiInnerMinRows = 8192;
+// the depth-128 block updates take the Ozaki product from this many rows (large
+// step: 420 ms with FP64 FMA below 8192 rows, 414 with it below 2048)
+constexpr int kOzakiBlockMinRows = 2048;
 // SMs the persistent bulk update leaves to the look-ahead chain: its CTAs fill
 // an SM (197 KB of shared memory, all of TMEM), so the chain's kernels run only
 // on SMs it does not hold (large workload: 476.5 ms a step with all 152 SMs,
@@ -279,7 +282,7 @@ void enqueue_cholesky_ozaki(psdp_ctx* c) {
                 ProfScope q(c, "chol_block_update", cs);
                 const double* Pb = A + (int64_t)b0 * K + b0 + wb;
                 double* Cb = A + (int64_t)(b0 + wb) * K + b0 + wb;
-                if (rest_b >= kOzakiInnerMinRows) {
+                if (rest_b >= kOzakiBlockMinRows) {
                     const int dpb = (wb + 31) / 32 * 32;
                     launch_ozaki_split(cs, Pb, K, 0, nullptr, rest_b, nullptr, wb, 0, dpb, 1, c->d_oz_sm, c->d_oz_em);
                     launch_ozaki_gemm(cs, c->d_oz_sm, rest_b, 0, c->d_oz_em, c->d_oz_sm, rest_b, 0, c->d_oz_em, rest_b,
