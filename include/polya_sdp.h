@@ -337,8 +337,8 @@ psdp_status psdp_tc_gemm_persist_check(int M, int N, int K, int split, int tri, 
  * cudaFree, no allocating library routine.  Every call looks up the array's
  * device address on the current device and sets the GEMM kernel's shared-memory
  * limit there.  The call is synchronous: it returns after the product is
- * complete on `stream` (it reads the kernel's timeout flag back), so it cannot
- * be recorded into a stream capture.  Every call shares the array; calls that
+ * complete on `stream` (it reads the kernel's timeout flag back and waits for
+ * the stream).  Every call shares the array; calls that
  * overlap on the GPU (other host threads, other streams) race.  An unread CUDA
  * error left by earlier work gives ECUDA before anything is enqueued and stays
  * pending for its owner.  Errors: EINVAL, ECUDA, ETIMEOUT (bounded wait). */

@@ -7,8 +7,8 @@
 // inputs and its output.  Its scratch is the 16-byte-padded, TF32-split copy of
 // A and B that the TMA loads read.  That scratch lives in one file-scope device
 // array below, which every GPU that loads the library holds until the process
-// exits.  The call is synchronous (it reads the kernel's timeout flag back and
-// waits for its stream), so it cannot be recorded into a stream capture.
+// exits.  The call is synchronous: it reads the kernel's timeout flag back and
+// waits for its stream before it returns.
 #include "psdp_internal.h"
 
 // Largest (M + N) * Kpad the scratch holds, Kpad = K rounded up to 64:
