@@ -50,12 +50,12 @@ NOMINAL_TF32_TFLOPS = 1100.0
 OZ_PAIRS = 36
 OZ_DEPTH = 384
 OZ_KERNEL = "k_ozaki_gemm_persist<64, 16>"
-# DRAM bytes per updated element of OZ_KERNEL's lower trailing update at depth 256:
-# dram__bytes_read.sum + dram__bytes_write.sum = 559.4 MB of one ncu capture of the
+# DRAM bytes per updated element of OZ_KERNEL's lower trailing update at depth 384:
+# dram__bytes_read.sum + dram__bytes_write.sum = 618.9 MB of one ncu capture of the
 # 8192 x 8192 update (33.56 M elements; profiles/ozaki_gemm_persist_8192.md).  The C
 # read-modify-write (16 B an element) dominates, so the traffic of a launch grows
 # with the elements it updates; re-capture when the kernel changes.
-OZ_DRAM_BYTES_PER_ELEMENT = 559.4e6 / (8192 * 8193 / 2)
+OZ_DRAM_BYTES_PER_ELEMENT = 618.9e6 / (8192 * 8193 / 2)
 KERNEL_OF = {"schur_gemm": "k_gemm_tn", "chol_syrk_gemm": "k_syrk_tri_persist", "oz_chol": OZ_KERNEL,
              "oz_schur": OZ_KERNEL, "chol32_syrk_tc": "k_tc_gemm_persist"}
 
@@ -767,7 +767,7 @@ def fp64_roofline(kern, prof, prof_ms, steps, K, work, engines, fp64_peak, pk, p
         elems = cf["bulk"] / (2.0 * oz_outer(K)) / kern[dom]["launches_per_step"]
         roof["traffic"] = OZ_DRAM_BYTES_PER_ELEMENT * elems
         roof["traffic_unit"] = "bytes per launch"
-        roof["traffic_source"] = (f"ncu capture of {OZ_KERNEL} on the 8192 x 8192 lower update at depth 256: "
+        roof["traffic_source"] = (f"ncu capture of {OZ_KERNEL} on the 8192 x 8192 lower update at depth 384: "
                                   f"{OZ_DRAM_BYTES_PER_ELEMENT:.2f} B per updated element, times the elements of "
                                   "an average bulk launch")
         roof["algorithmic_bytes"] = 16.0 * elems      # C read and written once
