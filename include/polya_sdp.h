@@ -362,9 +362,10 @@ psdp_status psdp_fp64_peaks(int device, double* dfma_tflops, double* dmma_tflops
  * C <- alpha A B^T + beta C, only the elements with i >= j when lower.  Each
  * row is split into eight BF16 digits of 7 bits below its own power-of-two
  * scale; the 36 digit-pair products are exact in the tensor cores' FP32
- * accumulation and are summed in int64 and FP64 (depth windows of 256, summed
- * in FP64): the error of each element is at most about
- * K 2^-56 max|A_i| max|B_j| + 2^-52 |(AB^T)_ij| per window.  Allocates its
+ * accumulation and are summed in int64 and FP64 (depth windows of 384, summed
+ * in FP64): the error of each element is at most
+ * K 2.8 2^(e_i + f_j - 56) + 2^-53 |(AB^T)_ij| per window, where 2^e_i is the
+ * power of two just above max|A_i| (so at most K 2^-52.5 max|A_i| max|B_j|).  Allocates its
  * own scratch.  Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT (bounded wait). */
 psdp_status psdp_ozaki_gemm_check(int M, int N, int K, const double* A, const double* B, double* C, double alpha,
                                   double beta, int lower);

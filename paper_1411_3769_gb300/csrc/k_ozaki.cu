@@ -16,8 +16,9 @@
 // is exact in BF16, and a_ik = 2^e_i sum_p s_p 2^(-7p) up to 2^(e_i - 57).
 //
 // Product.  sum_k a_ik b_jk = 2^(e_i + f_j) sum_{t=2..9} 2^(-7t) T_t with the
-// level sums T_t = sum_{p+q=t} sum_k s_p(a_ik) s_q(b_jk); the levels t > 9
-// carry less than 2^-63 of the scale and are left out.  Per k a level adds at
+// level sums T_t = sum_{p+q=t} sum_k s_p(a_ik) s_q(b_jk); the levels t > 9 are
+// left out: their pairs have digits of at most 64 in magnitude, so per k they
+// carry at most 2^12 (7 2^-70 + 6 2^-77 + ...) < 7.1 2^-58 of the scale.  Per k a level adds at
 // most 2 * 2^13 + (t - 3) * 2^12 <= 10 * 2^12 in magnitude, so over Kd <= 384
 // every partial sum is an integer of at most 15,728,640 < 2^24 in magnitude: the FP32 accumulation of the
 // tensor cores is exact.  Each level has its own TMEM accumulator (8 levels x
@@ -26,9 +27,10 @@
 // Combination (epilogue).  Va = T_2 128^3 + T_3 128^2 + T_4 128 + T_5 and
 // Vb = T_6 128^3 + T_7 128^2 + T_8 128 + T_9 in int64 (exact, below 2^47 in
 // magnitude); D_ij = 2^(e_i + f_j - 63) (Va 2^28 + Vb), rounded once by an FMA
-// of the exactly converted Va and Vb.  With the split's own rounding the error
-// of D_ij is at most about Kd 2^(e_i + f_j - 56) + 2^-53 |D_ij|, the accuracy of
-// an FP64 GEMM.
+// of the exactly converted Va and Vb.  With the split's own rounding (2^(e-57)
+// an entry, so 2^(e_i + f_j - 56) a product) and the levels left out, the error
+// of D_ij is at most Kd 2.8 2^(e_i + f_j - 56) + 2^-53 |D_ij|
+// <= Kd 2^-52.5 max|a_i| max|b_j| + 2^-53 |D_ij|, the accuracy of an FP64 GEMM.
 //
 // Kernel: persistent, one CTA per SM walking 128 x 64 tiles (128 TMEM lanes;
 // 8 levels x 64 columns fill the 512 TMEM columns); per stage 32 of k for all

@@ -5,11 +5,13 @@ The reference is the compensated dot product Dot2 of Ogita, Rump & Oishi
 ("Accurate sum and dot product", SIAM J. Sci. Comput. 2005): error-free
 products by Veltkamp splitting and error-free sums, accurate to about one
 rounding of the result for these well-conditioned data.  The bound the Ozaki
-product must meet follows from its construction: each row is represented to
-2^-57 of its own power-of-two scale 2^e (max |row| < 2^e <= 2 max |row|), the
-slice products are exact (every level sum an integer below 2^24 over a depth
-window of 384), and the combination rounds twice, so
-|D_oz - D| <= K 2^-56 2^(e_i + f_j) + 2^-52 |D|  <=  K 2^-54 max|A_i| max|B_j| + 2^-52 |D|.
+product must meet follows from its construction: each entry is represented to
+2^-57 of its row's power-of-two scale 2^e (max |row| < 2^e <= 2 max |row|), so
+a product to 2^-56 of 2^(e_i + f_j); the levels t > 9 left out carry less than
+7.1 2^-58 of it per k; the slice products are exact (every level sum an integer
+below 2^24 over a depth window of 384); and the combination rounds once, plus
+one rounding against the reference, so
+|D_oz - D| <= K 2.8 2^(e_i + f_j - 56) + 2^-52 |D|.
 """
 
 import numpy as np
@@ -55,15 +57,19 @@ def dot2(A, B):
     return s + c
 
 
+def _scale(A):
+    """2^e per row: the power of two just above the row's largest magnitude."""
+    m = np.abs(A).max(axis=1)
+    return np.ldexp(1.0, np.frexp(m)[1]) * (m > 0)
+
+
 def _bound(A, B, D):
     """Deeper than 384 the product is formed in windows of 384, each within the
     bound above, and the windows are summed in FP64 (one rounding each)."""
     K = A.shape[1]
-    ra = np.abs(A).max(axis=1)[:, None]
-    rb = np.abs(B).max(axis=1)[None, :]
     windows = -(-K // 384)
     extra = (windows - 1) * 2.0 ** -52 * (np.abs(A) @ np.abs(B).T) if windows > 1 else 0.0
-    return K * 2.0 ** -54 * ra * rb + 2.0 ** -52 * np.abs(D) + extra
+    return K * 2.8 * 2.0 ** -56 * _scale(A)[:, None] * _scale(B)[None, :] + 2.0 ** -52 * np.abs(D) + extra
 
 
 @pytest.mark.parametrize("M,N,K", [(300, 200, 256), (129, 65, 70), (128, 64, 32), (40, 300, 1), (257, 130, 200),
